@@ -1,0 +1,210 @@
+/*
+ * blest.h -- C ABI of the GB300 (sm_103a) BVSS breadth-first-search library.
+ *
+ * The library implements the data-parallel path of "Graph Traversal on
+ * Tensor Cores: A BFS Framework for Modern GPUs" (Elbek & Kaya): BFS as a
+ * binary sparse-matrix x sparse-frontier product (§2, Eq. 1-2) over the
+ * Binarized Virtual Slice Set layout (§3.1), with eager (Algorithm 2) and
+ * lazy (Algorithm 3) vertex updates, bottom-up levels (Algorithm 4) behind a
+ * per-level switch (Eq. 5), multi-source BFS (§6.1, Algorithm 5) and exact
+ * closeness centrality (§6.2, Eq. 6-7).
+ *
+ * Conventions shared by every entry point
+ *  - Graphs are CSR: row_ptr (int64, n+1 entries, row_ptr[0] = 0,
+ *    non-decreasing) and col_idx (int32, row_ptr[n] entries, each in [0, n)).
+ *    Row v lists the out-neighbours of v.  An undirected graph is given as a
+ *    symmetric CSR.  Rows need not be sorted; duplicate arcs and self loops
+ *    are ignored (they change no BFS level).
+ *  - Input arrays are caller-owned and may be host or device memory; they are
+ *    copied during the call and not retained.
+ *  - Output arrays are caller-allocated and may be host or device memory
+ *    (detected with cudaPointerGetAttributes).  Vertex ids in outputs are
+ *    always the caller's original ids: any reordering done by blest_build is
+ *    undone on the device.
+ *  - Levels are int32 hop distances from the source; unreached = -1.
+ *  - Every call is ordered on the handle's CUDA stream (blest_set_stream).
+ *    By default a call returns after its work is complete and reports any
+ *    device-side error (for example a grid-barrier timeout).  In asynchronous
+ *    mode a call whose outputs are all device memory returns after enqueueing
+ *    and blest_sync() reports the device status.
+ *  - A handle is not thread-safe: calls on one handle must be serialised.
+ *    Different handles may be used concurrently.
+ *  - On BLEST_ERR_INVALID the outputs are untouched.
+ */
+#ifndef BLEST_H
+#define BLEST_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct blest_graph *blest_handle;
+
+typedef enum {
+    BLEST_OK = 0,
+    BLEST_ERR_INVALID = 1,     /* bad argument, malformed CSR, source out of range */
+    BLEST_ERR_OOM = 2,         /* device or pinned-host allocation failed */
+    BLEST_ERR_CUDA = 3,        /* a CUDA runtime call failed (no GPU, launch failure) */
+    BLEST_ERR_TIMEOUT = 4,     /* a device-side wait exceeded its time budget */
+    BLEST_ERR_UNSUPPORTED = 5, /* valid request this build or graph does not support */
+    BLEST_ERR_INTERNAL = 6     /* a device-side consistency check failed */
+} blest_status;
+
+/* Vertex reordering applied by blest_build (§4). */
+enum {
+    BLEST_REORDER_NONE = 0,
+    BLEST_REORDER_RCM = 1,      /* reverse Cuthill-McKee (§4.2) */
+    BLEST_REORDER_JACCARD = 2,  /* JaccardWithWindows (§4.1, Algorithm 1) */
+    BLEST_REORDER_AUTO = 3      /* Jaccard if scale-free-like (§4.2 footnote), else RCM */
+};
+
+/* Per-level kernel choices. */
+enum {
+    BLEST_MODE_PUSH_EAGER_CC = 0,  /* Algorithm 2, CUDA-core AND + byte test */
+    BLEST_MODE_PUSH_EAGER_TC = 1,  /* Algorithm 2, m8n8k128 b1 AND.POPC (Fig. 3 layout) */
+    BLEST_MODE_PUSH_LAZY_CC = 2,   /* Algorithm 3 stage 1 on CUDA cores + stage 2 */
+    BLEST_MODE_PUSH_LAZY_TC = 3,   /* Algorithm 3 stage 1 on tensor cores + stage 2 */
+    BLEST_MODE_BOTTOM_UP = 4,      /* Algorithm 4 + stage 2 */
+    BLEST_NUM_MODES = 5
+};
+
+/* How the per-level mode is chosen. */
+enum {
+    BLEST_POLICY_HEURISTIC = 0, /* §5.3/§7.1: eager vs lazy by U_div, bottom-up by Eq. 5 */
+    BLEST_POLICY_LEARNED = 1,   /* MLP over per-level features (weights via blest_load_model) */
+    BLEST_POLICY_FIXED = 2,     /* one mode for every level (fixed_mode) */
+    BLEST_POLICY_SCHEDULE = 3   /* per-level modes from blest_set_schedule (testing) */
+};
+
+typedef struct blest_build_opts {
+    int32_t reorder;         /* BLEST_REORDER_*; default NONE */
+    int32_t sigma;           /* slice width; 8 (default) */
+    int32_t directed;        /* 0: CSR is symmetric (undirected); 1: directed */
+    int32_t jaccard_window;  /* W of Algorithm 1; default 65536, multiple of sigma */
+    int32_t probe_switch;    /* 1 (default): the 3-source switching probe of §7.1 runs at build */
+    int32_t engine_tc;       /* 1 (default): top-down levels use the b1 MMA; 0: CUDA cores */
+    float eta;               /* Eq. 5 constant; default 10 */
+    double udiv_threshold;   /* lazy if U_div > threshold (§7.1); default 25000 */
+    int32_t timeout_ms;      /* budget of each device-side wait; default 5000 */
+    int32_t block_threads;   /* CTA size of the persistent kernels; 0 = 512 */
+} blest_build_opts;
+
+/* Build-time facts about a handle. */
+typedef struct blest_info {
+    int64_t n, nnz;          /* vertices, distinct non-loop arcs */
+    int64_t num_slice_sets;  /* N_s */
+    int64_t num_vss;         /* N_v */
+    int64_t num_slices;
+    double update_divergence;/* U_div (§4.2) */
+    int32_t lazy;            /* 1 if the heuristic policy uses Algorithm 3 */
+    int32_t switching;       /* 1 if bottom-up switching is enabled */
+    int32_t reorder;         /* the reordering actually applied */
+    int32_t sigma;
+    int32_t grid_blocks;     /* persistent-kernel grid */
+    int32_t block_threads;
+    double build_ms;         /* device time of the build */
+    int64_t device_bytes;    /* device memory held by the handle */
+} blest_info;
+
+/* One record per BFS level of the last single-source BFS. */
+typedef struct blest_level_log {
+    int32_t level;           /* level being computed (1 = neighbours of the source) */
+    int32_t mode;            /* BLEST_MODE_* that ran */
+    int64_t frontier;        /* |X_{level-1}|: vertices in the input frontier */
+    int64_t frontier_edges;  /* out-arcs of those vertices */
+    int64_t unvisited;       /* vertices not visited before this level */
+    int64_t queue;           /* |Q_curr|: VSSs scheduled */
+    int64_t t_ns;            /* device time of the level (globaltimer) */
+} blest_level_log;
+
+/* Fill *opts with the defaults documented above. */
+void blest_default_opts(blest_build_opts *opts);
+
+/* Build a handle from a CSR graph (§3.1 BVSS construction, §4 reordering).
+ * n >= 1.  opts may be NULL (defaults).  The handle owns all device memory
+ * and must be released with blest_destroy.  Returns INVALID for a malformed
+ * CSR, UNSUPPORTED for sigma != 8 or n >= 2^31. */
+blest_status blest_build(int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
+                         const blest_build_opts *opts, blest_handle *out);
+
+/* Single-source BFS (Algorithms 2-4 under the handle's policy).
+ * levels: n int32 values, indexed by original vertex id. */
+blest_status blest_bfs(blest_handle h, int32_t source, int32_t *levels);
+
+/* Multi-source BFS (§6.1, Algorithm 5): k sources (1 <= k <= 1024,
+ * duplicates allowed) as bit lanes.  levels: k*n int32, levels[c*n + v] is
+ * the distance from sources[c] to v. */
+blest_status blest_msbfs(blest_handle h, const int32_t *sources, int32_t k, int32_t *levels);
+
+/* Exact closeness centrality by all-source BFS in 1024-lane batches (§6.2).
+ * far: n int64 distance sums (Eq. 6); cc: n doubles, cc[u] = (reach[u]-1) /
+ * far[u] (Eq. 7 with component-size normalisation; 0 when far[u] = 0), may be
+ * NULL; reach: n int64 component sizes, may be NULL.  Undirected graphs only
+ * (UNSUPPORTED otherwise). */
+blest_status blest_closeness(blest_handle h, int64_t *far, double *cc, int64_t *reach);
+
+/* Many small graphs in one handle: graph i has vertices [vtx_off[i],
+ * vtx_off[i+1]) (local ids from 0) and arcs [edge_off[i], edge_off[i+1]);
+ * its local row pointer is row_ptr[vtx_off[i] + i .. vtx_off[i+1] + i]
+ * (offsets relative to edge_off[i]).  Undirected graphs only. */
+blest_status blest_build_many(int32_t g, const int64_t *vtx_off, const int64_t *edge_off,
+                              const int64_t *row_ptr, const int32_t *col_idx_local,
+                              const blest_build_opts *opts, blest_handle *out);
+
+/* One BFS per graph of a blest_build_many handle, all in one persistent
+ * launch.  sources: g local ids; levels: sum of n_i int32, graph i at
+ * vtx_off[i]. */
+blest_status blest_bfs_many(blest_handle h, const int32_t *sources, int32_t *levels);
+
+/* Choose the per-level policy.  fixed_mode is used by BLEST_POLICY_FIXED. */
+blest_status blest_set_policy(blest_handle h, int32_t policy, int32_t fixed_mode);
+
+/* Per-level modes for BLEST_POLICY_SCHEDULE: level l (1-based) runs
+ * modes[(l-1) % len].  Copied. */
+blest_status blest_set_schedule(blest_handle h, const int32_t *modes, int32_t len);
+
+/* Load MLP weights for BLEST_POLICY_LEARNED (layout in blest_mlp_*). */
+blest_status blest_load_model(blest_handle h, const float *weights, int32_t nweights);
+
+/* Copy the per-level log of the last blest_bfs into buf (cap records);
+ * *len receives the number of levels. */
+blest_status blest_last_timings(blest_handle h, blest_level_log *buf, int64_t cap, int64_t *len);
+
+/* Build facts. */
+blest_status blest_get_info(blest_handle h, blest_info *info);
+
+/* Copy the device BVSS arrays (§3.1) to caller buffers (host or device):
+ * rowIds N_v*32*theta int32, masks N_v*32 uint32, realPtrs N_s+1 int32,
+ * virtualToReal N_v int32.  Any pointer may be NULL.  Ids are in the
+ * reordered space (see blest_get_perm). */
+blest_status blest_get_bvss(blest_handle h, int32_t *row_ids, uint32_t *masks, int32_t *real_ptrs,
+                            int32_t *virtual_to_real);
+
+/* new_of_old[v] = position of original vertex v after reordering. */
+blest_status blest_get_perm(blest_handle h, int32_t *new_of_old);
+
+/* Use a caller CUDA stream (a cudaStream_t, NULL = the handle's own).
+ * async = 1: calls with device-only outputs return after enqueueing. */
+blest_status blest_set_stream(blest_handle h, void *stream, int32_t async);
+
+/* Wait for the handle's stream and return the device status of the calls
+ * since the last sync. */
+blest_status blest_sync(blest_handle h);
+
+/* Release the handle and its device memory. */
+void blest_destroy(blest_handle h);
+
+const char *blest_status_string(blest_status s);
+
+/* Test hook for the timed-out grid barrier: launches a cooperative kernel in
+ * which one block waits on a barrier no other block joins.  Returns
+ * BLEST_ERR_TIMEOUT after about timeout_ms when the wait gives up as it
+ * should; the context stays usable. */
+blest_status blest_selftest_barrier_timeout(int32_t timeout_ms);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BLEST_H */

@@ -1,0 +1,276 @@
+"""Python binding of the GB300 BVSS BFS library (include/blest.h).
+
+Argument marshalling only: every step of the BFS path runs in the CUDA
+kernels of ``libblest.so``.  Arrays may be NumPy arrays (host) or torch
+tensors (host or CUDA); outputs are written in place.  Importing this module
+raises if the compiled library is missing -- build it first with
+``python -c "import __graft_entry__ as g; g.build()"`` (or
+``python paper_2606_05081_gb300/_build.py``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _build
+
+LIB_PATH = _build.LIB
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libblest.so is not built ({LIB_PATH}); run paper_2606_05081_gb300/_build.py")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+OK, ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_UNSUPPORTED, ERR_INTERNAL = range(7)
+REORDER_NONE, REORDER_RCM, REORDER_JACCARD, REORDER_AUTO = range(4)
+MODE_PUSH_EAGER_CC, MODE_PUSH_EAGER_TC, MODE_PUSH_LAZY_CC, MODE_PUSH_LAZY_TC, MODE_BOTTOM_UP = range(5)
+MODE_NAMES = ["push_eager_cc", "push_eager_tc", "push_lazy_cc", "push_lazy_tc", "bottom_up"]
+POLICY_HEURISTIC, POLICY_LEARNED, POLICY_FIXED, POLICY_SCHEDULE = range(4)
+MLP_NW = 12 + 32 * 6 + 32 + 32 * 32 + 32 + 5 * 32 + 5
+
+
+class BuildOpts(ctypes.Structure):
+    _fields_ = [("reorder", ctypes.c_int32), ("sigma", ctypes.c_int32), ("directed", ctypes.c_int32),
+                ("jaccard_window", ctypes.c_int32), ("probe_switch", ctypes.c_int32),
+                ("engine_tc", ctypes.c_int32), ("eta", ctypes.c_float), ("udiv_threshold", ctypes.c_double),
+                ("timeout_ms", ctypes.c_int32), ("block_threads", ctypes.c_int32)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("num_slice_sets", ctypes.c_int64),
+                ("num_vss", ctypes.c_int64), ("num_slices", ctypes.c_int64),
+                ("update_divergence", ctypes.c_double), ("lazy", ctypes.c_int32),
+                ("switching", ctypes.c_int32), ("reorder", ctypes.c_int32), ("sigma", ctypes.c_int32),
+                ("grid_blocks", ctypes.c_int32), ("block_threads", ctypes.c_int32),
+                ("build_ms", ctypes.c_double), ("device_bytes", ctypes.c_int64)]
+
+
+class LevelLog(ctypes.Structure):
+    _fields_ = [("level", ctypes.c_int32), ("mode", ctypes.c_int32), ("frontier", ctypes.c_int64),
+                ("frontier_edges", ctypes.c_int64), ("unvisited", ctypes.c_int64), ("queue", ctypes.c_int64),
+                ("t_ns", ctypes.c_int64)]
+
+
+_P = ctypes.c_void_p
+_H = ctypes.c_void_p
+_S = ctypes.c_int
+_sigs = {
+    "blest_default_opts": (None, [ctypes.POINTER(BuildOpts)]),
+    "blest_build": (_S, [ctypes.c_int64, _P, _P, ctypes.POINTER(BuildOpts), ctypes.POINTER(_H)]),
+    "blest_bfs": (_S, [_H, ctypes.c_int32, _P]),
+    "blest_msbfs": (_S, [_H, _P, ctypes.c_int32, _P]),
+    "blest_closeness": (_S, [_H, _P, _P, _P]),
+    "blest_build_many": (_S, [ctypes.c_int32, _P, _P, _P, _P, ctypes.POINTER(BuildOpts), ctypes.POINTER(_H)]),
+    "blest_bfs_many": (_S, [_H, _P, _P]),
+    "blest_set_policy": (_S, [_H, ctypes.c_int32, ctypes.c_int32]),
+    "blest_set_schedule": (_S, [_H, _P, ctypes.c_int32]),
+    "blest_load_model": (_S, [_H, _P, ctypes.c_int32]),
+    "blest_last_timings": (_S, [_H, _P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
+    "blest_get_info": (_S, [_H, ctypes.POINTER(Info)]),
+    "blest_get_bvss": (_S, [_H, _P, _P, _P, _P]),
+    "blest_get_perm": (_S, [_H, _P]),
+    "blest_set_stream": (_S, [_H, _P, ctypes.c_int32]),
+    "blest_sync": (_S, [_H]),
+    "blest_destroy": (None, [_H]),
+    "blest_status_string": (ctypes.c_char_p, [_S]),
+    "blest_selftest_barrier_timeout": (_S, [ctypes.c_int32]),
+    "blest_last_cuda_error": (ctypes.c_char_p, []),
+}
+for _name, (_res, _args) in _sigs.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+EXPORTED = sorted(k for k in _sigs if k != "blest_last_cuda_error")
+
+
+class BlestError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        msg = _lib.blest_status_string(code).decode()
+        extra = _lib.blest_last_cuda_error().decode() if code == ERR_CUDA else ""
+        super().__init__(f"{what}: {msg} ({code}) {extra}".strip())
+        self.code = code
+
+
+def _check(code: int, what: str):
+    if code != OK:
+        raise BlestError(code, what)
+
+
+def _ptr(a):
+    """Raw pointer of a NumPy array or torch tensor (host or device)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _dtype_ok(a, np_dtype, torch_name):
+    if hasattr(a, "data_ptr"):
+        if str(a.dtype) != f"torch.{torch_name}":
+            raise TypeError(f"expected torch.{torch_name}, got {a.dtype}")
+    elif np.asarray(a).dtype != np_dtype:
+        raise TypeError(f"expected {np_dtype}, got {np.asarray(a).dtype}")
+
+
+def default_opts(**kw) -> BuildOpts:
+    o = BuildOpts()
+    _lib.blest_default_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise TypeError(f"unknown option {k}")
+        setattr(o, k, v)
+    return o
+
+
+class Graph:
+    """A built graph (one blest handle)."""
+
+    def __init__(self, handle, n: int, many: bool = False):
+        self._h = handle
+        self.n = n
+        self.many = many
+
+    # ---------------------------------------------------------- lifetime
+    def close(self):
+        if self._h:
+            _lib.blest_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -------------------------------------------------------------- BFS
+    def bfs(self, source: int, out=None):
+        """Levels from one source (int32, -1 = unreached); out may be a host
+        array or a CUDA tensor of n int32."""
+        if out is None:
+            out = np.empty(self.n, np.int32)
+        _dtype_ok(out, np.int32, "int32")
+        _check(_lib.blest_bfs(self._h, int(source), _ptr(out)), "blest_bfs")
+        return out
+
+    def msbfs(self, sources, out=None):
+        src = np.ascontiguousarray(sources, dtype=np.int32) if not hasattr(sources, "data_ptr") else sources
+        k = len(src)
+        if out is None:
+            out = np.empty((k, self.n), np.int32)
+        _dtype_ok(out, np.int32, "int32")
+        _check(_lib.blest_msbfs(self._h, _ptr(src), k, _ptr(out)), "blest_msbfs")
+        return out
+
+    def closeness(self, far=None, cc=None, reach=None):
+        if far is None:
+            far = np.empty(self.n, np.int64)
+        if cc is None:
+            cc = np.empty(self.n, np.float64)
+        if reach is None:
+            reach = np.empty(self.n, np.int64)
+        _check(_lib.blest_closeness(self._h, _ptr(far), _ptr(cc), _ptr(reach)), "blest_closeness")
+        return far, cc, reach
+
+    def bfs_many(self, sources, out=None, total_n=None):
+        src = np.ascontiguousarray(sources, dtype=np.int32) if not hasattr(sources, "data_ptr") else sources
+        if out is None:
+            out = np.empty(int(total_n), np.int32)
+        _check(_lib.blest_bfs_many(self._h, _ptr(src), _ptr(out)), "blest_bfs_many")
+        return out
+
+    # ---------------------------------------------------------- control
+    def set_policy(self, policy: int, fixed_mode: int = 0):
+        _check(_lib.blest_set_policy(self._h, policy, fixed_mode), "blest_set_policy")
+
+    def set_schedule(self, modes):
+        m = np.ascontiguousarray(modes, dtype=np.int32)
+        _check(_lib.blest_set_schedule(self._h, m.ctypes.data, len(m)), "blest_set_schedule")
+
+    def load_model(self, weights):
+        w = np.ascontiguousarray(weights, dtype=np.float32)
+        _check(_lib.blest_load_model(self._h, w.ctypes.data, len(w)), "blest_load_model")
+
+    def set_stream(self, stream_ptr=None, async_: bool = False):
+        _check(_lib.blest_set_stream(self._h, stream_ptr, int(async_)), "blest_set_stream")
+
+    def sync(self):
+        _check(_lib.blest_sync(self._h), "blest_sync")
+
+    # ------------------------------------------------------ introspection
+    def info(self) -> dict:
+        i = Info()
+        _check(_lib.blest_get_info(self._h, ctypes.byref(i)), "blest_get_info")
+        return {f: getattr(i, f) for f, _ in Info._fields_}
+
+    def level_log(self):
+        n = ctypes.c_int64(0)
+        _check(_lib.blest_last_timings(self._h, None, 0, ctypes.byref(n)), "blest_last_timings")
+        buf = (LevelLog * max(1, n.value))()
+        _check(_lib.blest_last_timings(self._h, buf, n.value, ctypes.byref(n)), "blest_last_timings")
+        return [{f: getattr(buf[i], f) for f, _ in LevelLog._fields_} for i in range(n.value)]
+
+    def bvss(self) -> dict:
+        inf = self.info()
+        nv, ns = inf["num_vss"], inf["num_slice_sets"]
+        rows = np.empty(nv * 128, np.int32)
+        masks = np.empty(nv * 32, np.uint32)
+        real = np.empty(ns + 1, np.int32)
+        v2r = np.empty(nv, np.int32)
+        _check(_lib.blest_get_bvss(self._h, _ptr(rows), _ptr(masks), _ptr(real), _ptr(v2r)), "blest_get_bvss")
+        return dict(rowIds=rows, masks=masks, realPtrs=real, v2r=v2r, Nv=nv, Ns=ns)
+
+    def perm(self) -> np.ndarray:
+        p = np.empty(self.n, np.int32)
+        _check(_lib.blest_get_perm(self._h, _ptr(p)), "blest_get_perm")
+        return p
+
+
+def build(n: int, row_ptr, col_idx, **opts) -> Graph:
+    """Build a handle from a CSR graph (host or device arrays).
+    Options are the fields of blest_build_opts (reorder, directed, ...)."""
+    _dtype_ok(row_ptr, np.int64, "int64")
+    _dtype_ok(col_idx, np.int32, "int32")
+    o = default_opts(**opts)
+    h = _H()
+    rp = row_ptr if hasattr(row_ptr, "data_ptr") else np.ascontiguousarray(row_ptr)
+    ci = col_idx if hasattr(col_idx, "data_ptr") else np.ascontiguousarray(col_idx)
+    if hasattr(ci, "data_ptr") and ci.numel() == 0 or (isinstance(ci, np.ndarray) and ci.size == 0):
+        ci = np.zeros(1, np.int32)
+    _check(_lib.blest_build(int(n), _ptr(rp), _ptr(ci), ctypes.byref(o), ctypes.byref(h)), "blest_build")
+    return Graph(h, int(n))
+
+
+def build_graph(g, **opts) -> Graph:
+    """Build from a graphgen.Graph-like object (n, row_ptr, col, directed)."""
+    if getattr(g, "directed", False):
+        opts.setdefault("directed", 1)
+    return build(g.n, g.row_ptr, g.col, **opts)
+
+
+def build_many(batch, **opts) -> Graph:
+    o = default_opts(**opts)
+    h = _H()
+    _check(_lib.blest_build_many(int(batch.g), _ptr(batch.vtx_off), _ptr(batch.edge_off), _ptr(batch.row_ptr),
+                                 _ptr(batch.col), ctypes.byref(o), ctypes.byref(h)), "blest_build_many")
+    return Graph(h, int(batch.vtx_off[-1]), many=True)
+
+
+def selftest_barrier_timeout(timeout_ms: int = 20) -> int:
+    return int(_lib.blest_selftest_barrier_timeout(int(timeout_ms)))

@@ -1,0 +1,474 @@
+// Single-source BFS over BVSS: one persistent cooperative kernel runs every
+// level (§5.3 kernel fusion) and picks, per level, one of
+//   push eager  (Algorithm 2): visited check, atomic OR on the next frontier,
+//                the first setter of a slice-set byte enqueues its VSSs;
+//   push lazy   (Algorithm 3 stage 1): fire-and-forget OR into V_next, then
+//                stage 2 sweeps V_curr xor V_next, sets levels and enqueues;
+//   bottom-up   (Algorithm 4 stage 1): each unvisited vertex scans its
+//                in-neighbours for a frontier vertex, then stage 2;
+// the per-VSS hit test (Eq. 2) runs either on tensor cores with the
+// m8n8k128 b1 AND.POPC layout of Fig. 3 or on CUDA cores (AND + byte test).
+//
+// State between levels is the same whatever mode ran (levels L, visited
+// bits V_curr = V_next, exact frontier bits F, VSS queue Q, slice-set queue
+// SQ), so modes mix freely.  F, Q and SQ rotate over three buffers and the
+// per-level counters over four slots; the buffer of level l-2 is cleared
+// sparsely (only the slice-set bytes it holds) while level l runs, so a
+// top-down eager level needs a single grid barrier and no O(n) clearing.
+#include <cstdio>
+#include <cstring>
+
+#include "handle.h"
+#include "mlp.h"
+
+namespace {
+
+constexpr int BFS_MIN_BLOCKS = 2;
+
+struct BfsParams {
+    int n, W;
+    const int4 *__restrict__ rowIds;
+    const unsigned *__restrict__ masks;
+    const int *__restrict__ realPtrs;
+    const int *__restrict__ v2r;
+    const long long *__restrict__ rp;
+    const int *__restrict__ col;
+    const int *__restrict__ deg;
+    int *L;
+    unsigned *Vc, *Vn;
+    unsigned *F[3];
+    int *Q[3];
+    int *SQ[3];
+    Ctl *ctl;
+    blest_level_log *log;
+    int log_cap;
+    int src;
+    int policy, fixed_mode, lazy, tc, switching;
+    float eta;
+    const int *schedule;
+    int sched_len;
+    const float *mlp;
+    float avg_deg;
+    unsigned long long budget_ns;
+    const int *new_of_old;  // non-null: out[v] = L[new_of_old[v]]
+    int *out;
+};
+
+__device__ __forceinline__ unsigned hits_cc(unsigned m, unsigned alpha) {
+    const unsigned x = m & (alpha * 0x01010101u);
+    return (unsigned)((x & 0xFFu) != 0) | ((unsigned)((x & 0xFF00u) != 0) << 1) |
+           ((unsigned)((x & 0xFF0000u) != 0) << 2) | ((unsigned)((x >> 24) != 0) << 3);
+}
+
+// Fig. 3 layout: fragA = two packed sigma-bit masks in the low 16 bits;
+// fragB = alpha on lanes t mod 9 == 0, alpha << 8 on lanes t mod 9 == 4,
+// zero elsewhere.  Lane t's fragC pair is popc(mask_c & alpha) for its own
+// two slices, so no shuffle is needed.  bsel = 1, 256 or 0 by lane.
+__device__ __forceinline__ unsigned hits_tc(unsigned m, unsigned alpha, unsigned bsel) {
+    const unsigned fb = alpha * bsel;
+    int d0, d1, d2, d3;
+    asm volatile(
+        "mma.sync.aligned.m8n8k128.row.col.s32.b1.b1.s32.and.popc {%0,%1}, {%2}, {%3}, {%4,%5};\n"
+        : "=r"(d0), "=r"(d1)
+        : "r"(m & 0xFFFFu), "r"(fb), "r"(0), "r"(0));
+    asm volatile(
+        "mma.sync.aligned.m8n8k128.row.col.s32.b1.b1.s32.and.popc {%0,%1}, {%2}, {%3}, {%4,%5};\n"
+        : "=r"(d2), "=r"(d3)
+        : "r"(m >> 16), "r"(fb), "r"(0), "r"(0));
+    return (unsigned)(d0 != 0) | ((unsigned)(d1 != 0) << 1) | ((unsigned)(d2 != 0) << 2) |
+           ((unsigned)(d3 != 0) << 3);
+}
+
+__device__ __forceinline__ int pick(const int4 &r, int c) {
+    return c == 0 ? r.x : (c == 1 ? r.y : (c == 2 ? r.z : r.w));
+}
+
+// Warp-aggregated enqueue of up to 4 slice sets per lane (bit c of `want`
+// set => slice set ss[c]): their VSS ranges go to Q, the set ids to SQ.
+__device__ __forceinline__ void enqueue_sets(const BfsParams &P, unsigned want, const int ss[4], int *Q, int *SQ,
+                                             int slot) {
+    const int lane = lane_id();
+    if (!__any_sync(FULL_MASK, want != 0)) return;
+    int a[4], len[4];
+    int tot = 0, nset = 0;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        a[c] = 0;
+        len[c] = 0;
+        if (want >> c & 1u) {
+            a[c] = __ldg(&P.realPtrs[ss[c]]);
+            len[c] = __ldg(&P.realPtrs[ss[c] + 1]) - a[c];
+            tot += len[c];
+            ++nset;
+        }
+    }
+    const int incl = warp_incl_scan(tot);
+    const int sincl = warp_incl_scan(nset);
+    int qbase = 0, sbase = 0;
+    if (lane == 31) {
+        qbase = incl ? atomicAdd(&P.ctl->qlen[slot], incl) : 0;
+        sbase = atomicAdd(&P.ctl->sqlen[slot], sincl);
+    }
+    qbase = __shfl_sync(FULL_MASK, qbase, 31) + incl - tot;
+    sbase = __shfl_sync(FULL_MASK, sbase, 31) + sincl - nset;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        if (want >> c & 1u) {
+            SQ[sbase++] = ss[c];
+            for (int k = 0; k < len[c]; ++k) Q[qbase + k] = a[c] + k;
+            qbase += len[c];
+        }
+    }
+}
+
+__device__ __forceinline__ void flush_counts(const BfsParams &P, int slot, unsigned long long nv,
+                                             unsigned long long fe) {
+    nv = warp_sum(nv);
+    fe = warp_sum(fe);
+    if (lane_id() == 0 && nv) {
+        red_add_u64(&P.ctl->newv[slot], nv);
+        red_add_u64(&P.ctl->fedges[slot], fe);
+    }
+}
+
+// ---------------------------------------------------------------- push
+template <bool EAGER, bool TC>
+__device__ void push_level(const BfsParams &P, int ell, int bc, int bn, int slot, int qlen, unsigned bsel) {
+    const int lane = lane_id();
+    const int gwarp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
+    const unsigned *Fc = P.F[bc];
+    unsigned *Fn = P.F[bn];
+    const int *Qc = P.Q[bc];
+    unsigned long long nv = 0, fe = 0;
+    for (int w = gwarp; w < qlen; w += nwarps) {
+        const int vss = Qc[w];
+        const int ss = __ldg(&P.v2r[vss]);
+        const int4 r = __ldg(&P.rowIds[(size_t)vss * 32 + lane]);
+        const unsigned m = __ldg(&P.masks[(size_t)vss * 32 + lane]);
+        const unsigned alpha = ld_byte(Fc, ss);
+        const unsigned hits = TC ? hits_tc(m, alpha, bsel) : hits_cc(m, alpha);
+        if (EAGER) {
+            unsigned want = 0;
+            int sso[4] = {0, 0, 0, 0};
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                if (hits >> c & 1u) {
+                    const int u = pick(r, c);
+                    const unsigned bit = 1u << (u & 31);
+                    const int wd = u >> 5;
+                    if (!(P.Vc[wd] & bit)) {
+                        const unsigned old = atomicOr(&Fn[wd], bit);
+                        if (!(old & bit)) {
+                            P.L[u] = ell;
+                            red_or(&P.Vc[wd], bit);
+                            red_or(&P.Vn[wd], bit);
+                            nv += 1;
+                            fe += (unsigned long long)__ldg(&P.deg[u]);
+                            if (((old >> (u & 24)) & 0xFFu) == 0) {
+                                want |= 1u << c;
+                                sso[c] = u >> 3;
+                            }
+                        }
+                    }
+                }
+            }
+            enqueue_sets(P, want, sso, P.Q[bn], P.SQ[bn], slot);
+        } else {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                if (hits >> c & 1u) {
+                    const int u = pick(r, c);
+                    red_or(&P.Vn[u >> 5], 1u << (u & 31));
+                }
+            }
+        }
+    }
+    if (EAGER) flush_counts(P, slot, nv, fe);
+}
+
+// ------------------------------------------------------------ bottom-up
+__device__ void bottom_up_level(const BfsParams &P, int bc) {
+    const int lane = lane_id();
+    const int gwarp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
+    const unsigned *Fc = P.F[bc];
+    const int tail = P.n & 31;
+    for (int w = gwarp; w < P.W; w += nwarps) {
+        const unsigned vis = P.Vc[w];
+        unsigned unv = ~vis;
+        if (w == P.W - 1 && tail) unv &= (1u << tail) - 1u;
+        if (unv == 0) continue;
+        bool found = false;
+        if (unv >> lane & 1u) {
+            const int u = (w << 5) + lane;
+            const long long e = __ldg(&P.rp[u + 1]);
+            for (long long p = __ldg(&P.rp[u]); p < e; ++p) {
+                const int v = __ldg(&P.col[p]);
+                if (Fc[v >> 5] >> (v & 31) & 1u) { found = true; break; }
+            }
+        }
+        const unsigned bal = __ballot_sync(FULL_MASK, found);
+        if (lane == 0 && bal) P.Vn[w] = vis | bal;  // this warp owns word w in this phase
+    }
+}
+
+// --------------------------------------------------- stage 2 (finalize)
+__device__ void finalize_level(const BfsParams &P, int ell, int bn, int slot) {
+    const int lane = lane_id();
+    const int gwarp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
+    unsigned *Fn = P.F[bn];
+    unsigned long long nv = 0, fe = 0;
+    for (int base = gwarp * 32; base < P.W; base += nwarps * 32) {
+        const int t = base + lane;
+        unsigned diff = 0;
+        if (t < P.W) {
+            const unsigned next = P.Vn[t];
+            const unsigned cur = P.Vc[t];
+            diff = next ^ cur;
+            if (diff) {
+                P.Vc[t] = next;
+                Fn[t] = diff;
+                unsigned d = diff;
+                while (d) {
+                    const int b = __ffs(d) - 1;
+                    d &= d - 1;
+                    const int u = (t << 5) + b;
+                    P.L[u] = ell;
+                    fe += (unsigned long long)__ldg(&P.deg[u]);
+                }
+                nv += (unsigned long long)__popc(diff);
+            }
+        }
+        unsigned want = 0;
+        int sso[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            sso[c] = t * 4 + c;
+            if ((diff >> (8 * c)) & 0xFFu) want |= 1u << c;
+        }
+        enqueue_sets(P, want, sso, P.Q[bn], P.SQ[bn], slot);
+    }
+    flush_counts(P, slot, nv, fe);
+}
+
+// -------------------------------------------------------- mode decision
+// Called by a full warp; all lanes return the same mode.  Every block
+// evaluates it on the same inputs, so every block picks the same mode.
+__device__ __forceinline__ int decide_mode(const BfsParams &P, int ell, long long frontier, long long fedges,
+                                           long long unvisited, int qlen) {
+    int mode;
+    if (P.policy == BLEST_POLICY_FIXED) {
+        mode = P.fixed_mode;
+    } else if (P.policy == BLEST_POLICY_SCHEDULE && P.sched_len > 0) {
+        mode = P.schedule[(ell - 1) % P.sched_len];
+    } else if (P.policy == BLEST_POLICY_LEARNED && P.mlp) {
+        mode = mlp_choose_warp(P.mlp, frontier, fedges, unvisited, qlen, ell, P.avg_deg);
+    } else {
+        // §5.2/§7.1: lazy updates when U_div exceeds the threshold; Eq. 5
+        // switches to bottom-up when #unvisited < eta * |Q_curr|.
+        mode = P.lazy ? (P.tc ? BLEST_MODE_PUSH_LAZY_TC : BLEST_MODE_PUSH_LAZY_CC)
+                      : (P.tc ? BLEST_MODE_PUSH_EAGER_TC : BLEST_MODE_PUSH_EAGER_CC);
+        if (P.switching && (double)unvisited < (double)P.eta * (double)qlen) mode = BLEST_MODE_BOTTOM_UP;
+    }
+    if (mode < 0 || mode >= BLEST_NUM_MODES) mode = BLEST_MODE_PUSH_EAGER_CC;
+    return mode;
+}
+
+__global__ void __launch_bounds__(512, BFS_MIN_BLOCKS) k_bfs(BfsParams P) {
+    const int tid = (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    const int nthreads = (int)(gridDim.x * blockDim.x);
+    const int lane = lane_id();
+    const unsigned bsel = (lane % 9 == 0) ? 1u : ((lane % 9 == 4) ? 256u : 0u);
+    Ctl *ctl = P.ctl;
+    unsigned epoch = 0;
+    __shared__ int s_mode;
+
+    // ---- level 0 (Algorithm 2/3 init): L = inf except the source, frontier
+    // and visited bits hold the source, Q = VSSs of the source's slice set.
+    const int src = P.new_of_old ? __ldg(&P.new_of_old[P.src]) : P.src;
+    for (int i = tid; i < P.n; i += nthreads) P.L[i] = (i == src) ? 0 : -1;
+    for (int w = tid; w < P.W; w += nthreads) {
+        const unsigned b = (w == (src >> 5)) ? (1u << (src & 31)) : 0u;
+        P.Vc[w] = b;
+        P.Vn[w] = b;
+        P.F[0][w] = b;
+        P.F[1][w] = 0u;
+        P.F[2][w] = 0u;
+    }
+    {
+        const int ss = src >> 3;
+        const int a = __ldg(&P.realPtrs[ss]), e = __ldg(&P.realPtrs[ss + 1]);
+        for (int k = tid; k < e - a; k += nthreads) P.Q[0][k] = a + k;
+        if (tid == 0) {
+            P.SQ[0][0] = ss;
+            ctl->qlen[0] = e - a;
+            ctl->sqlen[0] = 1;
+            ctl->newv[0] = 1;
+            ctl->fedges[0] = (unsigned long long)__ldg(&P.deg[src]);
+        }
+    }
+    if (!grid_barrier(ctl, epoch, P.budget_ns)) return;
+
+    long long visited = 0;
+    int ell = 1;
+    for (;; ++ell) {
+        const int bc = (ell - 1) % 3, bn = ell % 3, bo = (ell + 1) % 3;
+        const int sc = (ell - 1) & 3, sn = ell & 3, so = (ell + 2) & 3, sz = (ell + 1) & 3;
+        const int qlen = ld_volatile_i32(&ctl->qlen[sc]);
+        const long long frontier = (long long)*(volatile unsigned long long *)&ctl->newv[sc];
+        const long long fedges = (long long)*(volatile unsigned long long *)&ctl->fedges[sc];
+        visited += frontier;
+        const long long unvisited = (long long)P.n - visited;
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            const long long t = (long long)global_ns();
+            if (ell >= 2 && ell - 2 < P.log_cap) P.log[ell - 2].t_ns = t - P.log[ell - 2].t_ns;
+            if (qlen > 0 && ell - 1 < P.log_cap) {
+                blest_level_log rec;
+                rec.level = ell;
+                rec.mode = -1;
+                rec.frontier = frontier;
+                rec.frontier_edges = fedges;
+                rec.unvisited = unvisited;
+                rec.queue = qlen;
+                rec.t_ns = t;
+                P.log[ell - 1] = rec;
+            }
+        }
+        if (qlen == 0) break;
+        if (threadIdx.x < 32) {
+            const int m = decide_mode(P, ell, frontier, fedges, unvisited, qlen);
+            if (threadIdx.x == 0) s_mode = m;
+        }
+        __syncthreads();
+        const int mode = s_mode;
+        if (blockIdx.x == 0 && threadIdx.x == 0 && ell - 1 < P.log_cap) P.log[ell - 1].mode = mode;
+
+        // housekeeping for the buffers of level ell-2 and the counters of ell+1
+        if (ell >= 2) {
+            const int sql = ld_volatile_i32(&ctl->sqlen[so]);
+            unsigned char *Fo = reinterpret_cast<unsigned char *>(P.F[bo]);
+            const int *SQo = P.SQ[bo];
+            for (int k = tid; k < sql; k += nthreads) Fo[SQo[k]] = 0;
+        }
+        if (tid == 0) {
+            ctl->qlen[sz] = 0;
+            ctl->sqlen[sz] = 0;
+            ctl->newv[sz] = 0;
+            ctl->fedges[sz] = 0;
+        }
+
+        if (mode == BLEST_MODE_PUSH_EAGER_CC || mode == BLEST_MODE_PUSH_EAGER_TC) {
+            if (mode == BLEST_MODE_PUSH_EAGER_TC)
+                push_level<true, true>(P, ell, bc, bn, sn, qlen, bsel);
+            else
+                push_level<true, false>(P, ell, bc, bn, sn, qlen, bsel);
+            if (!grid_barrier(ctl, epoch, P.budget_ns)) return;
+        } else {
+            if (mode == BLEST_MODE_PUSH_LAZY_TC)
+                push_level<false, true>(P, ell, bc, bn, sn, qlen, bsel);
+            else if (mode == BLEST_MODE_PUSH_LAZY_CC)
+                push_level<false, false>(P, ell, bc, bn, sn, qlen, bsel);
+            else
+                bottom_up_level(P, bc);
+            if (!grid_barrier(ctl, epoch, P.budget_ns)) return;
+            finalize_level(P, ell, bn, sn);
+            if (!grid_barrier(ctl, epoch, P.budget_ns)) return;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctl->nlevels = ell - 1;
+    // undo the reordering: out[v] = L[new_of_old[v]]
+    if (P.new_of_old)
+        for (int v = tid; v < P.n; v += nthreads) P.out[v] = P.L[__ldg(&P.new_of_old[v])];
+}
+
+}  // namespace
+
+int bfs_grid_for(int block, int *num_sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bfs, block, 0);
+    if (num_sms) *num_sms = sms;
+    return per_sm * sms;
+}
+
+blest_status bfs_prepare(blest_graph *h) {
+    const int64_t n = h->n;
+    const int64_t W = (n + 31) / 32;
+    blest_status bs;
+    if ((bs = dev_alloc_t(h, &h->w.L, (size_t)n)) != BLEST_OK) return bs;
+    if ((bs = dev_alloc_t(h, &h->w.Vc, (size_t)W + 1)) != BLEST_OK) return bs;
+    if ((bs = dev_alloc_t(h, &h->w.Vn, (size_t)W + 1)) != BLEST_OK) return bs;
+    for (int i = 0; i < 3; ++i) {
+        if ((bs = dev_alloc_t(h, &h->w.F[i], (size_t)W + 1)) != BLEST_OK) return bs;
+        if ((bs = dev_alloc_t(h, &h->w.Q[i], (size_t)(h->Nv > 0 ? h->Nv : 1))) != BLEST_OK) return bs;
+        if ((bs = dev_alloc_t(h, &h->w.SQ[i], (size_t)h->Ns + 1)) != BLEST_OK) return bs;
+    }
+    if ((bs = dev_alloc_t(h, &h->w.ctl, 1)) != BLEST_OK) return bs;
+    h->w.log_cap = 1 << 16;
+    if ((bs = dev_alloc_t(h, &h->w.log, (size_t)h->w.log_cap)) != BLEST_OK) return bs;
+    if (h->g.new_of_old)
+        if ((bs = dev_alloc_t(h, &h->w.out_tmp, (size_t)n)) != BLEST_OK) return bs;
+    int sms = 0;
+    h->grid = bfs_grid_for(h->block, &sms);
+    h->num_sms = sms;
+    if (h->grid <= 0) return BLEST_ERR_CUDA;
+    return BLEST_OK;
+}
+
+// Enqueue one BFS on h->stream; levels (original ids) land in dev_out.
+blest_status bfs_run(blest_graph *h, int32_t source, int32_t *dev_out) {
+    BfsParams P;
+    memset(&P, 0, sizeof P);
+    P.n = (int)h->n;
+    P.W = (int)((h->n + 31) / 32);
+    P.rowIds = h->g.rowIds;
+    P.masks = h->g.masks;
+    P.realPtrs = h->g.realPtrs;
+    P.v2r = h->g.v2r;
+    P.rp = h->g.rp;
+    P.col = h->g.col;
+    P.deg = h->g.deg;
+    P.Vc = h->w.Vc;
+    P.Vn = h->w.Vn;
+    for (int i = 0; i < 3; ++i) {
+        P.F[i] = h->w.F[i];
+        P.Q[i] = h->w.Q[i];
+        P.SQ[i] = h->w.SQ[i];
+    }
+    P.ctl = h->w.ctl;
+    P.log = h->w.log;
+    P.log_cap = h->w.log_cap;
+    P.policy = h->policy;
+    P.fixed_mode = h->fixed_mode;
+    P.lazy = h->lazy;
+    P.tc = h->engine_tc;
+    P.switching = h->switching;
+    P.eta = h->eta;
+    P.schedule = h->d_schedule;
+    P.sched_len = h->sched_len;
+    P.mlp = h->d_mlp;
+    P.avg_deg = h->n ? (float)((double)h->nnz / (double)h->n) : 0.f;
+    P.budget_ns = (unsigned long long)h->timeout_ms * 1000000ull;
+    P.src = source;
+    if (h->g.new_of_old) {
+        P.L = h->w.out_tmp;
+        P.new_of_old = h->g.new_of_old;
+        P.out = dev_out;
+    } else {
+        P.L = dev_out;
+    }
+    cudaError_t e = cudaMemsetAsync(h->w.ctl, 0, sizeof(Ctl), h->stream);
+    if (e != cudaSuccess) return BLEST_ERR_CUDA;
+    void *args[] = {&P};
+    e = cudaLaunchCooperativeKernel((const void *)k_bfs, dim3(h->grid), dim3(h->block), args, 0, h->stream);
+    if (e != cudaSuccess) {
+        blest_internal_record_cuda_error(e, "cudaLaunchCooperativeKernel(k_bfs)", __FILE__, __LINE__);
+        return BLEST_ERR_CUDA;
+    }
+    return BLEST_OK;
+}

@@ -1,0 +1,106 @@
+// Host-side state of a blest handle (shared by the translation units of the
+// library; not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/blest.h"
+#include "common.cuh"
+
+struct DevGraph {
+    // BVSS (§3.1), sigma = 8: rowIds int4[N_v*32], masks u32[N_v*32]
+    int4 *rowIds = nullptr;
+    unsigned *masks = nullptr;
+    int *realPtrs = nullptr;   // N_s + 1
+    int *v2r = nullptr;        // N_v
+    // in-neighbour CSR of the reordered graph (bottom-up, Algorithm 4)
+    long long *rp = nullptr;   // n + 1
+    int *col = nullptr;
+    int *deg = nullptr;        // out-degree in the reordered id space (features, TEPS)
+    // permutation (nullptr when no reordering): new_of_old, old_of_new
+    int *new_of_old = nullptr;
+    int *old_of_new = nullptr;
+};
+
+struct BfsWork {
+    int *L = nullptr;                 // n (reordered ids)
+    unsigned *Vc = nullptr, *Vn = nullptr;
+    unsigned *F[3] = {nullptr, nullptr, nullptr};
+    int *Q[3] = {nullptr, nullptr, nullptr};
+    int *SQ[3] = {nullptr, nullptr, nullptr};
+    Ctl *ctl = nullptr;
+    blest_level_log *log = nullptr;
+    int log_cap = 0;
+    int *out_tmp = nullptr;           // n, levels in reordered ids (when reordered)
+    int32_t *stage = nullptr;         // device staging for host outputs
+    size_t stage_count = 0;
+};
+
+struct MsbfsWork;  // defined in msbfs.cu
+struct ManyGraphs; // defined in many.cu
+
+struct blest_graph {
+    int64_t n = 0, nnz = 0;
+    int64_t Ns = 0, Nv = 0, num_slices = 0;
+    int sigma = 8;
+    int directed = 0;
+    int reorder = 0;
+    double udiv = 0.0;
+    int lazy = 0, switching = 0;
+    int engine_tc = 1;
+    float eta = 10.f;
+    double udiv_threshold = 25000.0;
+    int timeout_ms = 5000;
+    double build_ms = 0.0;
+    int64_t device_bytes = 0;
+
+    DevGraph g;
+    BfsWork w;
+
+    // launch geometry of the persistent kernels
+    int block = 512;
+    int grid = 0;
+    int num_sms = 0;
+    int device = 0;
+
+    // policy
+    int policy = BLEST_POLICY_HEURISTIC;
+    int fixed_mode = BLEST_MODE_PUSH_EAGER_TC;
+    int *d_schedule = nullptr;
+    int sched_len = 0;
+    float *d_mlp = nullptr;
+    int mlp_len = 0;
+
+    // streams and status
+    cudaStream_t own_stream = nullptr;
+    cudaStream_t stream = nullptr;
+    int async = 0;
+    Ctl *h_ctl = nullptr;             // pinned copy of the control block
+    int last_levels = 0;
+
+    MsbfsWork *ms = nullptr;
+    ManyGraphs *many = nullptr;
+
+    std::vector<void *> allocations;  // every device allocation, freed at destroy
+};
+
+// allocation helper: records the pointer in the handle
+blest_status dev_alloc(blest_graph *h, void **p, size_t bytes);
+template <typename T>
+static inline blest_status dev_alloc_t(blest_graph *h, T **p, size_t count) {
+    return dev_alloc(h, (void **)p, count * sizeof(T) + 16);
+}
+
+// is this pointer device-accessible memory?
+bool is_device_ptr(const void *p);
+
+// build helpers (build.cu)
+blest_status build_graph(blest_graph *h, const int64_t *row_ptr, const int32_t *col_idx,
+                         const blest_build_opts *o);
+
+// BFS (bfs.cu)
+blest_status bfs_prepare(blest_graph *h);
+blest_status bfs_run(blest_graph *h, int32_t source, int32_t *levels_dev_out);
+int bfs_grid_for(int block, int *num_sms);

@@ -1,0 +1,73 @@
+// Learned per-level kernel choice: a 3-layer MLP (6 -> 32 -> 32 -> 5, tanh
+// hidden units, fp32) that predicts the log device time of each level mode;
+// the level runs the mode with the smallest prediction.  The same weights
+// are trained on the device by mlp.cu.
+//
+// Weight vector layout (fp32, MLP_NW values):
+//   [0, 6)        feature means          [6, 12)      feature 1/std
+//   W1 [32][6]    b1 [32]                W2 [32][32]  b2 [32]
+//   W3 [5][32]    b3 [5]
+// Features, in order: log1p(frontier vertices), log1p(frontier out-arcs),
+// log1p(unvisited vertices), log1p(active BVSS slices = 128 * |Q|),
+// log1p(level index), log1p(average degree).
+#pragma once
+#include <cuda_runtime.h>
+
+#define MLP_IN 6
+#define MLP_H 32
+#define MLP_OUT 5
+#define MLP_OFF_MEAN 0
+#define MLP_OFF_ISTD 6
+#define MLP_OFF_W1 12
+#define MLP_OFF_B1 (MLP_OFF_W1 + MLP_H * MLP_IN)
+#define MLP_OFF_W2 (MLP_OFF_B1 + MLP_H)
+#define MLP_OFF_B2 (MLP_OFF_W2 + MLP_H * MLP_H)
+#define MLP_OFF_W3 (MLP_OFF_B2 + MLP_H)
+#define MLP_OFF_B3 (MLP_OFF_W3 + MLP_OUT * MLP_H)
+#define MLP_NW (MLP_OFF_B3 + MLP_OUT)
+
+__host__ __device__ inline void mlp_raw_features(float *x, long long frontier, long long fedges,
+                                                 long long unvisited, long long qlen, int level,
+                                                 float avg_deg) {
+    x[0] = log1pf((float)frontier);
+    x[1] = log1pf((float)fedges);
+    x[2] = log1pf((float)(unvisited > 0 ? unvisited : 0));
+    x[3] = log1pf(128.f * (float)qlen);
+    x[4] = log1pf((float)level);
+    x[5] = log1pf(avg_deg);
+}
+
+// Called by all 32 lanes of one warp; every lane returns the chosen mode.
+// Lane h owns hidden unit h of both layers.
+__device__ __forceinline__ int mlp_choose_warp(const float *__restrict__ w, long long frontier, long long fedges,
+                                               long long unvisited, long long qlen, int level, float avg_deg) {
+    const int lane = threadIdx.x & 31;
+    float x[MLP_IN];
+    mlp_raw_features(x, frontier, fedges, unvisited, qlen, level, avg_deg);
+#pragma unroll
+    for (int i = 0; i < MLP_IN; ++i) x[i] = (x[i] - w[MLP_OFF_MEAN + i]) * w[MLP_OFF_ISTD + i];
+    float a1 = w[MLP_OFF_B1 + lane];
+#pragma unroll
+    for (int i = 0; i < MLP_IN; ++i) a1 = fmaf(w[MLP_OFF_W1 + lane * MLP_IN + i], x[i], a1);
+    const float h1 = tanhf(a1);
+    float a2 = w[MLP_OFF_B2 + lane];
+#pragma unroll
+    for (int k = 0; k < MLP_H; ++k) a2 = fmaf(w[MLP_OFF_W2 + lane * MLP_H + k], __shfl_sync(0xFFFFFFFFu, h1, k), a2);
+    const float h2 = tanhf(a2);
+    float y = 0.f;
+    if (lane < MLP_OUT) y = w[MLP_OFF_B3 + lane];
+#pragma unroll
+    for (int k = 0; k < MLP_H; ++k) {
+        const float hk = __shfl_sync(0xFFFFFFFFu, h2, k);
+        if (lane < MLP_OUT) y = fmaf(w[MLP_OFF_W3 + lane * MLP_H + k], hk, y);
+    }
+    // argmin over the MLP_OUT predictions (lowest index on ties)
+    float best = __shfl_sync(0xFFFFFFFFu, y, 0);
+    int arg = 0;
+#pragma unroll
+    for (int o = 1; o < MLP_OUT; ++o) {
+        const float v = __shfl_sync(0xFFFFFFFFu, y, o);
+        if (v < best) { best = v; arg = o; }
+    }
+    return arg;
+}

@@ -1,0 +1,62 @@
+"""CPU-only checks of the C ABI boundary: the library builds, loads and
+exports every entry point that include/blest.h declares."""
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "blest.h")
+
+
+def _declared():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(blest_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for must in ["blest_build", "blest_bfs", "blest_msbfs", "blest_closeness", "blest_build_many",
+                 "blest_bfs_many", "blest_load_model", "blest_last_timings", "blest_status_string",
+                 "blest_destroy"]:
+        assert must in names
+
+
+def test_library_builds_and_exports_every_symbol():
+    from paper_2606_05081_gb300 import _build
+    lib = _build.build()
+    out = subprocess.run(["nm", "-D", "--defined-only", lib], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (blest_[a-z_0-9]+)", out))
+    missing = [n for n in _declared() if n not in exported]
+    assert not missing, f"declared but not exported: {missing}"
+
+
+def test_binding_loads_and_matches_header():
+    import paper_2606_05081_gb300 as blest
+    assert set(blest.EXPORTED) >= set(_declared())
+    assert blest._lib.blest_status_string(blest.OK) == b"ok"
+    assert blest._lib.blest_status_string(blest.ERR_TIMEOUT) == b"device wait timed out"
+    o = blest.default_opts()
+    assert o.sigma == 8 and abs(o.eta - 10.0) < 1e-6 and o.udiv_threshold == 25000.0
+    assert o.jaccard_window == 65536 and o.probe_switch == 1
+
+
+def test_binding_rejects_bad_dtypes():
+    import numpy as np
+
+    import paper_2606_05081_gb300 as blest
+    with pytest.raises(TypeError):
+        blest.build(3, np.array([0, 1, 2, 2], np.int32), np.array([1, 0], np.int32))
+
+
+def test_no_product_module_imports_oracle():
+    """The library path never routes through the CPU oracle."""
+    pkg = os.path.join(ROOT, "paper_2606_05081_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                src = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in src and "from oracle" not in src, f
+                assert "bfs_oracle" not in src, f

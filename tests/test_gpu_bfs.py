@@ -1,0 +1,193 @@
+"""GPU parity of the single-source BFS path against the CPU oracle.
+
+Every comparison is element by element and bit-exact: BFS levels, BVSS
+arrays and per-level frontier counts are integers.  U_div is a float
+statistic compared at 1e-12 relative (fp64 on both sides, different
+summation order).
+"""
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def blest():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2606_05081_gb300 as b
+    return b
+
+
+def _graphs():
+    return {
+        "rmat12": lambda: gg.rmat(12, seed=1),
+        "rmat10_ef4": lambda: gg.rmat(10, edge_factor=4, seed=7),
+        "grid_ragged": lambda: gg.grid(37, 53, seed=3),
+        "ba": lambda: gg.ba(3001, 3, seed=4),
+        "rgg": lambda: gg.rgg(4099, 8, seed=5),
+        "er_directed": lambda: gg.er(2501, 9000, seed=6, directed=True),
+        "star": lambda: gg.star(1500),
+        "path": lambda: gg.path(1003),
+        "union": lambda: gg.disjoint_union(gg.rmat(9, seed=2), gg.path(17), gg.from_edges(5, [], [], True)),
+    }
+
+
+GRAPHS = _graphs()
+
+
+@pytest.fixture(scope="module", params=sorted(GRAPHS))
+def case(request, blest):
+    g = GRAPHS[request.param]()
+    h = blest.build_graph(g)
+    yield request.param, g, h
+    h.close()
+
+
+def test_bvss_matches_oracle(case):
+    name, g, h = case
+    ref = oracle.bvss(g, 8)
+    got = h.bvss()
+    assert got["Nv"] == ref["Nv"] and got["Ns"] == ref["Ns"]
+    assert np.array_equal(got["realPtrs"], ref["realPtrs"])
+    assert np.array_equal(got["v2r"], ref["v2r"])
+    assert np.array_equal(got["rowIds"], ref["rowIds"])
+    assert np.array_equal(got["masks"], ref["masks"])
+    info = h.info()
+    assert info["nnz"] == g.nnz and info["num_slices"] == ref["num_slices"]
+    u = oracle.update_divergence(ref)
+    assert abs(info["update_divergence"] - u) <= 1e-12 * max(1.0, abs(u))
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2, 3, 4])
+def test_fixed_mode_levels(case, blest, mode):
+    name, g, h = case
+    h.set_policy(blest.POLICY_FIXED, mode)
+    try:
+        srcs = gg.sources(g, 6, 17)
+        for s in srcs:
+            assert np.array_equal(h.bfs(int(s)), oracle.bfs(g, int(s))), (name, mode, s)
+    finally:
+        h.set_policy(blest.POLICY_HEURISTIC)
+
+
+def test_heuristic_and_random_schedules(case, blest):
+    name, g, h = case
+    srcs = gg.sources(g, 4, 23)
+    refs = [oracle.bfs(g, int(s)) for s in srcs]
+    for s, r in zip(srcs, refs):
+        assert np.array_equal(h.bfs(int(s)), r)
+    rs = np.random.RandomState(5)
+    for trial in range(4):
+        h.set_schedule(rs.randint(0, 5, size=rs.randint(1, 9)))
+        h.set_policy(blest.POLICY_SCHEDULE)
+        for s, r in zip(srcs, refs):
+            assert np.array_equal(h.bfs(int(s)), r), (name, trial, s)
+    h.set_policy(blest.POLICY_HEURISTIC)
+
+
+def test_device_output_and_level_log(case, blest):
+    name, g, h = case
+    s = int(gg.sources(g, 1, 31)[0])
+    out = torch.full((g.n,), 7, dtype=torch.int32, device="cuda")
+    h.bfs(s, out)
+    ref = oracle.bfs(g, s)
+    assert np.array_equal(out.cpu().numpy(), ref)
+    log = h.level_log()
+    depth = int(ref.max())
+    assert len(log) == depth
+    counts = np.bincount(ref[ref >= 0])
+    deg = np.diff(g.row_ptr)
+    b = oracle.bvss(g, 8)
+    per_set = np.diff(b["realPtrs"])
+    visited = 0
+    for k, rec in enumerate(log):
+        assert rec["level"] == k + 1
+        frontier = np.flatnonzero(ref == k)
+        assert rec["frontier"] == counts[k]
+        assert rec["frontier_edges"] == int(deg[frontier].sum())
+        visited += counts[k]
+        assert rec["unvisited"] == g.n - visited
+        assert rec["queue"] == int(per_set[np.unique(frontier // 8)].sum())
+        assert 0 <= rec["mode"] < 5 and rec["t_ns"] >= 0
+
+
+def test_edge_cases(blest):
+    # single vertex, no edges
+    one = gg.from_edges(1, [], [], True)
+    with blest.build(1, one.row_ptr, np.zeros(1, np.int32)) as h:
+        assert h.bfs(0).tolist() == [0]
+    # isolated source in a larger graph; n not a multiple of 8 or 32
+    g = gg.disjoint_union(gg.cycle(45), gg.from_edges(3, [], [], True))
+    with blest.build_graph(g) as h:
+        lv = h.bfs(46)
+        assert lv[46] == 0 and (lv >= 0).sum() == 1
+        assert np.array_equal(h.bfs(3), oracle.bfs(g, 3))
+        with pytest.raises(blest.BlestError) as e:
+            h.bfs(48)
+        assert e.value.code == blest.ERR_INVALID
+        keep = np.full(g.n, 9, np.int32)
+        with pytest.raises(blest.BlestError):
+            h.bfs(-1, keep)
+        assert np.all(keep == 9)
+
+
+def test_malformed_csr_is_rejected(blest):
+    rp = np.array([0, 2, 1, 3], np.int64)
+    col = np.array([1, 2, 0], np.int32)
+    with pytest.raises(blest.BlestError) as e:
+        blest.build(3, rp, col)
+    assert e.value.code == blest.ERR_INVALID
+    rp = np.array([0, 1, 2, 3], np.int64)
+    col = np.array([1, 2, 3], np.int32)  # 3 out of range
+    with pytest.raises(blest.BlestError) as e:
+        blest.build(3, rp, col)
+    assert e.value.code == blest.ERR_INVALID
+
+
+def test_duplicates_and_self_loops_change_nothing(blest):
+    g = gg.rmat(10, seed=11)
+    src = np.repeat(np.arange(g.n), np.diff(g.row_ptr))
+    # add every arc twice plus a self loop on each vertex, unsorted rows
+    u = np.concatenate([src, src, np.arange(g.n)]).astype(np.int32)
+    v = np.concatenate([g.col, g.col, np.arange(g.n)]).astype(np.int32)
+    order = np.random.RandomState(0).permutation(len(u))
+    u, v = u[order], v[order]
+    rp = np.zeros(g.n + 1, np.int64)
+    np.add.at(rp, u + 1, 1)
+    rp = np.cumsum(rp)
+    col = v[np.argsort(u, kind="stable")]
+    with blest.build(g.n, rp, col.astype(np.int32)) as h:
+        assert h.info()["nnz"] == g.nnz
+        ref = oracle.bvss(g, 8)
+        got = h.bvss()
+        assert np.array_equal(got["masks"], ref["masks"]) and np.array_equal(got["rowIds"], ref["rowIds"])
+        for s in gg.sources(g, 3, 2):
+            assert np.array_equal(h.bfs(int(s)), oracle.bfs(g, int(s)))
+
+
+def test_barrier_timeout_returns_status_and_context_survives(blest):
+    assert blest.selftest_barrier_timeout(20) == blest.ERR_TIMEOUT
+    g = gg.path(100)
+    with blest.build_graph(g) as h:
+        assert np.array_equal(h.bfs(0), np.arange(100))
+
+
+def test_rmat16_64_sources_bit_exact(blest):
+    """Scale-16 RMAT, edge factor 16, no reordering, 64 seeded sources of
+    nonzero degree, heuristic policy (the small single-source workload)."""
+    g = gg.rmat(16, seed=1)
+    srcs = gg.sources(g, 64, 1)
+    ref = oracle.bfs_many(g, srcs)
+    with blest.build_graph(g) as h:
+        info = h.info()
+        assert info["lazy"] == 0  # U_div below 25,000 -> Algorithm 2
+        out = torch.empty(g.n, dtype=torch.int32, device="cuda")
+        for k, s in enumerate(srcs):
+            h.bfs(int(s), out)
+            assert np.array_equal(out.cpu().numpy(), ref[k]), k
