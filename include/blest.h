@@ -145,6 +145,14 @@ blest_status blest_msbfs(blest_handle h, const int32_t *sources, int32_t k, int3
  * (UNSUPPORTED otherwise). */
 blest_status blest_closeness(blest_handle h, int64_t *far, double *cc, int64_t *reach);
 
+/* Partial closeness: distance sums from the sources with original ids
+ * [first, first + count) only, written (not accumulated) to far and reach
+ * (n int64 each, reach may be NULL).  Sums over disjoint ranges add up to
+ * the full result; this is how an all-source run is split across calls,
+ * processes or GPUs.  Undirected graphs only. */
+blest_status blest_closeness_range(blest_handle h, int64_t first, int64_t count, int64_t *far,
+                                   int64_t *reach);
+
 /* Many small graphs in one handle: graph i has vertices [vtx_off[i],
  * vtx_off[i+1]) (local ids from 0) and arcs [edge_off[i], edge_off[i+1]);
  * its local row pointer is row_ptr[vtx_off[i] + i .. vtx_off[i+1] + i]

@@ -63,6 +63,7 @@ _sigs = {
     "blest_bfs": (_S, [_H, ctypes.c_int32, _P]),
     "blest_msbfs": (_S, [_H, _P, ctypes.c_int32, _P]),
     "blest_closeness": (_S, [_H, _P, _P, _P]),
+    "blest_closeness_range": (_S, [_H, ctypes.c_int64, ctypes.c_int64, _P, _P]),
     "blest_build_many": (_S, [ctypes.c_int32, _P, _P, _P, _P, ctypes.POINTER(BuildOpts), ctypes.POINTER(_H)]),
     "blest_bfs_many": (_S, [_H, _P, _P]),
     "blest_set_policy": (_S, [_H, ctypes.c_int32, ctypes.c_int32]),
@@ -187,6 +188,16 @@ class Graph:
             reach = np.empty(self.n, np.int64)
         _check(_lib.blest_closeness(self._h, _ptr(far), _ptr(cc), _ptr(reach)), "blest_closeness")
         return far, cc, reach
+
+    def closeness_range(self, first: int, count: int, far=None, reach=None):
+        """Distance sums from the sources [first, first+count) only."""
+        if far is None:
+            far = np.empty(self.n, np.int64)
+        if reach is None:
+            reach = np.empty(self.n, np.int64)
+        _check(_lib.blest_closeness_range(self._h, int(first), int(count), _ptr(far), _ptr(reach)),
+               "blest_closeness_range")
+        return far, reach
 
     def bfs_many(self, sources, out=None, total_n=None):
         src = np.ascontiguousarray(sources, dtype=np.int32) if not hasattr(sources, "data_ptr") else sources

@@ -50,6 +50,7 @@ static void free_all(blest_graph *h) {
     if (h->h_ctl) cudaFreeHost(h->h_ctl);
     if (h->own_stream) cudaStreamDestroy(h->own_stream);
     msbfs_release(h);
+    many_release(h);
 }
 
 extern "C" void blest_default_opts(blest_build_opts *o) {

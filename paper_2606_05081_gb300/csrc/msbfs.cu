@@ -1,22 +1,486 @@
+// Multi-source BFS (§6.1, Algorithm 5) and exact closeness centrality
+// (§6.2, Eq. 6-7).
+//
+// kappa BFSs run at once as bit lanes: every vertex owns a kappa-bit element
+// (KW = kappa/32 words) of the frontier F, visited V_curr and V_next arrays,
+// stored at the remapped index getVI(u, rho) = (u mod 8) * rho + u / 8
+// (rho = ceil(n/8)).  One persistent cooperative kernel runs all levels:
+//   stage 1 (lazy marking): a warp takes one VSS of the queue; its lanes
+//     form 32/KW groups of KW lanes, group g handling slices g, g+G, ...;
+//     lane w of a group holds word w of the 8 frontier elements of the VSS's
+//     slice set, so the hit vector of a slice is the OR of the frontier
+//     words its mask selects (Eq. 2 evaluated for kappa lanes at once); a
+//     nonzero word is OR-ed into V_next with one fire-and-forget atomic per
+//     word (coalesced across the group) and the target's slice set is
+//     marked dirty;
+//   stage 2 (finalize): only dirty slice sets are visited (a list built in
+//     stage 1); per vertex diff = V_curr xor V_next gives the lanes that
+//     reached it at this level: F = diff, V_curr = V_next, levels (source-
+//     major) and the closeness sums far += level * popc(diff) (Eq. 6),
+//     reach += popc(diff); activeSets = OR of the diffs; a set with any
+//     active lane enqueues its VSSs.
+// The words of lanes that are inactive for a slice set (activeSets word = 0)
+// are never loaded.
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
 #include "msbfs.h"
 
-void msbfs_release(blest_graph *h) { (void)h; }
+struct MsCtl {
+    unsigned long long bar;
+    int err;
+    int nlevels;
+    int timeout_where;
+    int qlen[2];
+    int dlen[2];
+};
+
+struct MsbfsWork {
+    int kappa = 0;
+    int KW = 0;
+    unsigned *F = nullptr, *Vc = nullptr, *Vn = nullptr, *active = nullptr;
+    int *dirty = nullptr;
+    int *dlist[2] = {nullptr, nullptr};
+    int *Q[2] = {nullptr, nullptr};
+    MsCtl *ctl = nullptr;
+    MsCtl *h_ctl = nullptr;
+    int *d_src = nullptr;
+    int grid = 0;
+    long long *far = nullptr, *reach = nullptr;   // closeness accumulators (reordered ids)
+};
+
+namespace {
+
+constexpr int MS_BLOCK = 512;
+
+struct MsParams {
+    int n, rho, k;
+    const int4 *__restrict__ rowIds;
+    const unsigned *__restrict__ masks;
+    const int *__restrict__ realPtrs;
+    const int *__restrict__ v2r;
+    unsigned *F, *Vc, *Vn, *active;
+    int *dirty;
+    int *dlist[2];
+    int *Q[2];
+    MsCtl *ctl;
+    const int *srcs;              // k source ids, original numbering
+    const int *new_of_old;        // may be null
+    const int *old_of_new;        // may be null
+    int *levels;                  // k*n, source-major, original ids; may be null
+    long long *far, *reach;       // may be null
+    unsigned long long budget_ns;
+};
+
+__device__ __forceinline__ bool ms_barrier(MsCtl *ctl, unsigned &epoch, unsigned long long budget) {
+    return grid_barrier(reinterpret_cast<Ctl *>(ctl), epoch, budget);
+}
+
+__device__ __forceinline__ int get_vi(int u, int rho) { return (u & 7) * rho + (u >> 3); }
+
+// warp-aggregated append of one slice set per lane (VSS range -> Q)
+__device__ __forceinline__ void ms_enqueue(const MsParams &P, bool want, int ss, int *Q, int slot) {
+    const int lane = lane_id();
+    if (!__any_sync(FULL_MASK, want)) return;
+    int a = 0, len = 0;
+    if (want) {
+        a = __ldg(&P.realPtrs[ss]);
+        len = __ldg(&P.realPtrs[ss + 1]) - a;
+    }
+    const int incl = warp_incl_scan(len);
+    int base = 0;
+    if (lane == 31 && incl) base = atomicAdd(&P.ctl->qlen[slot], incl);
+    base = __shfl_sync(FULL_MASK, base, 31) + incl - len;
+    for (int i = 0; i < len; ++i) Q[base + i] = a + i;
+}
+
+template <int KW>
+__device__ void ms_stage1(const MsParams &P, int qlen, const int *Qc, int dl, int *s_rows, unsigned char *s_m) {
+    constexpr int G = 32 / KW;
+    const int lane = lane_id();
+    const int g = lane / KW, w = lane % KW;
+    const int wib = threadIdx.x >> 5;
+    int *rows = s_rows + wib * 128;
+    unsigned char *m8s = s_m + wib * 128;
+    const int gwarp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
+    for (int it = gwarp; it < qlen; it += nwarps) {
+        const int vss = Qc[it];
+        const int ss = __ldg(&P.v2r[vss]);
+        const int4 r = __ldg(&P.rowIds[(size_t)vss * 32 + lane]);
+        const unsigned m = __ldg(&P.masks[(size_t)vss * 32 + lane]);
+        __syncwarp();
+        rows[lane * 4 + 0] = r.x;
+        rows[lane * 4 + 1] = r.y;
+        rows[lane * 4 + 2] = r.z;
+        rows[lane * 4 + 3] = r.w;
+        m8s[lane * 4 + 0] = (unsigned char)(m & 0xFFu);
+        m8s[lane * 4 + 1] = (unsigned char)((m >> 8) & 0xFFu);
+        m8s[lane * 4 + 2] = (unsigned char)((m >> 16) & 0xFFu);
+        m8s[lane * 4 + 3] = (unsigned char)(m >> 24);
+        const unsigned aw = P.active[(size_t)ss * KW + w];
+        unsigned f[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) f[j] = aw ? P.F[(size_t)get_vi(ss * 8 + j, P.rho) * KW + w] : 0u;
+        __syncwarp();
+#pragma unroll 2
+        for (int t = 0; t < 128 / G; ++t) {
+            const int kk = t * G + g;
+            const unsigned m8 = m8s[kk];
+            unsigned hit = 0;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) hit |= (m8 >> j & 1u) ? f[j] : 0u;
+            const int u = rows[kk];
+            if (hit) red_or(&P.Vn[(size_t)get_vi(u, P.rho) * KW + w], hit);
+            const unsigned bal = __ballot_sync(FULL_MASK, hit != 0);
+            if (w == 0 && ((bal >> (g * KW)) & (KW == 32 ? 0xFFFFFFFFu : ((1u << KW) - 1u)))) {
+                const int so = u >> 3;
+                if (ld_volatile_i32(&P.dirty[so]) == 0 && atomicExch(&P.dirty[so], 1) == 0)
+                    P.dlist[dl][atomicAdd(&P.ctl->dlen[dl], 1)] = so;
+            }
+        }
+    }
+}
+
+template <int KW>
+__device__ void ms_stage2(const MsParams &P, int ell, int dl, int qn) {
+    constexpr int G = 32 / KW;
+    const int lane = lane_id();
+    const int g = lane / KW, w = lane % KW;
+    const int gwarp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
+    const int dcount = ld_volatile_i32(&P.ctl->dlen[dl]);
+    const int *dlist = P.dlist[dl];
+    for (int base = gwarp * G; base < dcount; base += nwarps * G) {
+        const int i = base + g;
+        const bool valid = i < dcount;
+        const int ss = valid ? dlist[i] : 0;
+        unsigned A = 0;
+#pragma unroll 1
+        for (int j = 0; j < 8; ++j) {
+            const int u = ss * 8 + j;
+            unsigned diff = 0;
+            if (valid && u < P.n) {
+                const size_t e = (size_t)get_vi(u, P.rho) * KW + w;
+                const unsigned next = P.Vn[e];
+                const unsigned cur = P.Vc[e];
+                diff = next ^ cur;
+                P.F[e] = diff;
+                if (diff) {
+                    P.Vc[e] = next;
+                    A |= diff;
+                    if (P.levels) {
+                        const int uo = P.old_of_new ? __ldg(&P.old_of_new[u]) : u;
+                        unsigned d = diff;
+                        while (d) {
+                            const int b = __ffs(d) - 1;
+                            d &= d - 1;
+                            const int c = w * 32 + b;
+                            if (c < P.k) P.levels[(size_t)c * P.n + uo] = ell;
+                        }
+                    }
+                }
+            }
+            if (P.far) {
+                int cnt = __popc(diff);
+#pragma unroll
+                for (int o = KW / 2; o > 0; o >>= 1) cnt += __shfl_xor_sync(FULL_MASK, cnt, o, KW);
+                if (w == 0 && cnt) {
+                    P.far[u] += (long long)ell * cnt;
+                    P.reach[u] += cnt;
+                }
+            }
+        }
+        if (valid) {
+            P.active[(size_t)ss * KW + w] = A;
+        }
+        const unsigned bal = __ballot_sync(FULL_MASK, A != 0);
+        const bool any = ((bal >> (g * KW)) & (KW == 32 ? 0xFFFFFFFFu : ((1u << KW) - 1u))) != 0;
+        if (valid && w == 0) P.dirty[ss] = 0;
+        ms_enqueue(P, valid && w == 0 && any, ss, P.Q[qn], qn);
+    }
+}
+
+template <int KW>
+__global__ void __launch_bounds__(MS_BLOCK, 1) k_msbfs(MsParams P) {
+    __shared__ int s_rows[(MS_BLOCK / 32) * 128];
+    __shared__ unsigned char s_m[(MS_BLOCK / 32) * 128];
+    const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t nthreads = (size_t)gridDim.x * blockDim.x;
+    MsCtl *ctl = P.ctl;
+    unsigned epoch = 0;
+
+    // ---- init: zero the bit arrays and flags, -1 levels for the k lanes
+    const size_t words = (size_t)P.rho * 8 * KW;
+    for (size_t i = tid; i < words; i += nthreads) {
+        P.F[i] = 0u;
+        P.Vc[i] = 0u;
+        P.Vn[i] = 0u;
+    }
+    for (size_t i = tid; i < (size_t)P.rho * KW; i += nthreads) P.active[i] = 0u;
+    for (size_t i = tid; i < (size_t)P.rho; i += nthreads) P.dirty[i] = 0;
+    if (P.levels)
+        for (size_t i = tid; i < (size_t)P.k * P.n; i += nthreads) P.levels[i] = -1;
+    if (!ms_barrier(ctl, epoch, P.budget_ns)) return;
+    // ---- sources: lane c starts at srcs[c]
+    if (tid < (size_t)P.k) {
+        const int c = (int)tid;
+        const int so = __ldg(&P.srcs[c]);
+        const int u = P.new_of_old ? __ldg(&P.new_of_old[so]) : so;
+        const size_t e = (size_t)get_vi(u, P.rho) * KW + (c >> 5);
+        const unsigned bit = 1u << (c & 31);
+        atomicOr(&P.Vc[e], bit);
+        atomicOr(&P.Vn[e], bit);
+        atomicOr(&P.F[e], bit);
+        atomicOr(&P.active[(size_t)(u >> 3) * KW + (c >> 5)], bit);
+        if (P.levels) P.levels[(size_t)c * P.n + so] = 0;
+        if (P.reach) atomicAdd((unsigned long long *)&P.reach[u], 1ull);
+        if (atomicExch(&P.dirty[u >> 3], 1) == 0) P.dlist[1][atomicAdd(&ctl->dlen[1], 1)] = u >> 3;
+    }
+    if (!ms_barrier(ctl, epoch, P.budget_ns)) return;
+    {
+        // enqueue the source slice sets and clear their flags
+        const int cnt = ld_volatile_i32(&ctl->dlen[1]);
+        const int gwarp = (int)(tid >> 5), nwarps = (int)(nthreads >> 5);
+        for (int b = gwarp * 32; b < cnt; b += nwarps * 32) {
+            const int i = b + lane_id();
+            const bool ok = i < cnt;
+            const int ss = ok ? P.dlist[1][i] : 0;
+            if (ok) P.dirty[ss] = 0;
+            ms_enqueue(P, ok, ss, P.Q[0], 0);
+        }
+    }
+    if (!ms_barrier(ctl, epoch, P.budget_ns)) return;
+    if (tid == 0) ctl->dlen[1] = 0;
+    if (!ms_barrier(ctl, epoch, P.budget_ns)) return;
+
+    int ell = 1;
+    for (;; ++ell) {
+        const int qc = (ell - 1) & 1, qn = ell & 1, dl = ell & 1;
+        const int qlen = ld_volatile_i32(&ctl->qlen[qc]);
+        if (qlen == 0) break;
+        if (tid == 0) ctl->qlen[qn] = 0;
+        ms_stage1<KW>(P, qlen, P.Q[qc], dl, s_rows, s_m);
+        if (!ms_barrier(ctl, epoch, P.budget_ns)) return;
+        if (tid == 0) ctl->dlen[dl ^ 1] = 0;
+        ms_stage2<KW>(P, ell, dl, qn);
+        if (!ms_barrier(ctl, epoch, P.budget_ns)) return;
+    }
+    if (tid == 0) ctl->nlevels = ell - 1;
+}
+
+__global__ void k_cc(const long long *__restrict__ far, const long long *__restrict__ reach,
+                     const int *__restrict__ new_of_old, int n, long long *far_out, double *cc_out,
+                     long long *reach_out) {
+    const int stride = gridDim.x * blockDim.x;
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        const int u = new_of_old ? new_of_old[v] : v;
+        const long long f = far[u], r = reach[u];
+        if (far_out) far_out[v] = f;
+        if (reach_out) reach_out[v] = r;
+        if (cc_out) cc_out[v] = f > 0 ? (double)(r - 1) / (double)f : 0.0;   // Eq. 7, component-normalised
+    }
+}
+
+template <int KW>
+int ms_grid() {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_msbfs<KW>, MS_BLOCK, 0);
+    return per * sms;
+}
+
+}  // namespace
+
+void msbfs_release(blest_graph *h) {
+    if (h->ms) {
+        if (h->ms->h_ctl) cudaFreeHost(h->ms->h_ctl);
+        delete h->ms;
+        h->ms = nullptr;
+    }
+}
+
+static blest_status ms_prepare(blest_graph *h, int kappa) {
+    if (h->ms && h->ms->kappa >= kappa) return BLEST_OK;
+    if (h->ms && h->ms->kappa < kappa) {
+        // grow: the old arrays stay owned by the handle (freed at destroy)
+        if (h->ms->h_ctl) cudaFreeHost(h->ms->h_ctl);
+        delete h->ms;
+        h->ms = nullptr;
+    }
+    MsbfsWork *m = new MsbfsWork();
+    m->kappa = kappa;
+    m->KW = kappa / 32;
+    const size_t rho = (size_t)h->Ns;
+    const size_t words = rho * 8 * (size_t)m->KW;
+    blest_status st;
+    if ((st = dev_alloc_t(h, &m->F, words)) != BLEST_OK) { delete m; return st; }
+    if ((st = dev_alloc_t(h, &m->Vc, words)) != BLEST_OK) { delete m; return st; }
+    if ((st = dev_alloc_t(h, &m->Vn, words)) != BLEST_OK) { delete m; return st; }
+    if ((st = dev_alloc_t(h, &m->active, rho * m->KW)) != BLEST_OK) { delete m; return st; }
+    if ((st = dev_alloc_t(h, &m->dirty, rho)) != BLEST_OK) { delete m; return st; }
+    for (int i = 0; i < 2; ++i) {
+        if ((st = dev_alloc_t(h, &m->dlist[i], rho + 1)) != BLEST_OK) { delete m; return st; }
+        if ((st = dev_alloc_t(h, &m->Q[i], (size_t)(h->Nv > 0 ? h->Nv : 1))) != BLEST_OK) { delete m; return st; }
+    }
+    if ((st = dev_alloc_t(h, &m->ctl, 1)) != BLEST_OK) { delete m; return st; }
+    if ((st = dev_alloc_t(h, &m->d_src, 1024)) != BLEST_OK) { delete m; return st; }
+    if (cudaMallocHost((void **)&m->h_ctl, sizeof(MsCtl)) != cudaSuccess) { delete m; return BLEST_ERR_OOM; }
+    m->grid = kappa == 64 ? ms_grid<2>() : (kappa == 256 ? ms_grid<8>() : ms_grid<32>());
+    if (m->grid <= 0) { delete m; return BLEST_ERR_CUDA; }
+    h->ms = m;
+    return BLEST_OK;
+}
+
+// One multi-source launch over k <= kappa sources already on the device.
+static blest_status ms_launch(blest_graph *h, int k, int *levels_dev, long long *far, long long *reach) {
+    MsbfsWork *m = h->ms;
+    MsParams P;
+    memset(&P, 0, sizeof P);
+    P.n = (int)h->n;
+    P.rho = (int)h->Ns;
+    P.k = k;
+    P.rowIds = h->g.rowIds;
+    P.masks = h->g.masks;
+    P.realPtrs = h->g.realPtrs;
+    P.v2r = h->g.v2r;
+    P.F = m->F;
+    P.Vc = m->Vc;
+    P.Vn = m->Vn;
+    P.active = m->active;
+    P.dirty = m->dirty;
+    P.dlist[0] = m->dlist[0];
+    P.dlist[1] = m->dlist[1];
+    P.Q[0] = m->Q[0];
+    P.Q[1] = m->Q[1];
+    P.ctl = m->ctl;
+    P.srcs = m->d_src;
+    P.new_of_old = h->g.new_of_old;
+    P.old_of_new = h->g.old_of_new;
+    P.levels = levels_dev;
+    P.far = far;
+    P.reach = reach;
+    P.budget_ns = (unsigned long long)h->timeout_ms * 1000000ull;
+    if (cudaMemsetAsync(m->ctl, 0, sizeof(MsCtl), h->stream) != cudaSuccess) return BLEST_ERR_CUDA;
+    void *args[] = {&P};
+    const void *fn = m->KW == 2 ? (const void *)k_msbfs<2> : (m->KW == 8 ? (const void *)k_msbfs<8> : (const void *)k_msbfs<32>);
+    cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(m->grid), dim3(MS_BLOCK), args, 0, h->stream);
+    if (e != cudaSuccess) {
+        blest_internal_record_cuda_error(e, "cudaLaunchCooperativeKernel(k_msbfs)", __FILE__, __LINE__);
+        return BLEST_ERR_CUDA;
+    }
+    return BLEST_OK;
+}
+
+static blest_status ms_finish(blest_graph *h, bool sync) {
+    MsbfsWork *m = h->ms;
+    if (cudaMemcpyAsync(m->h_ctl, m->ctl, sizeof(MsCtl), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
+        return BLEST_ERR_CUDA;
+    if (!sync) return BLEST_OK;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return BLEST_ERR_CUDA;
+    if (m->h_ctl->err) return (blest_status)m->h_ctl->err;
+    return BLEST_OK;
+}
+
+static int kappa_for(int k) { return k <= 64 ? 64 : (k <= 256 ? 256 : 1024); }
 
 extern "C" blest_status blest_msbfs(blest_handle h, const int32_t *sources, int32_t k, int32_t *levels) {
-    (void)h; (void)sources; (void)k; (void)levels;
-    return BLEST_ERR_UNSUPPORTED;
+    if (!h || h->many || !sources || !levels || k < 1 || k > 1024) return BLEST_ERR_INVALID;
+    std::vector<int32_t> src((size_t)k);
+    if (cudaMemcpy(src.data(), sources, (size_t)k * 4, cudaMemcpyDefault) != cudaSuccess) return BLEST_ERR_CUDA;
+    for (int32_t s : src)
+        if (s < 0 || (int64_t)s >= h->n) return BLEST_ERR_INVALID;
+    blest_status st = ms_prepare(h, kappa_for(k));
+    if (st != BLEST_OK) return st;
+    const bool dev = is_device_ptr(levels);
+    int32_t *target = levels;
+    if (!dev) {
+        void *p = nullptr;
+        if (cudaMallocAsync(&p, (size_t)k * (size_t)h->n * 4, h->stream) != cudaSuccess) return BLEST_ERR_OOM;
+        target = (int32_t *)p;
+    }
+    if (cudaMemcpyAsync(h->ms->d_src, src.data(), (size_t)k * 4, cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
+        return BLEST_ERR_CUDA;
+    st = ms_launch(h, k, target, nullptr, nullptr);
+    if (st == BLEST_OK && !dev) {
+        if (cudaMemcpyAsync(levels, target, (size_t)k * (size_t)h->n * 4, cudaMemcpyDeviceToHost, h->stream) !=
+            cudaSuccess)
+            st = BLEST_ERR_CUDA;
+        cudaFreeAsync(target, h->stream);
+    }
+    if (st != BLEST_OK) return st;
+    return ms_finish(h, !dev || !h->async);
 }
+
+// Distance sums from the sources [first, first + count) (original ids),
+// accumulated into the handle's device accumulators.
+static blest_status closeness_batches(blest_graph *h, int64_t first, int64_t count) {
+    blest_status st = ms_prepare(h, 1024);
+    if (st != BLEST_OK) return st;
+    std::vector<int32_t> src(1024);
+    for (int64_t b = first; b < first + count; b += 1024) {
+        const int k = (int)((first + count - b) < 1024 ? (first + count - b) : 1024);
+        for (int c = 0; c < k; ++c) src[(size_t)c] = (int32_t)(b + c);
+        if (cudaMemcpyAsync(h->ms->d_src, src.data(), (size_t)k * 4, cudaMemcpyHostToDevice, h->stream) !=
+            cudaSuccess)
+            return BLEST_ERR_CUDA;
+        st = ms_launch(h, k, nullptr, h->ms->far, h->ms->reach);
+        if (st != BLEST_OK) return st;
+        st = ms_finish(h, true);  // the host buffer `src` is reused next batch
+        if (st != BLEST_OK) return st;
+    }
+    return BLEST_OK;
+}
+
+static blest_status closeness_common(blest_graph *h, int64_t first, int64_t count, int64_t *far, double *cc,
+                                     int64_t *reach) {
+    if (!h || h->many) return BLEST_ERR_INVALID;
+    if (h->directed) return BLEST_ERR_UNSUPPORTED;
+    if (first < 0 || count < 0 || first + count > h->n) return BLEST_ERR_INVALID;
+    blest_status st = ms_prepare(h, 1024);
+    if (st != BLEST_OK) return st;
+    MsbfsWork *m = h->ms;
+    if (!m->far) {
+        if ((st = dev_alloc_t(h, &m->far, (size_t)h->n)) != BLEST_OK) return st;
+        if ((st = dev_alloc_t(h, &m->reach, (size_t)h->n)) != BLEST_OK) return st;
+    }
+    if (cudaMemsetAsync(m->far, 0, (size_t)h->n * 8, h->stream) != cudaSuccess) return BLEST_ERR_CUDA;
+    if (cudaMemsetAsync(m->reach, 0, (size_t)h->n * 8, h->stream) != cudaSuccess) return BLEST_ERR_CUDA;
+    st = closeness_batches(h, first, count);
+    if (st != BLEST_OK) return st;
+    // outputs (original ids); host outputs are staged on the device
+    void *dfar = far, *dcc = cc, *dreach = reach;
+    std::vector<void *> tmp;
+    auto stage = [&](void *user, size_t bytes) -> void * {
+        if (!user || is_device_ptr(user)) return user;
+        void *p = nullptr;
+        if (cudaMallocAsync(&p, bytes, h->stream) != cudaSuccess) return nullptr;
+        tmp.push_back(p);
+        return p;
+    };
+    dfar = stage(far, (size_t)h->n * 8);
+    dcc = stage(cc, (size_t)h->n * 8);
+    dreach = stage(reach, (size_t)h->n * 8);
+    if ((far && !dfar) || (cc && !dcc) || (reach && !dreach)) return BLEST_ERR_OOM;
+    k_cc<<<(unsigned)((h->n + 255) / 256 < 65535 ? (h->n + 255) / 256 : 65535), 256, 0, h->stream>>>(
+        m->far, m->reach, h->g.new_of_old, (int)h->n, (long long *)dfar, (double *)dcc, (long long *)dreach);
+    if (far && dfar != far) cudaMemcpyAsync(far, dfar, (size_t)h->n * 8, cudaMemcpyDeviceToHost, h->stream);
+    if (cc && dcc != cc) cudaMemcpyAsync(cc, dcc, (size_t)h->n * 8, cudaMemcpyDeviceToHost, h->stream);
+    if (reach && dreach != reach) cudaMemcpyAsync(reach, dreach, (size_t)h->n * 8, cudaMemcpyDeviceToHost, h->stream);
+    for (void *p : tmp) cudaFreeAsync(p, h->stream);
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return BLEST_ERR_CUDA;
+    return BLEST_OK;
+}
+
 extern "C" blest_status blest_closeness(blest_handle h, int64_t *far, double *cc, int64_t *reach) {
-    (void)h; (void)far; (void)cc; (void)reach;
-    return BLEST_ERR_UNSUPPORTED;
+    if (!h || !far) return BLEST_ERR_INVALID;
+    return closeness_common(h, 0, h->n, far, cc, reach);
 }
-extern "C" blest_status blest_build_many(int32_t g, const int64_t *vtx_off, const int64_t *edge_off,
-                                         const int64_t *row_ptr, const int32_t *col_idx_local,
-                                         const blest_build_opts *opts, blest_handle *out) {
-    (void)g; (void)vtx_off; (void)edge_off; (void)row_ptr; (void)col_idx_local; (void)opts; (void)out;
-    return BLEST_ERR_UNSUPPORTED;
-}
-extern "C" blest_status blest_bfs_many(blest_handle h, const int32_t *sources, int32_t *levels) {
-    (void)h; (void)sources; (void)levels;
-    return BLEST_ERR_UNSUPPORTED;
+
+extern "C" blest_status blest_closeness_range(blest_handle h, int64_t first, int64_t count, int64_t *far,
+                                              int64_t *reach) {
+    if (!h || !far) return BLEST_ERR_INVALID;
+    return closeness_common(h, first, count, far, nullptr, reach);
 }

@@ -4,3 +4,4 @@
 #include "handle.h"
 
 void msbfs_release(blest_graph *h);
+void many_release(blest_graph *h);

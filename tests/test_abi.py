@@ -25,8 +25,8 @@ def test_header_declares_the_boundary():
 
 
 def test_library_builds_and_exports_every_symbol():
-    from paper_2606_05081_gb300 import _build
-    lib = _build.build()
+    import __graft_entry__ as ge
+    lib = ge._load_build_module().build()
     out = subprocess.run(["nm", "-D", "--defined-only", lib], capture_output=True, text=True, check=True).stdout
     exported = set(re.findall(r"\bT (blest_[a-z_0-9]+)", out))
     missing = [n for n in _declared() if n not in exported]
