@@ -35,6 +35,8 @@ WORKLOADS = {
     "rmat24": (lambda: gg.rmat(24, 16, seed=2), dict(reorder=0),
                "RMAT scale 24 (16.7M vertices), edge factor 16, a=.57 b=c=.19, undirected, "
                "labels scrambled"),
+    "rmat22": (lambda: gg.rmat(22, 16, seed=3), dict(reorder=0),
+               "RMAT scale 22 (4.2M vertices), edge factor 16, undirected, labels scrambled"),
     "rmat16": (lambda: gg.rmat(16, 16, seed=1), dict(reorder=0),
                "RMAT scale 16 (65,536 vertices), edge factor 16, undirected, no reordering"),
     "grid4096": (lambda: gg.grid(4096, 4096, 0.05, 0.001, seed=2), dict(reorder=0),
@@ -65,7 +67,7 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -190,11 +192,13 @@ def cpu_baseline(g, srcs, budget_s=15.0):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default="rmat24", choices=sorted(WORKLOADS))
     ap.add_argument("--impl", default="blest", choices=["blest", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sources", type=int, default=NUM_SOURCES)
+    ap.add_argument("--levels", action="store_true", help="print the per-level log of the first source to stderr")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "blest" else args.warmup
 
@@ -223,14 +227,16 @@ def main():
     g = build_fn()
     gen_s = time.time() - t0
     # replicas: each rank runs its own seeded sources on its own copy (weak scaling)
-    srcs = gg.sources(g, NUM_SOURCES, 7 + rank)
+    srcs = gg.sources(g, args.sources, 7 + rank)
     deg = np.diff(g.row_ptr)
     rp_d = torch.from_numpy(g.row_ptr).to(dev)
     col_d = torch.from_numpy(g.col).to(dev)
     h = blest.build(g.n, rp_d, col_d, **bopts)
     del rp_d, col_d
     info = h.info()
-    stream = torch.cuda.current_stream(dev)
+    # a dedicated stream: the events below and the library's kernels share it
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
     h.set_stream(stream.cuda_stream, True)
     out = torch.empty(g.n, dtype=torch.int32, device=dev)
     deg_d = torch.from_numpy(deg).to(dev)
@@ -245,6 +251,9 @@ def main():
         e = int(deg_d[reached].sum().item())
         edges.append(e if g.directed else e // 2)
         logs.append((h.level_log(), int(reached.sum().item())))
+    if args.levels and rank == 0:
+        for rec in logs[0][0]:
+            print("level", json.dumps(rec), file=sys.stderr)
 
     starts = [torch.cuda.Event(enable_timing=True) for _ in srcs]
     ends = [torch.cuda.Event(enable_timing=True) for _ in srcs]
@@ -317,7 +326,7 @@ def main():
         "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int32", "data": "synthetic",
         "config": {"workload": args.workload, "graph": desc, "n": g.n, "nnz": int(info["nnz"]),
-                   "sources": NUM_SOURCES, "reorder": int(info["reorder"]), "lazy": int(info["lazy"]),
+                   "sources": len(srcs), "reorder": int(info["reorder"]), "lazy": int(info["lazy"]),
                    "switching": int(info["switching"]), "policy": "heuristic",
                    "udiv": info["update_divergence"], "num_vss": int(info["num_vss"]),
                    "l2": "inputs larger than L2 (BVSS arrays), no flush", "parallelism": f"replicas{world}",
