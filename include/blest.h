@@ -206,6 +206,40 @@ void blest_destroy(blest_handle h);
 
 const char *blest_status_string(blest_status s);
 
+/* ---- Allocation-free BFS ------------------------------------------------
+ * The paper has no counterpart to this entry point.  It serves callers that
+ * cannot call cudaMalloc: code whose device memory is entirely owned by
+ * another allocator (a framework that reserves the whole pool up front) and
+ * latency-critical paths where cudaMalloc's implicit device synchronisation
+ * is not allowed.  It runs the single-source BFS kernel over a BVSS the
+ * caller already holds in device memory (for example copied out of a handle
+ * with blest_get_bvss), in a fixed top-down eager mode, and allocates
+ * nothing: its scratch (bitvectors, queues, control block, about 5.3 MB)
+ * is a static array of the library's device image that every GPU loading
+ * the library holds until the process exits.
+ *  - Limits: n <= 1,048,576 vertices and num_vss <= 262,144; larger graphs
+ *    return BLEST_ERR_UNSUPPORTED.
+ *  - The first call on each device looks up the array's device address with
+ *    that device current; make that first call before any stream capture.
+ *  - All calls share the scratch array: calls that overlap on the GPU (other
+ *    streams or host threads) race.  Each call clears what must start at zero.
+ *  - levels must be device memory (n int32); the call is synchronous on
+ *    `stream` (a cudaStream_t, NULL = the legacy default stream) and returns
+ *    the device status. */
+typedef struct blest_bvss_view {
+    int64_t n;                       /* vertices */
+    int64_t num_slice_sets;          /* N_s = ceil(n / 8) */
+    int64_t num_vss;                 /* N_v */
+    const int32_t *row_ids;          /* device, N_v*128 (blest_get_bvss layout) */
+    const uint32_t *masks;           /* device, N_v*32 */
+    const int32_t *real_ptrs;        /* device, N_s + 1 */
+    const int32_t *virtual_to_real;  /* device, N_v */
+    const int32_t *out_degree;       /* device, n out-degrees (per-level counters) */
+    int32_t engine_tc;               /* 1: b1 MMA hit test, 0: CUDA cores */
+} blest_bvss_view;
+
+blest_status blest_bfs_noalloc(const blest_bvss_view *g, int32_t source, int32_t *levels, void *stream);
+
 /* Test hook for the timed-out grid barrier: launches a cooperative kernel in
  * which one block waits on a barrier no other block joins.  Returns
  * BLEST_ERR_TIMEOUT after about timeout_ms when the wait gives up as it

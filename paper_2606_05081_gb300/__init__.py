@@ -54,6 +54,14 @@ class LevelLog(ctypes.Structure):
                 ("t_ns", ctypes.c_int64)]
 
 
+class BvssView(ctypes.Structure):
+    """blest_bvss_view: device pointers of a BVSS the caller owns."""
+    _fields_ = [("n", ctypes.c_int64), ("num_slice_sets", ctypes.c_int64), ("num_vss", ctypes.c_int64),
+                ("row_ids", ctypes.c_void_p), ("masks", ctypes.c_void_p), ("real_ptrs", ctypes.c_void_p),
+                ("virtual_to_real", ctypes.c_void_p), ("out_degree", ctypes.c_void_p),
+                ("engine_tc", ctypes.c_int32)]
+
+
 _P = ctypes.c_void_p
 _H = ctypes.c_void_p
 _S = ctypes.c_int
@@ -78,6 +86,7 @@ _sigs = {
     "blest_destroy": (None, [_H]),
     "blest_status_string": (ctypes.c_char_p, [_S]),
     "blest_selftest_barrier_timeout": (_S, [ctypes.c_int32]),
+    "blest_bfs_noalloc": (_S, [ctypes.POINTER(BvssView), ctypes.c_int32, _P, _P]),
     "blest_last_cuda_error": (ctypes.c_char_p, []),
 }
 for _name, (_res, _args) in _sigs.items():
@@ -285,3 +294,10 @@ def build_many(batch, **opts) -> Graph:
 
 def selftest_barrier_timeout(timeout_ms: int = 20) -> int:
     return int(_lib.blest_selftest_barrier_timeout(int(timeout_ms)))
+
+
+def bfs_noalloc(view: BvssView, source: int, levels, stream=None):
+    """Allocation-free BFS over a caller-held device BVSS (blest_bfs_noalloc).
+    levels must be a CUDA int32 tensor of view.n elements."""
+    _check(_lib.blest_bfs_noalloc(ctypes.byref(view), int(source), _ptr(levels), stream), "blest_bfs_noalloc")
+    return levels

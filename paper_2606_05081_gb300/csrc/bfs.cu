@@ -472,3 +472,124 @@ blest_status bfs_run(blest_graph *h, int32_t source, int32_t *dev_out) {
     }
     return BLEST_OK;
 }
+
+// ------------------------------------------------------------------------
+// Allocation-free single-source BFS (blest_bfs_noalloc in blest.h).
+//
+// Some callers cannot allocate device memory: a framework that reserves the
+// whole device pool for its own allocator up front, or a latency-critical
+// path where cudaMalloc's implicit device synchronisation is not allowed.
+// This entry point runs the same persistent kernel (k_bfs) as blest_bfs, but
+// its scratch -- visited and frontier bitvectors, the three VSS and
+// slice-set queues and the control block -- lives in the file-scope array
+// below, so the call allocates nothing.  The array is part of the library's
+// device image: every GPU that loads the library holds it (about 5.3 MB)
+// until the process exits.  All calls share it and it keeps the last call's
+// contents; the kernel rewrites every bitvector and queue it reads and the
+// control block is cleared before each launch.  Calls that overlap on the
+// GPU (different streams, or different host threads) race on the array.
+// ------------------------------------------------------------------------
+namespace {
+
+constexpr long long NOALLOC_MAX_N = 1ll << 20;     // vertices
+constexpr long long NOALLOC_MAX_NV = 1ll << 18;    // VSSs
+constexpr long long NOALLOC_W = NOALLOC_MAX_N / 32;           // bitvector words
+constexpr long long NOALLOC_NS = NOALLOC_MAX_N / 8 + 1;       // slice sets + 1
+constexpr size_t NOALLOC_CTL_BYTES = 256;
+constexpr size_t NOALLOC_BITS_BYTES = 5ull * (NOALLOC_W + 1) * 4;
+constexpr size_t NOALLOC_Q_BYTES = 3ull * NOALLOC_MAX_NV * 4;
+constexpr size_t NOALLOC_SQ_BYTES = 3ull * NOALLOC_NS * 4;
+constexpr size_t NOALLOC_BYTES = NOALLOC_CTL_BYTES + NOALLOC_BITS_BYTES + NOALLOC_Q_BYTES + NOALLOC_SQ_BYTES + 1024;
+static_assert(sizeof(Ctl) <= NOALLOC_CTL_BYTES, "control block fits its slot");
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+unsigned char *g_noalloc_addr[NOALLOC_MAX_DEVICES];   // device address per device ordinal
+int g_noalloc_grid[NOALLOC_MAX_DEVICES];
+
+// Once per device, with that device current: the host-side symbol is only a
+// stand-in, so look up the array's device address.
+blest_status noalloc_setup(int dev, unsigned char **base, int *grid) {
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return BLEST_ERR_UNSUPPORTED;
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            blest_internal_record_cuda_error(e, "cudaGetSymbolAddress(g_noalloc_scratch)", __FILE__, __LINE__);
+            return BLEST_ERR_CUDA;
+        }
+        int sms = 0;
+        const int g = bfs_grid_for(512, &sms);
+        if (g <= 0) return BLEST_ERR_CUDA;
+        g_noalloc_grid[dev] = g;
+        g_noalloc_addr[dev] = (unsigned char *)p;
+    }
+    *base = g_noalloc_addr[dev];
+    *grid = g_noalloc_grid[dev];
+    return BLEST_OK;
+}
+
+}  // namespace
+
+extern "C" blest_status blest_bfs_noalloc(const blest_bvss_view *g, int32_t source, int32_t *levels,
+                                          void *stream) {
+    if (!g || !levels || !g->row_ids || !g->masks || !g->real_ptrs || !g->virtual_to_real || !g->out_degree)
+        return BLEST_ERR_INVALID;
+    if (g->n < 1 || g->num_vss < 0 || g->num_slice_sets != (g->n + 7) / 8) return BLEST_ERR_INVALID;
+    if (g->n > NOALLOC_MAX_N || g->num_vss > NOALLOC_MAX_NV) return BLEST_ERR_UNSUPPORTED;
+    if (source < 0 || (int64_t)source >= g->n) return BLEST_ERR_INVALID;
+    if (!is_device_ptr(levels)) return BLEST_ERR_INVALID;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return BLEST_ERR_CUDA;
+    unsigned char *base = nullptr;
+    int grid = 0;
+    blest_status st = noalloc_setup(dev, &base, &grid);
+    if (st != BLEST_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+
+    const long long n = g->n, W = (n + 31) / 32, Ns = g->num_slice_sets;
+    const long long nv = g->num_vss > 0 ? g->num_vss : 1;
+    unsigned char *p = base;
+    Ctl *ctl = (Ctl *)p;
+    p += NOALLOC_CTL_BYTES;
+    BfsParams P;
+    memset(&P, 0, sizeof P);
+    P.Vc = (unsigned *)p; p += (W + 1) * 4;
+    P.Vn = (unsigned *)p; p += (W + 1) * 4;
+    for (int i = 0; i < 3; ++i) { P.F[i] = (unsigned *)p; p += (W + 1) * 4; }
+    for (int i = 0; i < 3; ++i) { P.Q[i] = (int *)p; p += nv * 4; }
+    for (int i = 0; i < 3; ++i) { P.SQ[i] = (int *)p; p += (Ns + 1) * 4; }
+    if ((size_t)(p - base) > NOALLOC_BYTES) return BLEST_ERR_INTERNAL;
+    P.n = (int)n;
+    P.W = (int)W;
+    P.rowIds = (const int4 *)g->row_ids;
+    P.masks = g->masks;
+    P.realPtrs = g->real_ptrs;
+    P.v2r = g->virtual_to_real;
+    P.rp = nullptr;              // bottom-up levels are never chosen: fixed top-down mode
+    P.col = nullptr;
+    P.deg = g->out_degree;
+    P.L = levels;
+    P.ctl = ctl;
+    P.log = nullptr;
+    P.log_cap = 0;
+    P.src = source;
+    P.policy = BLEST_POLICY_FIXED;
+    P.fixed_mode = g->engine_tc ? BLEST_MODE_PUSH_EAGER_TC : BLEST_MODE_PUSH_EAGER_CC;
+    P.eta = 10.f;
+    P.budget_ns = 5000ull * 1000000ull;
+    P.new_of_old = nullptr;
+    P.out = nullptr;
+    if (cudaMemsetAsync(ctl, 0, sizeof(Ctl), s) != cudaSuccess) return BLEST_ERR_CUDA;
+    void *args[] = {&P};
+    cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_bfs, dim3(grid), dim3(512), args, 0, s);
+    if (e != cudaSuccess) {
+        blest_internal_record_cuda_error(e, "cudaLaunchCooperativeKernel(k_bfs, no-alloc)", __FILE__, __LINE__);
+        return BLEST_ERR_CUDA;
+    }
+    Ctl hc;
+    if (cudaMemcpyAsync(&hc, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s) != cudaSuccess) return BLEST_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return BLEST_ERR_CUDA;
+    return hc.err ? (blest_status)hc.err : BLEST_OK;
+}
