@@ -110,24 +110,28 @@ class ClockSampler:
 
 
 def algorithmic_bytes(log, n: int, reached: int) -> float:
-    """Bytes one BFS must move, from the engine's per-level log:
-    push level: |Q| * (512 rowIds + 128 masks + 4 virtualToReal + 4 queue + 1 frontier byte);
-    lazy / bottom-up level: stage 2 reads V_curr and V_next (2 * 4 * ceil(n/32)) and writes
-    V_curr and F for changed words (8 B per new vertex, bounded by the word count);
-    bottom-up stage 1 reads V_curr (4 * ceil(n/32)) and, per unvisited vertex, its two
-    row pointers (16 B) and at least one column id (4 B);
-    plus level init (4n + 5 bitvectors) and one 4 B level write per reached vertex."""
+    """Bytes one BFS must move, from the engine's per-level log (one pass over
+    each array it touches; no credit for caching):
+      top-down level: |Q| * 649 B (512 rowIds + 128 masks + 4 virtualToReal +
+        4 queue entry + 1 frontier byte);
+      lazy / bottom-up level: stage 2 reads V_curr and V_next (8 B per 32
+        vertices) and writes V_curr and F for changed words (8 B per new vertex
+        at most); bottom-up stage 1 reads V_curr and the in-neighbour mask
+        (8 B per 32 vertices), two row pointers per probed vertex (16 B) and
+        4 B per in-neighbour id read;
+      every newly visited vertex: its level (4 B) and its degree (4 B);
+      init: 4 B per vertex of levels and 5 bitvectors (20 B per 32 vertices)."""
     W = (n + 31) // 32
-    b = 4.0 * n + 5 * 4.0 * W + 4.0 * reached
+    b = 4.0 * n + 20.0 * W + 8.0 * reached
     for i, rec in enumerate(log):
         mode = rec["mode"]
         new = log[i + 1]["frontier"] if i + 1 < len(log) else 0
         if mode in (0, 1, 2, 3):
             b += rec["queue"] * 649.0
         if mode in (2, 3, 4):
-            b += 2 * 4.0 * W + 8.0 * min(new, W)
+            b += 8.0 * W + 8.0 * min(new, W)
         if mode == 4:
-            b += 4.0 * W + 20.0 * rec["unvisited"]
+            b += 8.0 * W + 16.0 * rec.get("scanned_vertices", 0) + 4.0 * rec.get("scanned_arcs", 0)
     return b
 
 
@@ -198,6 +202,8 @@ def main():
     ap.add_argument("--impl", default="blest", choices=["blest", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sources", type=int, default=NUM_SOURCES)
+    ap.add_argument("--block", type=int, default=0, help="CTA size override (256, 512, 1024)")
+    ap.add_argument("--batch", type=int, default=0, help="VSSs in flight per warp override (1, 2, 4)")
     ap.add_argument("--levels", action="store_true", help="print the per-level log of the first source to stderr")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "blest" else args.warmup
@@ -231,6 +237,10 @@ def main():
     deg = np.diff(g.row_ptr)
     rp_d = torch.from_numpy(g.row_ptr).to(dev)
     col_d = torch.from_numpy(g.col).to(dev)
+    if args.block:
+        bopts = dict(bopts, block_threads=args.block)
+    if args.batch:
+        bopts = dict(bopts, vss_batch=args.batch)
     h = blest.build(g.n, rp_d, col_d, **bopts)
     del rp_d, col_d
     info = h.info()
@@ -329,6 +339,8 @@ def main():
                    "sources": len(srcs), "reorder": int(info["reorder"]), "lazy": int(info["lazy"]),
                    "switching": int(info["switching"]), "policy": "heuristic",
                    "udiv": info["update_divergence"], "num_vss": int(info["num_vss"]),
+                   "block_threads": int(info["block_threads"]), "grid_blocks": int(info["grid_blocks"]),
+                   "vss_batch": int(bopts.get("vss_batch", 2)),
                    "l2": "inputs larger than L2 (BVSS arrays), no flush", "parallelism": f"replicas{world}",
                    "graph_gen_s": round(gen_s, 1), "build_ms": round(info["build_ms"], 1)},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
@@ -339,6 +351,7 @@ def main():
         "gpu_launches": args.steps * len(srcs),
         "clocks": clk.summary(),
         "per_source_ms_median": float(np.median(per_source_ms)),
+        "levels_source0": [[r["mode"], r["queue"], round(r["t_ns"] / 1e3, 1)] for r in logs[0][0]],
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(g, srcs)

@@ -88,7 +88,8 @@ typedef struct blest_build_opts {
     float eta;               /* Eq. 5 constant; default 10 */
     double udiv_threshold;   /* lazy if U_div > threshold (§7.1); default 25000 */
     int32_t timeout_ms;      /* budget of each device-side wait; default 5000 */
-    int32_t block_threads;   /* CTA size of the persistent kernels; 0 = 512 */
+    int32_t block_threads;   /* CTA size of the persistent kernels: 256, 512 or 1024; 0 = 512 */
+    int32_t vss_batch;       /* VSSs a warp keeps in flight in top-down levels: 1, 2, 4; 0 = 2 */
 } blest_build_opts;
 
 /* Build-time facts about a handle. */
@@ -117,6 +118,8 @@ typedef struct blest_level_log {
     int64_t unvisited;       /* vertices not visited before this level */
     int64_t queue;           /* |Q_curr|: VSSs scheduled */
     int64_t t_ns;            /* device time of the level (globaltimer) */
+    int64_t scanned_vertices;/* bottom-up levels: unvisited vertices probed */
+    int64_t scanned_arcs;    /* bottom-up levels: in-neighbour ids read */
 } blest_level_log;
 
 /* Fill *opts with the defaults documented above. */

@@ -172,4 +172,6 @@ def permute(g, new_of_old):
     import graphgen as gg
     p = np.asarray(new_of_old, np.int64)
     src = np.repeat(np.arange(g.n), np.diff(g.row_ptr))
-    return gg.from_edges(g.n, p[src].astype(np.int32), p[g.col].astype(np.int32), symmetrize=False)
+    out = gg.from_edges(g.n, p[src].astype(np.int32), p[g.col].astype(np.int32), symmetrize=False)
+    out.directed = g.directed
+    return out

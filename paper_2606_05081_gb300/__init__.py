@@ -36,7 +36,8 @@ class BuildOpts(ctypes.Structure):
     _fields_ = [("reorder", ctypes.c_int32), ("sigma", ctypes.c_int32), ("directed", ctypes.c_int32),
                 ("jaccard_window", ctypes.c_int32), ("probe_switch", ctypes.c_int32),
                 ("engine_tc", ctypes.c_int32), ("eta", ctypes.c_float), ("udiv_threshold", ctypes.c_double),
-                ("timeout_ms", ctypes.c_int32), ("block_threads", ctypes.c_int32)]
+                ("timeout_ms", ctypes.c_int32), ("block_threads", ctypes.c_int32),
+                ("vss_batch", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -51,7 +52,8 @@ class Info(ctypes.Structure):
 class LevelLog(ctypes.Structure):
     _fields_ = [("level", ctypes.c_int32), ("mode", ctypes.c_int32), ("frontier", ctypes.c_int64),
                 ("frontier_edges", ctypes.c_int64), ("unvisited", ctypes.c_int64), ("queue", ctypes.c_int64),
-                ("t_ns", ctypes.c_int64)]
+                ("t_ns", ctypes.c_int64), ("scanned_vertices", ctypes.c_int64),
+                ("scanned_arcs", ctypes.c_int64)]
 
 
 class BvssView(ctypes.Structure):

@@ -23,7 +23,7 @@
 
 namespace {
 
-constexpr int BFS_MIN_BLOCKS = 2;
+constexpr int BFS_MAX_THREADS = 1024;
 
 struct BfsParams {
     int n, W;
@@ -34,6 +34,7 @@ struct BfsParams {
     const long long *__restrict__ rp;
     const int *__restrict__ col;
     const int *__restrict__ deg;
+    const unsigned *__restrict__ nz;  // bit u set iff u has an in-neighbour (bottom-up levels)
     int *L;
     unsigned *Vc, *Vn;
     unsigned *F[3];
@@ -48,6 +49,7 @@ struct BfsParams {
     const int *schedule;
     int sched_len;
     const float *mlp;
+    int batch;              // VSSs in flight per warp in top-down levels (1, 2, 4)
     float avg_deg;
     unsigned long long budget_ns;
     const int *new_of_old;  // non-null: out[v] = L[new_of_old[v]]
@@ -132,7 +134,11 @@ __device__ __forceinline__ void flush_counts(const BfsParams &P, int slot, unsig
 }
 
 // ---------------------------------------------------------------- push
-template <bool EAGER, bool TC>
+// Eager (Algorithm 2) or lazy (Algorithm 3 stage 1) top-down level.  A warp
+// keeps B VSSs in flight: it loads the B queue entries, then their slices
+// and masks, then their frontier bytes, before using any of them, so the
+// dependent-load chain is paid once per B VSSs.
+template <bool EAGER, bool TC, int B>
 __device__ void push_level(const BfsParams &P, int ell, int bc, int bn, int slot, int qlen, unsigned bsel) {
     const int lane = lane_id();
     const int gwarp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
@@ -141,45 +147,65 @@ __device__ void push_level(const BfsParams &P, int ell, int bc, int bn, int slot
     unsigned *Fn = P.F[bn];
     const int *Qc = P.Q[bc];
     unsigned long long nv = 0, fe = 0;
-    for (int w = gwarp; w < qlen; w += nwarps) {
-        const int vss = Qc[w];
-        const int ss = __ldg(&P.v2r[vss]);
-        const int4 r = __ldg(&P.rowIds[(size_t)vss * 32 + lane]);
-        const unsigned m = __ldg(&P.masks[(size_t)vss * 32 + lane]);
-        const unsigned alpha = ld_byte(Fc, ss);
-        const unsigned hits = TC ? hits_tc(m, alpha, bsel) : hits_cc(m, alpha);
-        if (EAGER) {
-            unsigned want = 0;
-            int sso[4] = {0, 0, 0, 0};
+    for (int w0 = gwarp * B; w0 < qlen; w0 += nwarps * B) {
+        int vss[B], ss[B];
+        int4 r[B];
+        unsigned m[B], alpha[B];
+        // lane b < B fetches queue entry w0 + b; one shuffle spreads them
+        const int mine = (lane < B && w0 + lane < qlen) ? Qc[w0 + lane] : -1;
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                if (hits >> c & 1u) {
-                    const int u = pick(r, c);
-                    const unsigned bit = 1u << (u & 31);
-                    const int wd = u >> 5;
-                    if (!(P.Vc[wd] & bit)) {
-                        const unsigned old = atomicOr(&Fn[wd], bit);
-                        if (!(old & bit)) {
-                            P.L[u] = ell;
-                            red_or(&P.Vc[wd], bit);
-                            red_or(&P.Vn[wd], bit);
-                            nv += 1;
-                            fe += (unsigned long long)__ldg(&P.deg[u]);
-                            if (((old >> (u & 24)) & 0xFFu) == 0) {
-                                want |= 1u << c;
-                                sso[c] = u >> 3;
+        for (int b = 0; b < B; ++b) vss[b] = __shfl_sync(FULL_MASK, mine, b);
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            if (vss[b] >= 0) {
+                ss[b] = __ldg(&P.v2r[vss[b]]);
+                r[b] = __ldg(&P.rowIds[(size_t)vss[b] * 32 + lane]);
+                m[b] = __ldg(&P.masks[(size_t)vss[b] * 32 + lane]);
+            } else {
+                ss[b] = 0;
+                r[b] = make_int4(0, 0, 0, 0);
+                m[b] = 0u;
+            }
+        }
+#pragma unroll
+        for (int b = 0; b < B; ++b) alpha[b] = vss[b] >= 0 ? ld_byte(Fc, ss[b]) : 0u;
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            if (vss[b] < 0) continue;   // warp-uniform
+            const unsigned hits = TC ? hits_tc(m[b], alpha[b], bsel) : hits_cc(m[b], alpha[b]);
+            if (EAGER) {
+                unsigned want = 0;
+                int sso[4] = {0, 0, 0, 0};
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    if (hits >> c & 1u) {
+                        const int u = pick(r[b], c);
+                        const unsigned bit = 1u << (u & 31);
+                        const int wd = u >> 5;
+                        if (!(P.Vc[wd] & bit)) {
+                            const unsigned old = atomicOr(&Fn[wd], bit);
+                            if (!(old & bit)) {
+                                P.L[u] = ell;
+                                red_or(&P.Vc[wd], bit);
+                                red_or(&P.Vn[wd], bit);
+                                nv += 1;
+                                fe += (unsigned long long)__ldg(&P.deg[u]);
+                                if (((old >> (u & 24)) & 0xFFu) == 0) {
+                                    want |= 1u << c;
+                                    sso[c] = u >> 3;
+                                }
                             }
                         }
                     }
                 }
-            }
-            enqueue_sets(P, want, sso, P.Q[bn], P.SQ[bn], slot);
-        } else {
+                enqueue_sets(P, want, sso, P.Q[bn], P.SQ[bn], slot);
+            } else {
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                if (hits >> c & 1u) {
-                    const int u = pick(r, c);
-                    red_or(&P.Vn[u >> 5], 1u << (u & 31));
+                for (int c = 0; c < 4; ++c) {
+                    if (hits >> c & 1u) {
+                        const int u = pick(r[b], c);
+                        red_or(&P.Vn[u >> 5], 1u << (u & 31));
+                    }
                 }
             }
         }
@@ -188,32 +214,127 @@ __device__ void push_level(const BfsParams &P, int ell, int bc, int bn, int slot
 }
 
 // ------------------------------------------------------------ bottom-up
-__device__ void bottom_up_level(const BfsParams &P, int bc) {
+// Algorithm 4 stage 1.  A warp loads 32 visited words at once (lane = word),
+// keeps only unvisited vertices that have in-neighbours (nz mask), and then
+// walks the compacted list 32 vertices at a time (lane = vertex).  Each lane
+// probes its in-neighbours four at a time: four column loads, then four
+// frontier-bit loads, then the test.  Found bits collect in shared memory
+// and each word's V_next is written once by the warp that owns it.
+__device__ __forceinline__ int nth_set_bit(unsigned x, int k) {
+    // position of the k-th (0-based) set bit of x
+    int pos = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+        const unsigned lo = x & ((1u << step) - 1u);
+        const int c = __popc(lo);
+        if (k >= c) { k -= c; x >>= step; pos += step; }
+        else x = lo;
+    }
+    return pos;
+}
+
+__device__ void bottom_up_level(const BfsParams &P, int bc, int slot, unsigned *s_found) {
     const int lane = lane_id();
     const int gwarp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
+    unsigned *found = s_found + (threadIdx.x >> 5) * 32;
     const unsigned *Fc = P.F[bc];
     const int tail = P.n & 31;
-    for (int w = gwarp; w < P.W; w += nwarps) {
-        const unsigned vis = P.Vc[w];
-        unsigned unv = ~vis;
-        if (w == P.W - 1 && tail) unv &= (1u << tail) - 1u;
-        if (unv == 0) continue;
-        bool found = false;
-        if (unv >> lane & 1u) {
-            const int u = (w << 5) + lane;
-            const long long e = __ldg(&P.rp[u + 1]);
-            for (long long p = __ldg(&P.rp[u]); p < e; ++p) {
-                const int v = __ldg(&P.col[p]);
-                if (Fc[v >> 5] >> (v & 31) & 1u) { found = true; break; }
+    unsigned long long sv = 0, sa = 0;
+    for (int base = gwarp * 32; base < P.W; base += nwarps * 32) {
+        const int w = base + lane;
+        unsigned vis = 0u, unv = 0u;
+        if (w < P.W) {
+            vis = P.Vc[w];
+            unv = ~vis & __ldg(&P.nz[w]);
+            if (w == P.W - 1 && tail) unv &= (1u << tail) - 1u;
+        }
+        found[lane] = 0u;
+        const int cnt = __popc(unv);
+        const int incl = warp_incl_scan(cnt);
+        const int total = __shfl_sync(FULL_MASK, incl, 31);
+        const int excl = incl - cnt;
+        __syncwarp();
+        // two compacted vertices per lane per round: idx = b + lane and b + 32 + lane
+        for (int b = 0; b < total; b += 64) {
+            int u[2];
+            long long p[2], e[2];
+            bool act[2], hit[2];
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const int idx = b + 32 * k + lane;
+                act[k] = idx < total;
+                hit[k] = false;
+                // owner lane: the largest lane whose exclusive prefix is <= idx (a lane with
+                // cnt == 0 shares its prefix with the next lane, so the largest one owns idx)
+                int j = 0;
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1) {
+                    const int ex = __shfl_sync(FULL_MASK, excl, j + step);
+                    if (idx >= ex) j += step;
+                }
+                const unsigned uj = __shfl_sync(FULL_MASK, unv, j);
+                const int ej = __shfl_sync(FULL_MASK, excl, j);
+                u[k] = act[k] ? ((base + j) << 5) + nth_set_bit(uj, idx - ej) : 0;
+            }
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                p[k] = act[k] ? __ldg(&P.rp[u[k]]) : 0;
+                e[k] = act[k] ? __ldg(&P.rp[u[k] + 1]) : 0;
+                if (act[k]) sv += 1;
+            }
+            // first probe round of both vertices together, then the rare longer scans
+            int v[2][4];
+            unsigned fw[2][4];
+#pragma unroll
+            for (int k = 0; k < 2; ++k)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) v[k][q] = (p[k] + q < e[k]) ? __ldg(&P.col[p[k] + q]) : -1;
+#pragma unroll
+            for (int k = 0; k < 2; ++k)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) fw[k][q] = v[k][q] >= 0 ? Fc[v[k][q] >> 5] : 0u;
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                sa += (unsigned long long)((e[k] - p[k]) < 4 ? (e[k] - p[k] > 0 ? e[k] - p[k] : 0) : 4);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) hit[k] |= (v[k][q] >= 0) && ((fw[k][q] >> (v[k][q] & 31)) & 1u);
+                p[k] += 4;
+            }
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                while (act[k] && !hit[k] && p[k] < e[k]) {
+                    sa += (unsigned long long)((e[k] - p[k]) < 4 ? (e[k] - p[k]) : 4);
+                    int w4[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) w4[q] = (p[k] + q < e[k]) ? __ldg(&P.col[p[k] + q]) : -1;
+                    unsigned f4[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) f4[q] = w4[q] >= 0 ? Fc[w4[q] >> 5] : 0u;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) hit[k] |= (w4[q] >= 0) && ((f4[q] >> (w4[q] & 31)) & 1u);
+                    p[k] += 4;
+                }
+                if (act[k] && hit[k]) atomicOr(&found[(u[k] >> 5) - base], 1u << (u[k] & 31));
             }
         }
-        const unsigned bal = __ballot_sync(FULL_MASK, found);
-        if (lane == 0 && bal) P.Vn[w] = vis | bal;  // this warp owns word w in this phase
+        __syncwarp();
+        const unsigned f = found[lane];
+        if (f) P.Vn[w] = vis | f;   // this warp owns word w in this phase
+        __syncwarp();
+    }
+    sv = warp_sum(sv);
+    sa = warp_sum(sa);
+    if (lane == 0 && sv) {
+        red_add_u64(&P.ctl->scan_v[slot], sv);
+        red_add_u64(&P.ctl->scan_a[slot], sa);
     }
 }
 
 // --------------------------------------------------- stage 2 (finalize)
+// Algorithm 3 stage 2.  Lane = word for the V_curr / V_next sweep and the
+// F writes; then, word by word over the words that changed, lane = vertex
+// for the level stores and degree loads, so both are coalesced.
 __device__ void finalize_level(const BfsParams &P, int ell, int bn, int slot) {
     const int lane = lane_id();
     const int gwarp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
@@ -230,15 +351,27 @@ __device__ void finalize_level(const BfsParams &P, int ell, int bn, int slot) {
             if (diff) {
                 P.Vc[t] = next;
                 Fn[t] = diff;
-                unsigned d = diff;
-                while (d) {
-                    const int b = __ffs(d) - 1;
-                    d &= d - 1;
-                    const int u = (t << 5) + b;
-                    P.L[u] = ell;
-                    fe += (unsigned long long)__ldg(&P.deg[u]);
-                }
                 nv += (unsigned long long)__popc(diff);
+            }
+        }
+        const unsigned changed = __ballot_sync(FULL_MASK, diff != 0);
+        if (changed) {
+            // eight words per round: their degree loads are independent and in flight together
+#pragma unroll 1
+            for (int j0 = 0; j0 < 32; j0 += 8) {
+                if (!((changed >> j0) & 0xFFu)) continue;   // warp-uniform
+                unsigned long long d8 = 0;
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const int j = j0 + k;
+                    const unsigned dj = __shfl_sync(FULL_MASK, diff, j);
+                    if (dj >> lane & 1u) {
+                        const int u = ((base + j) << 5) + lane;
+                        P.L[u] = ell;
+                        d8 += (unsigned long long)__ldg(&P.deg[u]);
+                    }
+                }
+                fe += d8;
             }
         }
         unsigned want = 0;
@@ -276,7 +409,22 @@ __device__ __forceinline__ int decide_mode(const BfsParams &P, int ell, long lon
     return mode;
 }
 
-__global__ void __launch_bounds__(512, BFS_MIN_BLOCKS) k_bfs(BfsParams P) {
+template <bool EAGER>
+__device__ __forceinline__ void push_dispatch(const BfsParams &P, bool tc, int ell, int bc, int bn, int sn, int qlen,
+                                              unsigned bsel) {
+    if (tc) {
+        if (P.batch >= 4) push_level<EAGER, true, 4>(P, ell, bc, bn, sn, qlen, bsel);
+        else if (P.batch == 2) push_level<EAGER, true, 2>(P, ell, bc, bn, sn, qlen, bsel);
+        else push_level<EAGER, true, 1>(P, ell, bc, bn, sn, qlen, bsel);
+    } else {
+        if (P.batch >= 4) push_level<EAGER, false, 4>(P, ell, bc, bn, sn, qlen, bsel);
+        else if (P.batch == 2) push_level<EAGER, false, 2>(P, ell, bc, bn, sn, qlen, bsel);
+        else push_level<EAGER, false, 1>(P, ell, bc, bn, sn, qlen, bsel);
+    }
+}
+
+__global__ void __launch_bounds__(BFS_MAX_THREADS, 1) k_bfs(BfsParams P) {
+    __shared__ unsigned s_found[BFS_MAX_THREADS];
     const int tid = (int)(blockIdx.x * blockDim.x + threadIdx.x);
     const int nthreads = (int)(gridDim.x * blockDim.x);
     const int lane = lane_id();
@@ -323,7 +471,11 @@ __global__ void __launch_bounds__(512, BFS_MIN_BLOCKS) k_bfs(BfsParams P) {
         const long long unvisited = (long long)P.n - visited;
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             const long long t = (long long)global_ns();
-            if (ell >= 2 && ell - 2 < P.log_cap) P.log[ell - 2].t_ns = t - P.log[ell - 2].t_ns;
+            if (ell >= 2 && ell - 2 < P.log_cap) {
+                P.log[ell - 2].t_ns = t - P.log[ell - 2].t_ns;
+                P.log[ell - 2].scanned_vertices = (long long)*(volatile unsigned long long *)&ctl->scan_v[sc];
+                P.log[ell - 2].scanned_arcs = (long long)*(volatile unsigned long long *)&ctl->scan_a[sc];
+            }
             if (qlen > 0 && ell - 1 < P.log_cap) {
                 blest_level_log rec;
                 rec.level = ell;
@@ -333,6 +485,8 @@ __global__ void __launch_bounds__(512, BFS_MIN_BLOCKS) k_bfs(BfsParams P) {
                 rec.unvisited = unvisited;
                 rec.queue = qlen;
                 rec.t_ns = t;
+                rec.scanned_vertices = 0;
+                rec.scanned_arcs = 0;
                 P.log[ell - 1] = rec;
             }
         }
@@ -357,21 +511,18 @@ __global__ void __launch_bounds__(512, BFS_MIN_BLOCKS) k_bfs(BfsParams P) {
             ctl->sqlen[sz] = 0;
             ctl->newv[sz] = 0;
             ctl->fedges[sz] = 0;
+            ctl->scan_v[sz] = 0;
+            ctl->scan_a[sz] = 0;
         }
 
         if (mode == BLEST_MODE_PUSH_EAGER_CC || mode == BLEST_MODE_PUSH_EAGER_TC) {
-            if (mode == BLEST_MODE_PUSH_EAGER_TC)
-                push_level<true, true>(P, ell, bc, bn, sn, qlen, bsel);
-            else
-                push_level<true, false>(P, ell, bc, bn, sn, qlen, bsel);
+            push_dispatch<true>(P, mode == BLEST_MODE_PUSH_EAGER_TC, ell, bc, bn, sn, qlen, bsel);
             if (!grid_barrier(ctl, epoch, P.budget_ns)) return;
         } else {
-            if (mode == BLEST_MODE_PUSH_LAZY_TC)
-                push_level<false, true>(P, ell, bc, bn, sn, qlen, bsel);
-            else if (mode == BLEST_MODE_PUSH_LAZY_CC)
-                push_level<false, false>(P, ell, bc, bn, sn, qlen, bsel);
+            if (mode == BLEST_MODE_BOTTOM_UP)
+                bottom_up_level(P, bc, sn, s_found);
             else
-                bottom_up_level(P, bc);
+                push_dispatch<false>(P, mode == BLEST_MODE_PUSH_LAZY_TC, ell, bc, bn, sn, qlen, bsel);
             if (!grid_barrier(ctl, epoch, P.budget_ns)) return;
             finalize_level(P, ell, bn, sn);
             if (!grid_barrier(ctl, epoch, P.budget_ns)) return;
@@ -396,6 +547,20 @@ int bfs_grid_for(int block, int *num_sms) {
     return per_sm * sms;
 }
 
+// nz[w] bit b set iff vertex 32w+b has an in-neighbour (a nonempty row of
+// the in-neighbour CSR); bottom-up levels never probe the others.
+__global__ void k_nz_mask(const long long *__restrict__ rp, int n, int W, unsigned *nz) {
+    const int stride = gridDim.x * blockDim.x;
+    for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < W; w += stride) {
+        unsigned m = 0;
+        for (int b = 0; b < 32; ++b) {
+            const int u = (w << 5) + b;
+            if (u < n && rp[u + 1] > rp[u]) m |= 1u << b;
+        }
+        nz[w] = m;
+    }
+}
+
 blest_status bfs_prepare(blest_graph *h) {
     const int64_t n = h->n;
     const int64_t W = (n + 31) / 32;
@@ -409,6 +574,10 @@ blest_status bfs_prepare(blest_graph *h) {
         if ((bs = dev_alloc_t(h, &h->w.SQ[i], (size_t)h->Ns + 1)) != BLEST_OK) return bs;
     }
     if ((bs = dev_alloc_t(h, &h->w.ctl, 1)) != BLEST_OK) return bs;
+    if ((bs = dev_alloc_t(h, &h->g.nz, (size_t)W + 1)) != BLEST_OK) return bs;
+    k_nz_mask<<<(unsigned)((W + 255) / 256 < 65535 ? (W + 255) / 256 : 65535), 256, 0, h->stream>>>(
+        h->g.rp, (int)n, (int)W, h->g.nz);
+    if (cudaGetLastError() != cudaSuccess) return BLEST_ERR_CUDA;
     h->w.log_cap = 1 << 16;
     if ((bs = dev_alloc_t(h, &h->w.log, (size_t)h->w.log_cap)) != BLEST_OK) return bs;
     if (h->g.new_of_old)
@@ -452,6 +621,8 @@ blest_status bfs_run(blest_graph *h, int32_t source, int32_t *dev_out) {
     P.schedule = h->d_schedule;
     P.sched_len = h->sched_len;
     P.mlp = h->d_mlp;
+    P.nz = h->g.nz;
+    P.batch = h->vss_batch;
     P.avg_deg = h->n ? (float)((double)h->nnz / (double)h->n) : 0.f;
     P.budget_ns = (unsigned long long)h->timeout_ms * 1000000ull;
     P.src = source;

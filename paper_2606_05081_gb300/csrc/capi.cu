@@ -66,6 +66,7 @@ extern "C" void blest_default_opts(blest_build_opts *o) {
     o->udiv_threshold = 25000.0;
     o->timeout_ms = 5000;
     o->block_threads = 512;
+    o->vss_batch = 2;
 }
 
 static blest_status finish_call(blest_graph *h, bool must_sync) {
@@ -139,7 +140,9 @@ extern "C" blest_status blest_build(int64_t n, const int64_t *row_ptr, const int
     if (o.sigma == 0) o.sigma = 8;
     if (o.sigma != 8) return BLEST_ERR_UNSUPPORTED;
     if (o.block_threads == 0) o.block_threads = 512;
-    if (o.block_threads != 128 && o.block_threads != 256 && o.block_threads != 512) return BLEST_ERR_INVALID;
+    if (o.block_threads != 256 && o.block_threads != 512 && o.block_threads != 1024) return BLEST_ERR_INVALID;
+    if (o.vss_batch == 0) o.vss_batch = 2;
+    if (o.vss_batch != 1 && o.vss_batch != 2 && o.vss_batch != 4) return BLEST_ERR_INVALID;
     if (o.timeout_ms <= 0) o.timeout_ms = 5000;
     if (o.reorder < 0 || o.reorder > BLEST_REORDER_AUTO) return BLEST_ERR_INVALID;
     if (o.jaccard_window <= 0) o.jaccard_window = 65536;
@@ -154,6 +157,7 @@ extern "C" blest_status blest_build(int64_t n, const int64_t *row_ptr, const int
     h->udiv_threshold = o.udiv_threshold;
     h->timeout_ms = o.timeout_ms;
     h->block = o.block_threads;
+    h->vss_batch = o.vss_batch;
     h->fixed_mode = h->engine_tc ? BLEST_MODE_PUSH_EAGER_TC : BLEST_MODE_PUSH_EAGER_CC;
     cudaError_t e = cudaGetDevice(&h->device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking);

@@ -76,6 +76,8 @@ struct Ctl {
     int sqlen[4];          // slice-set queue length per level slot
     unsigned long long newv[4];    // vertices discovered per level slot
     unsigned long long fedges[4];  // out-arcs of those vertices
+    unsigned long long scan_v[4];  // bottom-up: vertices probed
+    unsigned long long scan_a[4];  // bottom-up: in-neighbour ids read
 };
 
 // Timed-out grid barrier for a cooperative launch.  Every block calls it the

@@ -19,6 +19,7 @@ struct DevGraph {
     long long *rp = nullptr;   // n + 1
     int *col = nullptr;
     int *deg = nullptr;        // out-degree in the reordered id space (features, TEPS)
+    unsigned *nz = nullptr;    // bit u set iff u has an in-neighbour (bottom-up skips the rest)
     // permutation (nullptr when no reordering): new_of_old, old_of_new
     int *new_of_old = nullptr;
     int *old_of_new = nullptr;
@@ -50,6 +51,7 @@ struct blest_graph {
     double udiv = 0.0;
     int lazy = 0, switching = 0;
     int engine_tc = 1;
+    int vss_batch = 2;
     float eta = 10.f;
     double udiv_threshold = 25000.0;
     int timeout_ms = 5000;
