@@ -202,6 +202,7 @@ def main():
     ap.add_argument("--impl", default="blest", choices=["blest", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sources", type=int, default=NUM_SOURCES)
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-policy arm")
     ap.add_argument("--block", type=int, default=0, help="CTA size override (256, 512, 1024)")
     ap.add_argument("--batch", type=int, default=0, help="VSSs in flight per warp override (1, 2, 4)")
     ap.add_argument("--levels", action="store_true", help="print the per-level log of the first source to stderr")
@@ -276,15 +277,20 @@ def main():
             if record:
                 ends[i].record(stream)
 
-    for _ in range(args.warmup):
-        step(False)
-    h.sync()
-    torch.cuda.synchronize()
-    per_source_ms = np.zeros((args.steps, len(srcs)))
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
+    def measure(policy, engine_tc):
+        """Warm-up, then the timed steps under one level-mode policy; returns
+        per-source device ms [steps, sources], the timed region's ms and the
+        per-source level logs of the policy."""
+        h.set_engine(engine_tc)
+        h.set_policy(policy)
+        for _ in range(args.warmup):
+            step(False)
+        h.sync()
+        torch.cuda.synchronize()
+        psm = np.zeros((args.steps, len(srcs)))
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
         t_start = torch.cuda.Event(enable_timing=True)
         t_end = torch.cuda.Event(enable_timing=True)
         t_start.record(stream)
@@ -292,31 +298,56 @@ def main():
             step(True)
             torch.cuda.synchronize()
             for i in range(len(srcs)):
-                per_source_ms[k, i] = starts[i].elapsed_time(ends[i])
+                psm[k, i] = starts[i].elapsed_time(ends[i])
         t_end.record(stream)
         torch.cuda.synchronize()
-    h.sync()
-    if dist:
-        dist.barrier()
-    total_ms = t_start.elapsed_time(t_end)
-    if dist:
-        tt = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
+        h.sync()
+        if dist:
+            dist.barrier()
+        tot = t_start.elapsed_time(t_end)
+        if dist:
+            tt = torch.tensor([tot], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            tot = float(tt.item())
+        plogs = []
+        for s_ in srcs:
+            h.bfs(int(s_), out)
+            h.sync()
+            plogs.append(h.level_log())
+        return psm, tot, plogs
 
-    rates = (np.asarray(edges)[None, :] / (per_source_ms * 1e-3)) / 1e9
-    hmean = harmonic(rates.ravel())
-    value = hmean
-    if dist:
-        vt = torch.tensor([hmean], device=dev, dtype=torch.float64)
-        dist.all_reduce(vt)
-        value = float(vt.item())
+    def gteps(psm):
+        rates = (np.asarray(edges)[None, :] / (psm * 1e-3)) / 1e9
+        v = harmonic(rates.ravel())
+        if dist:
+            vt = torch.tensor([v], device=dev, dtype=torch.float64)
+            dist.all_reduce(vt)
+            v = float(vt.item())
+        return v
 
-    # roofline of the persistent BFS kernel
+    from paper_2606_05081_gb300 import switch
+    weights = switch.load_weights()
+    policies = [("plain_tc", blest.POLICY_HEURISTIC, True), ("heuristic_cc", blest.POLICY_HEURISTIC, False)]
+    if weights is not None and not args.no_learned:
+        h.load_model(weights)
+        policies.append(("learned", blest.POLICY_LEARNED, False))
+    results = {}
+    with ClockSampler(local) as clk:
+        for name, pol, tc in policies:
+            results[name] = measure(pol, tc)
+    head = "learned" if "learned" in results else "heuristic_cc"
+    per_source_ms, total_ms, head_logs = results[head]
+    value = gteps(per_source_ms)
+    variants = {name: {"gteps": gteps(r[0]), "per_source_ms_median": float(np.median(r[0])),
+                       "ms_per_step": r[1] / args.steps} for name, r in results.items()}
+
+    # roofline of the persistent BFS kernel under the headline policy
     hbm, peak_kind = peaks()
     mean_ms = per_source_ms.mean(axis=0)
-    alg = np.array([algorithmic_bytes(lg, g.n, r) for lg, r in logs])
+    reached = [lg_r for _, lg_r in logs]
+    alg = np.array([algorithmic_bytes(lg, g.n, r) for lg, r in zip(head_logs, reached)])
     achieved = float(np.sum(alg) / np.sum(mean_ms * 1e-3) / 1e9)
+    logs = [(lg, r) for lg, r in zip(head_logs, reached)]
 
     # end to end through the C ABI with host buffers (synchronous calls)
     h.set_stream(None, False)
@@ -337,7 +368,7 @@ def main():
         "vs_baseline": None, "dtype": "int32", "data": "synthetic",
         "config": {"workload": args.workload, "graph": desc, "n": g.n, "nnz": int(info["nnz"]),
                    "sources": len(srcs), "reorder": int(info["reorder"]), "lazy": int(info["lazy"]),
-                   "switching": int(info["switching"]), "policy": "heuristic",
+                   "switching": int(info["switching"]), "policy": head,
                    "udiv": info["update_divergence"], "num_vss": int(info["num_vss"]),
                    "block_threads": int(info["block_threads"]), "grid_blocks": int(info["grid_blocks"]),
                    "vss_batch": int(bopts.get("vss_batch", 2)),
@@ -348,7 +379,8 @@ def main():
                      "kernel": "k_bfs (persistent, all levels)"},
         "e2e": {"value": e2e, "unit": "GTEPS", "h2d_bytes_per_step": 4 * len(srcs),
                 "d2h_bytes_per_step": 4 * g.n * len(srcs)},
-        "gpu_launches": args.steps * len(srcs),
+        "gpu_launches": args.steps * len(srcs) * len(results),
+        "variants": variants,
         "clocks": clk.summary(),
         "per_source_ms_median": float(np.median(per_source_ms)),
         "levels_source0": [[r["mode"], r["queue"], round(r["t_ns"] / 1e3, 1)] for r in logs[0][0]],

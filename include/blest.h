@@ -84,7 +84,8 @@ typedef struct blest_build_opts {
     int32_t directed;        /* 0: CSR is symmetric (undirected); 1: directed */
     int32_t jaccard_window;  /* W of Algorithm 1; default 65536, multiple of sigma */
     int32_t probe_switch;    /* 1 (default): the 3-source switching probe of §7.1 runs at build */
-    int32_t engine_tc;       /* 1 (default): top-down levels use the b1 MMA; 0: CUDA cores */
+    int32_t engine_tc;       /* top-down hit test: 1 = b1 MMA (Fig. 3 layout), 0 (default) = CUDA
+                                cores (measured faster on GB300) */
     float eta;               /* Eq. 5 constant; default 10 */
     double udiv_threshold;   /* lazy if U_div > threshold (§7.1); default 25000 */
     int32_t timeout_ms;      /* budget of each device-side wait; default 5000 */
@@ -172,6 +173,10 @@ blest_status blest_bfs_many(blest_handle h, const int32_t *sources, int32_t *lev
 /* Choose the per-level policy.  fixed_mode is used by BLEST_POLICY_FIXED. */
 blest_status blest_set_policy(blest_handle h, int32_t policy, int32_t fixed_mode);
 
+/* Hit-test engine of the heuristic policy's top-down levels: 1 = b1 MMA
+ * (Fig. 3 layout, the paper's), 0 = CUDA cores. */
+blest_status blest_set_engine(blest_handle h, int32_t tc);
+
 /* Per-level modes for BLEST_POLICY_SCHEDULE: level l (1-based) runs
  * modes[(l-1) % len].  Copied. */
 blest_status blest_set_schedule(blest_handle h, const int32_t *modes, int32_t len);
@@ -208,6 +213,39 @@ blest_status blest_sync(blest_handle h);
 void blest_destroy(blest_handle h);
 
 const char *blest_status_string(blest_status s);
+
+/* ---- Learned level-mode policy (replaces the hand-set rule of §5.3 / §7.1)
+ * A 3-layer MLP (6 -> 32 -> 32 -> 5, tanh, fp32) predicts the log device
+ * time of each BLEST_MODE_* from six per-level features; BLEST_POLICY_LEARNED
+ * runs the mode with the smallest prediction.  Weights: BLEST_MLP_NW floats,
+ * [0,6) feature means, [6,12) feature 1/std, then W1[32][6], b1[32],
+ * W2[32][32], b2[32], W3[5][32], b3[5].  All arrays below may be host or
+ * device memory and are row-major (one sample per row). */
+#define BLEST_MLP_NW 1457
+
+/* Raw features of level-log records, exactly as the BFS kernel computes
+ * them: out[n*6] = log1p of (frontier, frontier_edges, unvisited, 128*queue,
+ * level, avg_deg). */
+blest_status blest_mlp_features(const blest_level_log *recs, int64_t n, float avg_deg, float *out);
+
+/* Masked mean squared error of the predictions against targets (n*5 log
+ * times, mask 1 = observed) and its gradient (BLEST_MLP_NW floats; the
+ * normalisation entries get 0). */
+blest_status blest_mlp_loss_grad(const float *features, const float *targets, const float *mask, int64_t n,
+                                 const float *weights, float *loss, float *grad);
+
+/* Full-batch Adam training on the device, deterministic.  weight_decay adds
+ * (weight_decay/2)|w|^2 over the trainable entries to the loss.  weights:
+ * in = initial values (normalisation entries included, never updated), out
+ * = trained.  loss_out: the data loss before each of the `epochs` steps, may
+ * be NULL.  The mask entries weight the squared errors (0 = unobserved). */
+blest_status blest_mlp_train(const float *features, const float *targets, const float *mask, int64_t n,
+                             int32_t epochs, float lr, float weight_decay, float *weights, float *loss_out);
+
+/* Predictions (n*5, may be NULL) and chosen modes (n, may be NULL) with the
+ * in-kernel inference routine. */
+blest_status blest_mlp_predict(const float *weights, const float *features, int64_t n, float *pred,
+                               int32_t *choice);
 
 /* ---- Allocation-free BFS ------------------------------------------------
  * The paper has no counterpart to this entry point.  It serves callers that

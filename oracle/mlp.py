@@ -91,8 +91,12 @@ def loss_and_grad(w, raw, target, mask):
     return loss, g
 
 
-def adam_step(w, g, m, v, t, lr=1e-2, b1=0.9, b2=0.999, eps=1e-8):
-    """One Adam step (t counts from 1); normalisation entries are frozen."""
+def adam_step(w, g, m, v, t, lr=1e-2, b1=0.9, b2=0.999, eps=1e-8, wd=0.0):
+    """One Adam step (t counts from 1); normalisation entries are frozen.
+    wd adds an L2 penalty (wd/2)|w|^2 of the trainable entries to the loss,
+    i.e. wd * w to their gradient."""
+    g = np.asarray(g, np.float64).copy()
+    g[OFF_W1:] += wd * np.asarray(w, np.float64)[OFF_W1:]
     m = b1 * m + (1 - b1) * g
     v = b2 * v + (1 - b2) * g * g
     mh = m / (1 - b1 ** t)

@@ -78,6 +78,7 @@ _sigs = {
     "blest_bfs_many": (_S, [_H, _P, _P]),
     "blest_set_policy": (_S, [_H, ctypes.c_int32, ctypes.c_int32]),
     "blest_set_schedule": (_S, [_H, _P, ctypes.c_int32]),
+    "blest_set_engine": (_S, [_H, ctypes.c_int32]),
     "blest_load_model": (_S, [_H, _P, ctypes.c_int32]),
     "blest_last_timings": (_S, [_H, _P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
     "blest_get_info": (_S, [_H, ctypes.POINTER(Info)]),
@@ -89,6 +90,10 @@ _sigs = {
     "blest_status_string": (ctypes.c_char_p, [_S]),
     "blest_selftest_barrier_timeout": (_S, [ctypes.c_int32]),
     "blest_bfs_noalloc": (_S, [ctypes.POINTER(BvssView), ctypes.c_int32, _P, _P]),
+    "blest_mlp_features": (_S, [_P, ctypes.c_int64, ctypes.c_float, _P]),
+    "blest_mlp_loss_grad": (_S, [_P, _P, _P, ctypes.c_int64, _P, _P, _P]),
+    "blest_mlp_train": (_S, [_P, _P, _P, ctypes.c_int64, ctypes.c_int32, ctypes.c_float, ctypes.c_float, _P, _P]),
+    "blest_mlp_predict": (_S, [_P, _P, ctypes.c_int64, _P, _P]),
     "blest_last_cuda_error": (ctypes.c_char_p, []),
 }
 for _name, (_res, _args) in _sigs.items():
@@ -221,6 +226,9 @@ class Graph:
     def set_policy(self, policy: int, fixed_mode: int = 0):
         _check(_lib.blest_set_policy(self._h, policy, fixed_mode), "blest_set_policy")
 
+    def set_engine(self, tc: bool):
+        _check(_lib.blest_set_engine(self._h, int(bool(tc))), "blest_set_engine")
+
     def set_schedule(self, modes):
         m = np.ascontiguousarray(modes, dtype=np.int32)
         _check(_lib.blest_set_schedule(self._h, m.ctypes.data, len(m)), "blest_set_schedule")
@@ -303,3 +311,50 @@ def bfs_noalloc(view: BvssView, source: int, levels, stream=None):
     levels must be a CUDA int32 tensor of view.n elements."""
     _check(_lib.blest_bfs_noalloc(ctypes.byref(view), int(source), _ptr(levels), stream), "blest_bfs_noalloc")
     return levels
+
+
+# ------------------------------------------------------------- learned policy
+def _f32(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    if shape is not None:
+        a = a.reshape(shape)
+    return a
+
+
+def mlp_features(records, avg_deg: float) -> np.ndarray:
+    """Raw features (n, 6) of level-log records, computed by the device."""
+    n = len(records)
+    buf = (LevelLog * n)()
+    for i, r in enumerate(records):
+        for f, _ in LevelLog._fields_:
+            setattr(buf[i], f, int(r[f]))
+    out = np.empty((n, 6), np.float32)
+    _check(_lib.blest_mlp_features(buf, n, float(avg_deg), out.ctypes.data), "blest_mlp_features")
+    return out
+
+
+def mlp_loss_grad(features, targets, mask, weights):
+    X, T, M, W = _f32(features), _f32(targets), _f32(mask), _f32(weights)
+    loss = ctypes.c_float(0)
+    g = np.empty(MLP_NW, np.float32)
+    _check(_lib.blest_mlp_loss_grad(X.ctypes.data, T.ctypes.data, M.ctypes.data, len(X), W.ctypes.data,
+                                    ctypes.byref(loss), g.ctypes.data), "blest_mlp_loss_grad")
+    return float(loss.value), g
+
+
+def mlp_train(features, targets, mask, weights, epochs: int = 2000, lr: float = 1e-2, weight_decay: float = 0.0):
+    X, T, M = _f32(features), _f32(targets), _f32(mask)
+    W = _f32(weights).copy()
+    hist = np.empty(epochs, np.float32)
+    _check(_lib.blest_mlp_train(X.ctypes.data, T.ctypes.data, M.ctypes.data, len(X), int(epochs), float(lr),
+                                float(weight_decay), W.ctypes.data, hist.ctypes.data), "blest_mlp_train")
+    return W, hist
+
+
+def mlp_predict(weights, features):
+    W, X = _f32(weights), _f32(features)
+    pred = np.empty((len(X), 5), np.float32)
+    ch = np.empty(len(X), np.int32)
+    _check(_lib.blest_mlp_predict(W.ctypes.data, X.ctypes.data, len(X), pred.ctypes.data, ch.ctypes.data),
+           "blest_mlp_predict")
+    return pred, ch

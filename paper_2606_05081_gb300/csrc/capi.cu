@@ -61,7 +61,7 @@ extern "C" void blest_default_opts(blest_build_opts *o) {
     o->directed = 0;
     o->jaccard_window = 65536;
     o->probe_switch = 1;
-    o->engine_tc = 1;
+    o->engine_tc = 0;
     o->eta = 10.f;
     o->udiv_threshold = 25000.0;
     o->timeout_ms = 5000;
@@ -223,6 +223,12 @@ extern "C" blest_status blest_set_policy(blest_handle h, int32_t policy, int32_t
     if (policy == BLEST_POLICY_LEARNED && !h->d_mlp) return BLEST_ERR_INVALID;
     h->policy = policy;
     if (policy == BLEST_POLICY_FIXED) h->fixed_mode = fixed_mode;
+    return BLEST_OK;
+}
+
+extern "C" blest_status blest_set_engine(blest_handle h, int32_t tc) {
+    if (!h || (tc != 0 && tc != 1)) return BLEST_ERR_INVALID;
+    h->engine_tc = tc;
     return BLEST_OK;
 }
 

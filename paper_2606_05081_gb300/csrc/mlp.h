@@ -37,15 +37,14 @@ __host__ __device__ inline void mlp_raw_features(float *x, long long frontier, l
     x[5] = log1pf(avg_deg);
 }
 
-// Called by all 32 lanes of one warp; every lane returns the chosen mode.
-// Lane h owns hidden unit h of both layers.
-__device__ __forceinline__ int mlp_choose_warp(const float *__restrict__ w, long long frontier, long long fedges,
-                                               long long unvisited, long long qlen, int level, float avg_deg) {
+// Warp-cooperative forward pass on raw features x (all 32 lanes call it;
+// lane h owns hidden unit h of both layers).  Lane o < MLP_OUT returns the
+// prediction for mode o (other lanes return 0).
+__device__ __forceinline__ float mlp_forward_warp(const float *__restrict__ w, const float *xr) {
     const int lane = threadIdx.x & 31;
     float x[MLP_IN];
-    mlp_raw_features(x, frontier, fedges, unvisited, qlen, level, avg_deg);
 #pragma unroll
-    for (int i = 0; i < MLP_IN; ++i) x[i] = (x[i] - w[MLP_OFF_MEAN + i]) * w[MLP_OFF_ISTD + i];
+    for (int i = 0; i < MLP_IN; ++i) x[i] = (xr[i] - w[MLP_OFF_MEAN + i]) * w[MLP_OFF_ISTD + i];
     float a1 = w[MLP_OFF_B1 + lane];
 #pragma unroll
     for (int i = 0; i < MLP_IN; ++i) a1 = fmaf(w[MLP_OFF_W1 + lane * MLP_IN + i], x[i], a1);
@@ -61,7 +60,11 @@ __device__ __forceinline__ int mlp_choose_warp(const float *__restrict__ w, long
         const float hk = __shfl_sync(0xFFFFFFFFu, h2, k);
         if (lane < MLP_OUT) y = fmaf(w[MLP_OFF_W3 + lane * MLP_H + k], hk, y);
     }
-    // argmin over the MLP_OUT predictions (lowest index on ties)
+    return y;
+}
+
+// argmin over the MLP_OUT predictions (lowest index on ties); all lanes get it
+__device__ __forceinline__ int mlp_argmin_warp(float y) {
     float best = __shfl_sync(0xFFFFFFFFu, y, 0);
     int arg = 0;
 #pragma unroll
@@ -70,4 +73,12 @@ __device__ __forceinline__ int mlp_choose_warp(const float *__restrict__ w, long
         if (v < best) { best = v; arg = o; }
     }
     return arg;
+}
+
+// Called by all 32 lanes of one warp; every lane returns the chosen mode.
+__device__ __forceinline__ int mlp_choose_warp(const float *__restrict__ w, long long frontier, long long fedges,
+                                               long long unvisited, long long qlen, int level, float avg_deg) {
+    float x[MLP_IN];
+    mlp_raw_features(x, frontier, fedges, unvisited, qlen, level, avg_deg);
+    return mlp_argmin_warp(mlp_forward_warp(w, x));
 }

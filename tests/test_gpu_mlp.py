@@ -1,0 +1,122 @@
+"""The learned level-mode policy on the GPU: the device forward/backward
+against the fp64 oracle, deterministic training, the in-kernel decisions
+against the same network evaluated outside the BFS, levels exact whatever
+the network picks, and the gain of a trained network over the paper's rule
+on held-out graphs."""
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+from oracle import mlp as omlp
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def blest():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2606_05081_gb300 as b
+    return b
+
+
+def _data(n=500, seed=1):
+    rs = np.random.RandomState(seed)
+    X = rs.uniform(0, 16, (n, 6)).astype(np.float32)
+    Y = (rs.normal(10, 1.5, (n, 5)) + 0.2 * X[:, :1]).astype(np.float32)
+    M = (rs.uniform(size=(n, 5)) > 0.1).astype(np.float32)
+    return X, Y, M
+
+
+def test_loss_and_gradient_match_fp64_oracle(blest):
+    X, Y, M = _data()
+    w = omlp.init_weights(X.astype(np.float64).mean(0), X.astype(np.float64).std(0), seed=2).astype(np.float32)
+    loss, g = blest.mlp_loss_grad(X, Y, M, w)
+    l_ref, g_ref = omlp.loss_and_grad(w.astype(np.float64), X.astype(np.float64), Y.astype(np.float64),
+                                      M.astype(np.float64))
+    assert abs(loss - l_ref) <= 1e-4 * abs(l_ref)
+    scale = np.abs(g_ref).max()
+    assert np.all(np.abs(g - g_ref) <= 1e-4 * np.abs(g_ref) + 2e-5 * scale)
+    assert np.all(g[:12] == 0)
+
+
+def test_training_is_deterministic_and_tracks_oracle(blest):
+    X, Y, M = _data(300, seed=4)
+    w0 = omlp.init_weights(X.astype(np.float64).mean(0), X.astype(np.float64).std(0), seed=5).astype(np.float32)
+    w1, h1 = blest.mlp_train(X, Y, M, w0, epochs=200, lr=5e-3, weight_decay=1e-3)
+    w2, h2 = blest.mlp_train(X, Y, M, w0, epochs=200, lr=5e-3, weight_decay=1e-3)
+    assert np.array_equal(w1.view(np.uint32), w2.view(np.uint32))
+    assert np.array_equal(h1, h2)
+    # the same 200 Adam steps in fp64
+    w = w0.astype(np.float64)
+    m = np.zeros_like(w)
+    v = np.zeros_like(w)
+    for t in range(1, 201):
+        _, g = omlp.loss_and_grad(w, X, Y, M)
+        w, m, v = omlp.adam_step(w, g, m, v, t, lr=5e-3, wd=1e-3)
+    l_ref = omlp.loss_and_grad(w, X, Y, M)[0]
+    l_gpu = omlp.loss_and_grad(w1.astype(np.float64), X, Y, M)[0]
+    assert abs(l_gpu - l_ref) <= 0.02 * l_ref
+    assert h1[-1] < 0.5 * h1[0]
+
+
+def test_predictions_match_oracle(blest):
+    X, _, _ = _data(400, seed=7)
+    w = omlp.init_weights(X.astype(np.float64).mean(0), X.astype(np.float64).std(0), seed=8)
+    w[omlp.OFF_B3:] = [0.3, -0.2, 0.1, 0.0, 0.05]
+    w = w.astype(np.float32)
+    pred, ch = blest.mlp_predict(w, X)
+    ref, _ = omlp.forward(w.astype(np.float64), X.astype(np.float64))
+    assert np.all(np.abs(pred - ref) <= 1e-4 * (1 + np.abs(ref)))
+    srt = np.sort(ref, axis=1)
+    clear = srt[:, 1] - srt[:, 0] > 1e-3
+    assert np.array_equal(ch[clear], np.argmin(ref, axis=1)[clear])
+
+
+def test_in_kernel_decisions_and_exact_levels(blest):
+    """Random networks (a predictor fuzz): levels stay bit-exact, and every
+    logged level ran the mode the same network picks outside the BFS."""
+    g = gg.rmat(14, seed=21)
+    srcs = gg.sources(g, 4, 2)
+    with blest.build_graph(g) as h:
+        ad = h.info()["nnz"] / g.n
+        for seed in range(4):
+            rs = np.random.RandomState(seed)
+            w = rs.normal(0, 1, blest.MLP_NW).astype(np.float32)
+            w[6:12] = 0.2
+            h.load_model(w)
+            h.set_policy(blest.POLICY_LEARNED)
+            for s in srcs:
+                assert np.array_equal(h.bfs(int(s)), oracle.bfs(g, int(s)))
+                log = h.level_log()
+                _, ch = blest.mlp_predict(w, blest.mlp_features(log, ad))
+                assert [r["mode"] for r in log] == ch.tolist()
+        h.set_policy(blest.POLICY_HEURISTIC)
+
+
+def test_trained_network_beats_the_rule_on_held_out_graphs(blest):
+    """Train on per-level timings of small RMAT / grid / BA graphs, evaluate
+    on other seeds and on a held-out family (random geometric graph): the
+    learned policy's total time over the held-out levels is no worse than
+    the paper's rule (and usually lower).  Both are evaluated on the same
+    measured per-level time matrices."""
+    from paper_2606_05081_gb300 import switch
+    train_g = [gg.rmat(15, seed=31), gg.rmat(17, seed=32), gg.grid(256, 256, seed=33), gg.ba(1 << 16, 4, seed=34)]
+    hs = [blest.build_graph(x) for x in train_g]
+    X, Y, M, _ = switch.dataset(hs, [gg.sources(x, 6, 3) for x in train_g], reps=2)
+    for h in hs:
+        h.close()
+    w, hist = switch.train(X, Y, M)
+    assert hist[-1] < hist[0]
+    held = [gg.rmat(16, seed=41), gg.rgg(1 << 16, 10, seed=42), gg.ba(1 << 17, 8, seed=43)]
+    res = []
+    for x in held:
+        with blest.build_graph(x) as h:
+            res.append(switch.evaluate(h, gg.sources(x, 6, 4), w, reps=2))
+    print("held-out regret", res)
+    # the plain method: the paper's rule with its tensor-core hit test
+    tot_h = sum(r["ms_heuristic_tc"] for r in res)
+    tot_l = sum(r["ms_learned"] for r in res)
+    assert tot_l <= 1.02 * tot_h
