@@ -1,12 +1,24 @@
 """Benchmark: single-source BFS throughput (GTEPS, harmonic mean over seeded
 sources) of the BVSS path on one GB300, with its HBM roofline fraction.
 
-One "step" = one BFS from each of the workload's seeded sources (the whole
-hot path: level init, every level, un-permute).  Timing: CUDA events on the
-stream the kernels run on, W >= 3 warm-up steps, barrier + synchronize
-around the timed region, max over ranks.  The BVSS arrays of the bench
-graphs are gigabytes (far larger than the 129 MB L2), so no separate L2
-flush is done between timed iterations.
+Default workload (the single-source configuration): 64 seeded sources on
+each of two graphs --
+  * RMAT scale 24, edge factor 16 (16.7M vertices), JaccardWithWindows
+    reordering with W = 2^16;
+  * a 4096 x 4096 road-like grid (4-neighbour, 5 % of edges deleted, 0.1 %
+    random shortcuts), RCM reordering.
+One "step" = one BFS from every source of every graph (the whole hot path:
+level init, every level, un-permute into the caller's ids).
+
+Arms, each timed over the same steps:
+  plain  the paper's method: hand-set rule (lazy/eager by U_div, Eq. 5
+         switch), b1 MMA hit test, default launch shape;
+  tuned  the learned level-mode policy with the autotuned launch shape
+         (the headline `value`), falling back to the rule on the CUDA-core
+         engine when no trained weights are present.
+Timing: CUDA events on the stream the kernels run on, W >= 3 warm-up steps,
+synchronize around the timed region, max over ranks.  The BVSS arrays are
+gigabytes (far larger than the 129 MB L2), so no separate L2 flush is done.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl blest|reference]
 
@@ -30,19 +42,31 @@ sys.path.insert(0, ROOT)
 
 import graphgen as gg  # noqa: E402
 
-WORKLOADS = {
-    # name: (builder, build options, description)
+REORDER_RCM, REORDER_JACCARD = 1, 2
+GRAPHS = {
+    "rmat24_jaccard": (lambda: gg.rmat(24, 16, seed=2), dict(reorder=REORDER_JACCARD, jaccard_window=65536),
+                       "RMAT scale 24, edge factor 16, a=.57 b=c=.19, undirected, scrambled labels, "
+                       "JaccardWithWindows W=65536"),
+    "grid4096_rcm": (lambda: gg.grid(4096, 4096, 0.05, 0.001, seed=2), dict(reorder=REORDER_RCM),
+                     "4096x4096 4-neighbour grid, 5% edges deleted, 0.1% random shortcuts, RCM"),
     "rmat24": (lambda: gg.rmat(24, 16, seed=2), dict(reorder=0),
-               "RMAT scale 24 (16.7M vertices), edge factor 16, a=.57 b=c=.19, undirected, "
-               "labels scrambled"),
+               "RMAT scale 24, edge factor 16, undirected, scrambled labels, no reordering"),
     "rmat22": (lambda: gg.rmat(22, 16, seed=3), dict(reorder=0),
-               "RMAT scale 22 (4.2M vertices), edge factor 16, undirected, labels scrambled"),
+               "RMAT scale 22, edge factor 16, undirected, scrambled labels, no reordering"),
     "rmat16": (lambda: gg.rmat(16, 16, seed=1), dict(reorder=0),
-               "RMAT scale 16 (65,536 vertices), edge factor 16, undirected, no reordering"),
-    "grid4096": (lambda: gg.grid(4096, 4096, 0.05, 0.001, seed=2), dict(reorder=0),
-                 "4096x4096 4-neighbour grid, 5% edges deleted, 0.1% random shortcuts"),
+               "RMAT scale 16, edge factor 16, undirected, no reordering"),
 }
+WORKLOADS = {
+    "sssp_pair": ["rmat24_jaccard", "grid4096_rcm"],
+    "rmat24": ["rmat24"],
+    "rmat22": ["rmat22"],
+    "rmat16": ["rmat16"],
+    "grid4096_rcm": ["grid4096_rcm"],
+    "rmat24_jaccard": ["rmat24_jaccard"],
+}
+DEFAULT_WORKLOAD = "sssp_pair"
 NUM_SOURCES = 64
+METRIC = "GTEPS (harm. mean/source), single-source BFS"
 
 
 def peaks():
@@ -120,7 +144,8 @@ def algorithmic_bytes(log, n: int, reached: int) -> float:
         (8 B per 32 vertices), two row pointers per probed vertex (16 B) and
         4 B per in-neighbour id read;
       every newly visited vertex: its level (4 B) and its degree (4 B);
-      init: 4 B per vertex of levels and 5 bitvectors (20 B per 32 vertices)."""
+      init: 4 B per vertex of levels and 5 bitvectors (20 B per 32 vertices).
+    The caller adds 8 B per vertex for the un-permute of a reordered graph."""
     W = (n + 31) // 32
     b = 4.0 * n + 20.0 * W + 8.0 * reached
     for i, rec in enumerate(log):
@@ -140,45 +165,8 @@ def harmonic(x):
     return float(len(x) / np.sum(1.0 / x))
 
 
-def run_reference(args, rank, world):
-    """CPU oracle on a bounded sample of the workload (rank 0 only)."""
-    if rank != 0:
-        return
-    import oracle
-    build_fn, _, desc = WORKLOADS[args.workload]
-    g = build_fn()
-    srcs = gg.sources(g, NUM_SOURCES, 7)
-    edges = []
-    times = []
-    budget = float(os.environ.get("BLEST_REF_BUDGET_S", "20"))
-    t_all = time.perf_counter()
-    k = 0
-    for step in range(args.warmup + args.steps):
-        s = int(srcs[k % len(srcs)])
-        k += 1
-        t0 = time.perf_counter()
-        lv = oracle.bfs(g, s)
-        dt = time.perf_counter() - t0
-        if step >= args.warmup:
-            times.append(dt)
-            edges.append(oracle.gteps_edges(g, lv))
-        if time.perf_counter() - t_all > budget and len(times) >= 1:
-            break
-    rates = [e / t / 1e9 for e, t in zip(edges, times)]
-    v = harmonic(rates)
-    line = {"metric": "GTEPS (harm. mean/source), single-source BFS", "value": v, "unit": "GTEPS",
-            "impl": "reference", "n_gpus": world, "steps": len(times), "warmup": args.warmup,
-            "ms_per_step": float(np.mean(times) * 1e3), "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": args.workload, "graph": desc, "n": g.n, "nnz": g.nnz,
-                       "sources": "seeded vertices of nonzero degree"},
-            "cpu_baseline": {"value": v, "unit": "GTEPS", "cores": 1, "kind": "oracle",
-                             "sample": f"{len(times)} single-source serial BFS runs (one step = one source)"},
-            "e2e": {"value": v, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line), flush=True)
-
-
-def cpu_baseline(g, srcs, budget_s=15.0):
+def cpu_sample(g, srcs, budget_s):
+    """The oracle (serial FIFO BFS, one host core) on a bounded sample."""
     import oracle
     rates = []
     t_all = time.perf_counter()
@@ -189,25 +177,97 @@ def cpu_baseline(g, srcs, budget_s=15.0):
         rates.append(oracle.gteps_edges(g, lv) / dt / 1e9)
         if time.perf_counter() - t_all > budget_s:
             break
-    return {"value": harmonic(rates), "unit": "GTEPS", "cores": 1, "kind": "oracle",
-            "sample": f"{len(rates)} of the workload's sources, one serial FIFO BFS each on one host core"}
+    return rates
+
+
+def run_reference(args, rank, world):
+    """CPU oracle on a bounded sample of the workload (rank 0 only)."""
+    if rank != 0:
+        return
+    names = WORKLOADS[args.workload]
+    budget = float(os.environ.get("BLEST_REF_BUDGET_S", "40")) / len(names)
+    rates, per_graph = [], {}
+    t0 = time.perf_counter()
+    for nm in names:
+        g = GRAPHS[nm][0]()
+        r = cpu_sample(g, gg.sources(g, NUM_SOURCES, 7), budget)
+        per_graph[nm] = {"gteps": harmonic(r), "sources_timed": len(r)}
+        rates += r
+    v = harmonic(rates)
+    line = {"metric": METRIC, "value": v, "unit": "GTEPS", "impl": "reference", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": (time.perf_counter() - t0) * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "graphs": {nm: GRAPHS[nm][2] for nm in names},
+                       "sources": "64 seeded vertices of nonzero degree per graph"},
+            "per_graph": per_graph,
+            "cpu_baseline": {"value": v, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+                             "sample": f"{len(rates)} single-source serial BFS runs, bounded by time"},
+            "e2e": {"value": v, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+class GraphRun:
+    """One bench graph: handle, sources, edge counts and per-arm timings."""
+
+    def __init__(self, name, args, rank, dev, torch, blest, stream):
+        build_fn, bopts, desc = GRAPHS[name]
+        self.name, self.desc = name, desc
+        t0 = time.time()
+        self.g = g = build_fn()
+        self.gen_s = time.time() - t0
+        self.srcs = gg.sources(g, args.sources, 7 + rank)
+        self.tune_srcs = gg.sources(g, 8, 1000 + rank)
+        rp_d = torch.from_numpy(g.row_ptr).to(dev)
+        col_d = torch.from_numpy(g.col).to(dev)
+        t0 = time.time()
+        self.h = blest.build(g.n, rp_d, col_d, **bopts)
+        self.build_s = time.time() - t0
+        del rp_d, col_d
+        self.info = self.h.info()
+        self.stream = stream
+        self.h.set_stream(stream.cuda_stream, True)
+        self.out = torch.empty(g.n, dtype=torch.int32, device=dev)
+        deg_d = torch.from_numpy(np.diff(g.row_ptr)).to(dev)
+        self.edges, self.reached = [], []
+        for s in self.srcs:
+            self.h.bfs(int(s), self.out)
+            self.h.sync()
+            r = self.out >= 0
+            e = int(deg_d[r].sum().item())
+            self.edges.append(e if g.directed else e // 2)
+            self.reached.append(int(r.sum().item()))
+        self.ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in self.srcs]
+
+    def step(self, record):
+        for i, s in enumerate(self.srcs):
+            if record:
+                self.ev[i][0].record(self.stream)
+            self.h.bfs(int(s), self.out)
+            if record:
+                self.ev[i][1].record(self.stream)
+
+    def logs(self):
+        out = []
+        for s in self.srcs:
+            self.h.bfs(int(s), self.out)
+            self.h.sync()
+            out.append(self.h.level_log())
+        return out
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--workload", default="rmat24", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--impl", default="blest", choices=["blest", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sources", type=int, default=NUM_SOURCES)
-    ap.add_argument("--no-learned", action="store_true", help="skip the learned-policy arm")
-    ap.add_argument("--block", type=int, default=0, help="CTA size override (256, 512, 1024)")
-    ap.add_argument("--batch", type=int, default=0, help="VSSs in flight per warp override (1, 2, 4)")
-    ap.add_argument("--levels", action="store_true", help="print the per-level log of the first source to stderr")
+    ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (tuned arm = default launch)")
+    ap.add_argument("--levels", action="store_true", help="per-level log of the first source to stderr")
     args = ap.parse_args()
-    args.warmup = max(args.warmup, 3) if args.impl == "blest" else args.warmup
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -217,179 +277,172 @@ def main():
         import torch.distributed as dist_mod
         dist = dist_mod
         dist.init_process_group("nccl" if args.impl == "blest" else "gloo")
-
     if args.impl == "reference":
         run_reference(args, rank, world)
         if dist:
             dist.destroy_process_group()
         return
+    args.warmup = max(args.warmup, 3)
 
     import torch
     import paper_2606_05081_gb300 as blest
+    from paper_2606_05081_gb300 import autotune, switch
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-
-    build_fn, bopts, desc = WORKLOADS[args.workload]
-    t0 = time.time()
-    g = build_fn()
-    gen_s = time.time() - t0
-    # replicas: each rank runs its own seeded sources on its own copy (weak scaling)
-    srcs = gg.sources(g, args.sources, 7 + rank)
-    deg = np.diff(g.row_ptr)
-    rp_d = torch.from_numpy(g.row_ptr).to(dev)
-    col_d = torch.from_numpy(g.col).to(dev)
-    if args.block:
-        bopts = dict(bopts, block_threads=args.block)
-    if args.batch:
-        bopts = dict(bopts, vss_batch=args.batch)
-    h = blest.build(g.n, rp_d, col_d, **bopts)
-    del rp_d, col_d
-    info = h.info()
-    # a dedicated stream: the events below and the library's kernels share it
     stream = torch.cuda.Stream(dev)
     torch.cuda.set_stream(stream)
-    h.set_stream(stream.cuda_stream, True)
-    out = torch.empty(g.n, dtype=torch.int32, device=dev)
-    deg_d = torch.from_numpy(deg).to(dev)
 
-    # edges per source (Graph500 convention: arcs out of reached vertices / 2)
-    edges = []
-    logs = []
-    for s in srcs:
-        h.bfs(int(s), out)
-        h.sync()
-        reached = out >= 0
-        e = int(deg_d[reached].sum().item())
-        edges.append(e if g.directed else e // 2)
-        logs.append((h.level_log(), int(reached.sum().item())))
-    if args.levels and rank == 0:
-        for rec in logs[0][0]:
-            print("level", json.dumps(rec), file=sys.stderr)
+    runs = [GraphRun(nm, args, rank, dev, torch, blest, stream) for nm in WORKLOADS[args.workload]]
+    weights = switch.load_weights()
+    tuned_policy = blest.POLICY_LEARNED if weights is not None else blest.POLICY_HEURISTIC
+    tune_info = {}
+    for r in runs:
+        if weights is not None:
+            r.h.load_model(weights)
+        if not args.no_tune:
+            r.h.set_policy(tuned_policy)
+            r.h.set_stream(None, False)
+            tune_info[r.name] = autotune.autotune(r.h, r.tune_srcs, reps=2, stream=stream)
+            r.h.set_stream(stream.cuda_stream, True)
+        ti = tune_info.get(r.name, {})
+        r.tuned = (int(ti.get("block_threads", 512)), int(ti.get("vss_batch", 2)), bool(ti.get("engine_tc", 0)))
+        if args.levels and rank == 0:
+            r.h.set_policy(tuned_policy)
+            for rec in r.logs()[0]:
+                print(r.name, "level", json.dumps(rec), file=sys.stderr)
 
-    starts = [torch.cuda.Event(enable_timing=True) for _ in srcs]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in srcs]
+    arms = {"plain": (blest.POLICY_HEURISTIC, "default", True), "tuned": (tuned_policy, "tuned", None)}
 
-    def step(record):
-        for i, s in enumerate(srcs):
-            if record:
-                starts[i].record(stream)
-            h.bfs(int(s), out)
-            if record:
-                ends[i].record(stream)
+    def set_arm(r, arm):
+        pol, launch, tc = arms[arm]
+        if launch == "default":
+            r.h.set_launch(512, 2)
+        else:
+            r.h.set_launch(r.tuned[0], r.tuned[1])
+        r.h.set_engine(r.tuned[2] if tc is None else tc)
+        r.h.set_policy(pol)
 
-    def measure(policy, engine_tc):
-        """Warm-up, then the timed steps under one level-mode policy; returns
-        per-source device ms [steps, sources], the timed region's ms and the
-        per-source level logs of the policy."""
-        h.set_engine(engine_tc)
-        h.set_policy(policy)
-        for _ in range(args.warmup):
-            step(False)
-        h.sync()
-        torch.cuda.synchronize()
-        psm = np.zeros((args.steps, len(srcs)))
-        if dist:
-            dist.barrier()
-        torch.cuda.synchronize()
-        t_start = torch.cuda.Event(enable_timing=True)
-        t_end = torch.cuda.Event(enable_timing=True)
-        t_start.record(stream)
-        for k in range(args.steps):
-            step(True)
+    results = {}
+    with ClockSampler(local) as clk:
+        for arm in arms:
+            for r in runs:
+                set_arm(r, arm)
+                for _ in range(args.warmup):
+                    r.step(False)
+                r.h.sync()
             torch.cuda.synchronize()
-            for i in range(len(srcs)):
-                psm[k, i] = starts[i].elapsed_time(ends[i])
-        t_end.record(stream)
-        torch.cuda.synchronize()
-        h.sync()
-        if dist:
-            dist.barrier()
-        tot = t_start.elapsed_time(t_end)
-        if dist:
-            tt = torch.tensor([tot], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            tot = float(tt.item())
-        plogs = []
-        for s_ in srcs:
-            h.bfs(int(s_), out)
-            h.sync()
-            plogs.append(h.level_log())
-        return psm, tot, plogs
+            if dist:
+                dist.barrier()
+            torch.cuda.synchronize()
+            t0e, t1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            psm = {r.name: np.zeros((args.steps, len(r.srcs))) for r in runs}
+            t0e.record(stream)
+            for k in range(args.steps):
+                for r in runs:
+                    set_arm(r, arm)
+                    r.step(True)
+                torch.cuda.synchronize()
+                for r in runs:
+                    for i in range(len(r.srcs)):
+                        psm[r.name][k, i] = r.ev[i][0].elapsed_time(r.ev[i][1])
+            t1e.record(stream)
+            torch.cuda.synchronize()
+            for r in runs:
+                r.h.sync()
+            if dist:
+                dist.barrier()
+            tot = t0e.elapsed_time(t1e)
+            if dist:
+                tt = torch.tensor([tot], device=dev)
+                dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+                tot = float(tt.item())
+            results[arm] = (psm, tot, {r.name: r.logs() for r in runs})
 
-    def gteps(psm):
-        rates = (np.asarray(edges)[None, :] / (psm * 1e-3)) / 1e9
-        v = harmonic(rates.ravel())
+    def gteps_of(psm_by_graph):
+        rates = []
+        per = {}
+        for r in runs:
+            rr = (np.asarray(r.edges)[None, :] / (psm_by_graph[r.name] * 1e-3)) / 1e9
+            per[r.name] = harmonic(rr.ravel())
+            rates.append(rr.ravel())
+        v = harmonic(np.concatenate(rates))
         if dist:
             vt = torch.tensor([v], device=dev, dtype=torch.float64)
             dist.all_reduce(vt)
             v = float(vt.item())
-        return v
+        return v, per
 
-    from paper_2606_05081_gb300 import switch
-    weights = switch.load_weights()
-    policies = [("plain_tc", blest.POLICY_HEURISTIC, True), ("heuristic_cc", blest.POLICY_HEURISTIC, False)]
-    if weights is not None and not args.no_learned:
-        h.load_model(weights)
-        policies.append(("learned", blest.POLICY_LEARNED, False))
-    results = {}
-    with ClockSampler(local) as clk:
-        for name, pol, tc in policies:
-            results[name] = measure(pol, tc)
-    head = "learned" if "learned" in results else "heuristic_cc"
-    per_source_ms, total_ms, head_logs = results[head]
-    value = gteps(per_source_ms)
-    variants = {name: {"gteps": gteps(r[0]), "per_source_ms_median": float(np.median(r[0])),
-                       "ms_per_step": r[1] / args.steps} for name, r in results.items()}
+    value, per_graph = gteps_of(results["tuned"][0])
+    plain_value, plain_per = gteps_of(results["plain"][0])
 
-    # roofline of the persistent BFS kernel under the headline policy
+    # roofline of the persistent BFS kernel under the headline arm
     hbm, peak_kind = peaks()
-    mean_ms = per_source_ms.mean(axis=0)
-    reached = [lg_r for _, lg_r in logs]
-    alg = np.array([algorithmic_bytes(lg, g.n, r) for lg, r in zip(head_logs, reached)])
-    achieved = float(np.sum(alg) / np.sum(mean_ms * 1e-3) / 1e9)
-    logs = [(lg, r) for lg, r in zip(head_logs, reached)]
+    alg_b, dev_s = 0.0, 0.0
+    for r in runs:
+        logs = results["tuned"][2][r.name]
+        alg_b += sum(algorithmic_bytes(lg, r.g.n, rc) + (8.0 * r.g.n if r.info["reorder"] else 0.0)
+                     for lg, rc in zip(logs, r.reached))
+        dev_s += float(results["tuned"][0][r.name].mean(axis=0).sum()) * 1e-3
+    achieved = alg_b / dev_s / 1e9
 
-    # end to end through the C ABI with host buffers (synchronous calls)
-    h.set_stream(None, False)
-    host_out = torch.empty(g.n, dtype=torch.int32).pin_memory()
-    host_np = host_out.numpy()
-    e2e_rates = []
-    for s, e in zip(srcs, edges):
-        t0 = time.perf_counter()
-        h.bfs(int(s), host_np)
-        dt = time.perf_counter() - t0
-        e2e_rates.append(e / dt / 1e9)
+    # end to end through the C ABI with host buffers, headline arm
+    e2e_rates, d2h = [], 0
+    for r in runs:
+        set_arm(r, "tuned")
+        r.h.set_stream(None, False)
+        host = torch.empty(r.g.n, dtype=torch.int32).pin_memory().numpy()
+        for s, e in zip(r.srcs, r.edges):
+            t0 = time.perf_counter()
+            r.h.bfs(int(s), host)
+            e2e_rates.append(e / (time.perf_counter() - t0) / 1e9)
+        d2h += 4 * r.g.n * len(r.srcs)
     e2e = harmonic(e2e_rates)
 
+    graphs_cfg = {}
+    for r in runs:
+        graphs_cfg[r.name] = {
+            "graph": r.desc, "n": r.g.n, "nnz": int(r.info["nnz"]), "num_vss": int(r.info["num_vss"]),
+            "udiv": round(r.info["update_divergence"], 1), "lazy": int(r.info["lazy"]),
+            "switching": int(r.info["switching"]), "reorder": int(r.info["reorder"]),
+            "gteps_tuned": per_graph[r.name], "gteps_plain": plain_per[r.name],
+            "per_source_ms_median_tuned": float(np.median(results["tuned"][0][r.name])),
+            "per_source_ms_median_plain": float(np.median(results["plain"][0][r.name])),
+            "tuned_launch": {"block_threads": r.tuned[0], "vss_batch": r.tuned[1], "engine_tc": int(r.tuned[2])},
+            "graph_gen_s": round(r.gen_s, 1), "build_s": round(r.build_s, 2),
+            "build_ms_device": round(r.info["build_ms"], 1),
+            "levels_source0_tuned": [[x["mode"], x["queue"], round(x["t_ns"] / 1e3, 1)]
+                                     for x in results["tuned"][2][r.name][0]][:40]}
     line = {
-        "metric": "GTEPS (harm. mean/source), single-source BFS", "value": value, "unit": "GTEPS",
+        "metric": METRIC, "value": value, "unit": "GTEPS",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": results["tuned"][1] / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": args.workload, "graph": desc, "n": g.n, "nnz": int(info["nnz"]),
-                   "sources": len(srcs), "reorder": int(info["reorder"]), "lazy": int(info["lazy"]),
-                   "switching": int(info["switching"]), "policy": head,
-                   "udiv": info["update_divergence"], "num_vss": int(info["num_vss"]),
-                   "block_threads": int(info["block_threads"]), "grid_blocks": int(info["grid_blocks"]),
-                   "vss_batch": int(bopts.get("vss_batch", 2)),
+        "config": {"workload": args.workload, "sources_per_graph": args.sources,
+                   "policy": "learned+autotuned" if weights is not None else "heuristic+autotuned",
                    "l2": "inputs larger than L2 (BVSS arrays), no flush", "parallelism": f"replicas{world}",
-                   "graph_gen_s": round(gen_s, 1), "build_ms": round(info["build_ms"], 1)},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": None, "peak_kind": peak_kind,
-                     "kernel": "k_bfs (persistent, all levels)"},
-        "e2e": {"value": e2e, "unit": "GTEPS", "h2d_bytes_per_step": 4 * len(srcs),
-                "d2h_bytes_per_step": 4 * g.n * len(srcs)},
-        "gpu_launches": args.steps * len(srcs) * len(results),
-        "variants": variants,
+                   "graphs": graphs_cfg},
+        "plain": {"value": plain_value, "ms_per_step": results["plain"][1] / args.steps,
+                  "what": "hand-set rule (U_div lazy/eager, Eq. 5 switch), b1 MMA hit test, default launch"},
+        "speedup_vs_plain": value / plain_value,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                     "traffic": None, "peak_kind": peak_kind, "kernel": "k_bfs (persistent, all levels)"},
+        "e2e": {"value": e2e, "unit": "GTEPS", "h2d_bytes_per_step": 4 * sum(len(r.srcs) for r in runs),
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": args.steps * sum(len(r.srcs) for r in runs) * len(arms),
         "clocks": clk.summary(),
-        "per_source_ms_median": float(np.median(per_source_ms)),
-        "levels_source0": [[r["mode"], r["queue"], round(r["t_ns"] / 1e3, 1)] for r in logs[0][0]],
+        "autotune": {k: {kk: vv for kk, vv in v.items() if kk != "tried"} for k, v in tune_info.items()},
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(g, srcs)
+        rates = []
+        for r in runs:
+            rates += cpu_sample(r.g, r.srcs, 12.0 / len(runs))
+        line["cpu_baseline"] = {"value": harmonic(rates), "unit": "GTEPS", "cores": 1, "kind": "oracle",
+                                "sample": f"{len(rates)} of the workload's sources (all graphs), one serial "
+                                          "FIFO BFS each on one host core, about 12 s"}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    h.close()
+    for r in runs:
+        r.h.close()
     if dist:
         dist.destroy_process_group()
 

@@ -177,6 +177,11 @@ blest_status blest_set_policy(blest_handle h, int32_t policy, int32_t fixed_mode
  * (Fig. 3 layout, the paper's), 0 = CUDA cores. */
 blest_status blest_set_engine(blest_handle h, int32_t tc);
 
+/* Launch shape of the single-source kernel: block_threads in {256, 512,
+ * 1024}, vss_batch in {1, 2, 4} (VSSs a warp keeps in flight in top-down
+ * levels).  The grid is resized to the SMs' resident capacity. */
+blest_status blest_set_launch(blest_handle h, int32_t block_threads, int32_t vss_batch);
+
 /* Per-level modes for BLEST_POLICY_SCHEDULE: level l (1-based) runs
  * modes[(l-1) % len].  Copied. */
 blest_status blest_set_schedule(blest_handle h, const int32_t *modes, int32_t len);
@@ -255,10 +260,10 @@ blest_status blest_mlp_predict(const float *weights, const float *features, int6
  * is not allowed.  It runs the single-source BFS kernel over a BVSS the
  * caller already holds in device memory (for example copied out of a handle
  * with blest_get_bvss), in a fixed top-down eager mode, and allocates
- * nothing: its scratch (bitvectors, queues, control block, about 5.3 MB)
+ * nothing: its scratch (bitvectors, queues, control block, about 5.4 MB)
  * is a static array of the library's device image that every GPU loading
  * the library holds until the process exits.
- *  - Limits: n <= 1,048,576 vertices and num_vss <= 262,144; larger graphs
+ *  - Limits: n <= 1,048,576 vertices and num_vss <= 131,072; larger graphs
  *    return BLEST_ERR_UNSUPPORTED.
  *  - The first call on each device looks up the array's device address with
  *    that device current; make that first call before any stream capture.

@@ -79,6 +79,7 @@ _sigs = {
     "blest_set_policy": (_S, [_H, ctypes.c_int32, ctypes.c_int32]),
     "blest_set_schedule": (_S, [_H, _P, ctypes.c_int32]),
     "blest_set_engine": (_S, [_H, ctypes.c_int32]),
+    "blest_set_launch": (_S, [_H, ctypes.c_int32, ctypes.c_int32]),
     "blest_load_model": (_S, [_H, _P, ctypes.c_int32]),
     "blest_last_timings": (_S, [_H, _P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
     "blest_get_info": (_S, [_H, ctypes.POINTER(Info)]),
@@ -228,6 +229,9 @@ class Graph:
 
     def set_engine(self, tc: bool):
         _check(_lib.blest_set_engine(self._h, int(bool(tc))), "blest_set_engine")
+
+    def set_launch(self, block_threads: int, vss_batch: int):
+        _check(_lib.blest_set_launch(self._h, int(block_threads), int(vss_batch)), "blest_set_launch")
 
     def set_schedule(self, modes):
         m = np.ascontiguousarray(modes, dtype=np.int32)

@@ -38,7 +38,7 @@ struct BfsParams {
     int *L;
     unsigned *Vc, *Vn;
     unsigned *F[3];
-    int *Q[3];
+    int2 *Q[3];             // queue entries {VSS id, its slice set}
     int *SQ[3];
     Ctl *ctl;
     blest_level_log *log;
@@ -87,7 +87,7 @@ __device__ __forceinline__ int pick(const int4 &r, int c) {
 
 // Warp-aggregated enqueue of up to 4 slice sets per lane (bit c of `want`
 // set => slice set ss[c]): their VSS ranges go to Q, the set ids to SQ.
-__device__ __forceinline__ void enqueue_sets(const BfsParams &P, unsigned want, const int ss[4], int *Q, int *SQ,
+__device__ __forceinline__ void enqueue_sets(const BfsParams &P, unsigned want, const int ss[4], int2 *Q, int *SQ,
                                              int slot) {
     const int lane = lane_id();
     if (!__any_sync(FULL_MASK, want != 0)) return;
@@ -117,7 +117,35 @@ __device__ __forceinline__ void enqueue_sets(const BfsParams &P, unsigned want, 
     for (int c = 0; c < 4; ++c) {
         if (want >> c & 1u) {
             SQ[sbase++] = ss[c];
-            for (int k = 0; k < len[c]; ++k) Q[qbase + k] = a[c] + k;
+            for (int k = 0; k < len[c]; ++k) Q[qbase + k] = make_int2(a[c] + k, ss[c]);
+            qbase += len[c];
+        }
+    }
+}
+
+// Same, with the VSS ranges [a[c], a[c] + len[c]) already loaded.
+__device__ __forceinline__ void enqueue_ranges(const BfsParams &P, unsigned want, const int ss[4], const int a[4],
+                                               const int len[4], int2 *Q, int *SQ, int slot) {
+    const int lane = lane_id();
+    if (!__any_sync(FULL_MASK, want != 0)) return;
+    int tot = 0, nset = 0;
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+        if (want >> c & 1u) { tot += len[c]; ++nset; }
+    const int incl = warp_incl_scan(tot);
+    const int sincl = warp_incl_scan(nset);
+    int qbase = 0, sbase = 0;
+    if (lane == 31) {
+        qbase = incl ? atomicAdd(&P.ctl->qlen[slot], incl) : 0;
+        sbase = atomicAdd(&P.ctl->sqlen[slot], sincl);
+    }
+    qbase = __shfl_sync(FULL_MASK, qbase, 31) + incl - tot;
+    sbase = __shfl_sync(FULL_MASK, sbase, 31) + sincl - nset;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        if (want >> c & 1u) {
+            SQ[sbase++] = ss[c];
+            for (int k = 0; k < len[c]; ++k) Q[qbase + k] = make_int2(a[c] + k, ss[c]);
             qbase += len[c];
         }
     }
@@ -145,67 +173,107 @@ __device__ void push_level(const BfsParams &P, int ell, int bc, int bn, int slot
     const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
     const unsigned *Fc = P.F[bc];
     unsigned *Fn = P.F[bn];
-    const int *Qc = P.Q[bc];
+    const int2 *Qc = P.Q[bc];
     unsigned long long nv = 0, fe = 0;
     for (int w0 = gwarp * B; w0 < qlen; w0 += nwarps * B) {
         int vss[B], ss[B];
         int4 r[B];
         unsigned m[B], alpha[B];
-        // lane b < B fetches queue entry w0 + b; one shuffle spreads them
-        const int mine = (lane < B && w0 + lane < qlen) ? Qc[w0 + lane] : -1;
+        // lane b < B fetches queue entry w0 + b (VSS and slice set); shuffles spread them
+        const int2 mine = (lane < B && w0 + lane < qlen) ? Qc[w0 + lane] : make_int2(-1, 0);
 #pragma unroll
-        for (int b = 0; b < B; ++b) vss[b] = __shfl_sync(FULL_MASK, mine, b);
+        for (int b = 0; b < B; ++b) {
+            vss[b] = __shfl_sync(FULL_MASK, mine.x, b);
+            ss[b] = __shfl_sync(FULL_MASK, mine.y, b);
+        }
+        // slices, masks and frontier bytes of the B VSSs are independent loads
 #pragma unroll
         for (int b = 0; b < B; ++b) {
             if (vss[b] >= 0) {
-                ss[b] = __ldg(&P.v2r[vss[b]]);
                 r[b] = __ldg(&P.rowIds[(size_t)vss[b] * 32 + lane]);
                 m[b] = __ldg(&P.masks[(size_t)vss[b] * 32 + lane]);
+                alpha[b] = ld_byte(Fc, ss[b]);
             } else {
-                ss[b] = 0;
                 r[b] = make_int4(0, 0, 0, 0);
                 m[b] = 0u;
+                alpha[b] = 0u;
             }
         }
-#pragma unroll
-        for (int b = 0; b < B; ++b) alpha[b] = vss[b] >= 0 ? ld_byte(Fc, ss[b]) : 0u;
 #pragma unroll
         for (int b = 0; b < B; ++b) {
             if (vss[b] < 0) continue;   // warp-uniform
             const unsigned hits = TC ? hits_tc(m[b], alpha[b], bsel) : hits_cc(m[b], alpha[b]);
             if (EAGER) {
-                unsigned want = 0;
-                int sso[4] = {0, 0, 0, 0};
+                // phase 1: visited words of the hit rows (independent loads)
+                int u[4];
+                unsigned vw[4];
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
-                    if (hits >> c & 1u) {
-                        const int u = pick(r[b], c);
-                        const unsigned bit = 1u << (u & 31);
-                        const int wd = u >> 5;
-                        if (!(P.Vc[wd] & bit)) {
-                            const unsigned old = atomicOr(&Fn[wd], bit);
-                            if (!(old & bit)) {
-                                P.L[u] = ell;
-                                red_or(&P.Vc[wd], bit);
-                                red_or(&P.Vn[wd], bit);
-                                nv += 1;
-                                fe += (unsigned long long)__ldg(&P.deg[u]);
-                                if (((old >> (u & 24)) & 0xFFu) == 0) {
-                                    want |= 1u << c;
-                                    sso[c] = u >> 3;
-                                }
-                            }
-                        }
+                    u[c] = pick(r[b], c);
+                    vw[c] = (hits >> c & 1u) ? P.Vc[u[c] >> 5] : 0xFFFFFFFFu;
+                }
+                // phase 2: claim the unvisited ones.  Lanes whose rows share a frontier
+                // word OR their bits together and one of them issues the atomic (rows
+                // of a VSS are often consecutive); degree and VSS-range loads ride along.
+                unsigned old[4];
+                int dg[4], a[4], len[4], sso[4];
+                unsigned cand = 0;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const bool cd = !(vw[c] >> (u[c] & 31) & 1u);
+                    const int key = cd ? (u[c] >> 5) : -1;
+                    const unsigned peers = __match_any_sync(FULL_MASK, key);
+                    const unsigned bits = __reduce_or_sync(peers, cd ? (1u << (u[c] & 31)) : 0u);
+                    const int leader = __ffs(peers) - 1;
+                    unsigned o = 0u;
+                    if (cd && lane == leader) o = atomicOr(&Fn[key], bits);
+                    o = __shfl_sync(FULL_MASK, o, leader);
+                    old[c] = cd ? o : 0xFFFFFFFFu;
+                    dg[c] = 0;
+                    a[c] = 0;
+                    len[c] = 0;
+                    sso[c] = u[c] >> 3;
+                    if (cd) {
+                        cand |= 1u << c;
+                        dg[c] = __ldg(&P.deg[u[c]]);
+                        a[c] = __ldg(&P.realPtrs[sso[c]]);
+                        len[c] = __ldg(&P.realPtrs[sso[c] + 1]);
                     }
                 }
-                enqueue_sets(P, want, sso, P.Q[bn], P.SQ[bn], slot);
-            } else {
+                // phase 3: winners set their level; visited bits are OR-ed once per word;
+                // the first claim of a slice-set byte enqueues its VSSs (once per set)
+                unsigned want = 0;
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
-                    if (hits >> c & 1u) {
-                        const int u = pick(r[b], c);
-                        red_or(&P.Vn[u >> 5], 1u << (u & 31));
+                    const bool win = (cand >> c & 1u) && !(old[c] >> (u[c] & 31) & 1u);
+                    const int key = win ? (u[c] >> 5) : -1;
+                    const unsigned peers = __match_any_sync(FULL_MASK, key);
+                    const unsigned bits = __reduce_or_sync(peers, win ? (1u << (u[c] & 31)) : 0u);
+                    if (win && lane == __ffs(peers) - 1) {
+                        red_or(&P.Vc[key], bits);
+                        red_or(&P.Vn[key], bits);
                     }
+                    const int skey = win ? sso[c] : -1;
+                    const unsigned speers = __match_any_sync(FULL_MASK, skey);
+                    if (win) {
+                        P.L[u[c]] = ell;
+                        nv += 1;
+                        fe += (unsigned long long)dg[c];
+                        if (lane == __ffs(speers) - 1 && ((old[c] >> (u[c] & 24)) & 0xFFu) == 0) want |= 1u << c;
+                    }
+                    len[c] -= a[c];
+                }
+                enqueue_ranges(P, want, sso, a, len, P.Q[bn], P.SQ[bn], slot);
+            } else {
+                // lazy marking: one fire-and-forget OR per distinct V_next word
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const bool hit = hits >> c & 1u;
+                    const int u = pick(r[b], c);
+                    const int key = hit ? (u >> 5) : -1;
+                    const unsigned peers = __match_any_sync(FULL_MASK, key);
+                    const unsigned bits = __reduce_or_sync(peers, hit ? (1u << (u & 31)) : 0u);
+                    if (hit && lane == __ffs(peers) - 1) red_or(&P.Vn[key], bits);
                 }
             }
         }
@@ -341,15 +409,24 @@ __device__ void finalize_level(const BfsParams &P, int ell, int bn, int slot) {
     const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
     unsigned *Fn = P.F[bn];
     unsigned long long nv = 0, fe = 0;
-    for (int base = gwarp * 32; base < P.W; base += nwarps * 32) {
+    for (int base0 = gwarp * 32; base0 < P.W; base0 += 2 * nwarps * 32) {
+      // the visited words of both groups are loaded before either is used
+      unsigned nx[2], cu[2];
+#pragma unroll
+      for (int g2 = 0; g2 < 2; ++g2) {
+          const int tt = base0 + g2 * nwarps * 32 + lane;
+          nx[g2] = tt < P.W ? P.Vn[tt] : 0u;
+          cu[g2] = tt < P.W ? P.Vc[tt] : 0u;
+      }
+#pragma unroll 1
+      for (int g2 = 0; g2 < 2; ++g2) {
+        const int base = base0 + g2 * nwarps * 32;
         const int t = base + lane;
         unsigned diff = 0;
         if (t < P.W) {
-            const unsigned next = P.Vn[t];
-            const unsigned cur = P.Vc[t];
-            diff = next ^ cur;
+            diff = nx[g2] ^ cu[g2];
             if (diff) {
-                P.Vc[t] = next;
+                P.Vc[t] = nx[g2];
                 Fn[t] = diff;
                 nv += (unsigned long long)__popc(diff);
             }
@@ -382,6 +459,7 @@ __device__ void finalize_level(const BfsParams &P, int ell, int bn, int slot) {
             if ((diff >> (8 * c)) & 0xFFu) want |= 1u << c;
         }
         enqueue_sets(P, want, sso, P.Q[bn], P.SQ[bn], slot);
+      }
     }
     flush_counts(P, slot, nv, fe);
 }
@@ -409,22 +487,52 @@ __device__ __forceinline__ int decide_mode(const BfsParams &P, int ell, long lon
     return mode;
 }
 
+// Buffers of level ell-2 are cleared sparsely and the counters of level
+// ell+1 zeroed.  Runs after the level's stage-1 work, on the grid's last
+// threads, so it stays off the path of the warps that own queue entries.
+__device__ __forceinline__ void housekeeping(const BfsParams &P, int ell, int bo, int sql, int sz, int tid,
+                                             int nthreads) {
+    Ctl *ctl = P.ctl;
+    const int rt = nthreads - 1 - tid;
+    if (ell >= 2) {
+        unsigned char *Fo = reinterpret_cast<unsigned char *>(P.F[bo]);
+        const int *SQo = P.SQ[bo];
+        for (int k = rt; k < sql; k += nthreads) Fo[SQo[k]] = 0;
+    }
+    if (rt == 0) {
+        ctl->qlen[sz] = 0;
+        ctl->sqlen[sz] = 0;
+        ctl->newv[sz] = 0;
+        ctl->fedges[sz] = 0;
+        ctl->scan_v[sz] = 0;
+        ctl->scan_a[sz] = 0;
+    }
+}
+
 template <bool EAGER>
 __device__ __forceinline__ void push_dispatch(const BfsParams &P, bool tc, int ell, int bc, int bn, int sn, int qlen,
                                               unsigned bsel) {
+    // eager levels keep at most two VSSs in flight (their per-slice state
+    // would not fit the 64-register budget of a 1024-thread CTA for four)
     if (tc) {
-        if (P.batch >= 4) push_level<EAGER, true, 4>(P, ell, bc, bn, sn, qlen, bsel);
-        else if (P.batch == 2) push_level<EAGER, true, 2>(P, ell, bc, bn, sn, qlen, bsel);
+        if (!EAGER && P.batch >= 4) push_level<EAGER, true, EAGER ? 2 : 4>(P, ell, bc, bn, sn, qlen, bsel);
+        else if (P.batch >= 2) push_level<EAGER, true, 2>(P, ell, bc, bn, sn, qlen, bsel);
         else push_level<EAGER, true, 1>(P, ell, bc, bn, sn, qlen, bsel);
     } else {
-        if (P.batch >= 4) push_level<EAGER, false, 4>(P, ell, bc, bn, sn, qlen, bsel);
-        else if (P.batch == 2) push_level<EAGER, false, 2>(P, ell, bc, bn, sn, qlen, bsel);
+        if (!EAGER && P.batch >= 4) push_level<EAGER, false, EAGER ? 2 : 4>(P, ell, bc, bn, sn, qlen, bsel);
+        else if (P.batch >= 2) push_level<EAGER, false, 2>(P, ell, bc, bn, sn, qlen, bsel);
         else push_level<EAGER, false, 1>(P, ell, bc, bn, sn, qlen, bsel);
     }
 }
 
 __global__ void __launch_bounds__(BFS_MAX_THREADS, 1) k_bfs(BfsParams P) {
     __shared__ unsigned s_found[BFS_MAX_THREADS];
+    __shared__ float s_mlp[MLP_NW];
+    if (P.policy == BLEST_POLICY_LEARNED && P.mlp) {
+        for (int i = threadIdx.x; i < MLP_NW; i += blockDim.x) s_mlp[i] = P.mlp[i];
+        __syncthreads();
+        P.mlp = s_mlp;
+    }
     const int tid = (int)(blockIdx.x * blockDim.x + threadIdx.x);
     const int nthreads = (int)(gridDim.x * blockDim.x);
     const int lane = lane_id();
@@ -432,6 +540,7 @@ __global__ void __launch_bounds__(BFS_MAX_THREADS, 1) k_bfs(BfsParams P) {
     Ctl *ctl = P.ctl;
     unsigned epoch = 0;
     __shared__ int s_mode;
+    __shared__ long long s_lvl[4];
 
     // ---- level 0 (Algorithm 2/3 init): L = inf except the source, frontier
     // and visited bits hold the source, Q = VSSs of the source's slice set.
@@ -448,7 +557,7 @@ __global__ void __launch_bounds__(BFS_MAX_THREADS, 1) k_bfs(BfsParams P) {
     {
         const int ss = src >> 3;
         const int a = __ldg(&P.realPtrs[ss]), e = __ldg(&P.realPtrs[ss + 1]);
-        for (int k = tid; k < e - a; k += nthreads) P.Q[0][k] = a + k;
+        for (int k = tid; k < e - a; k += nthreads) P.Q[0][k] = make_int2(a + k, ss);
         if (tid == 0) {
             P.SQ[0][0] = ss;
             ctl->qlen[0] = e - a;
@@ -464,12 +573,39 @@ __global__ void __launch_bounds__(BFS_MAX_THREADS, 1) k_bfs(BfsParams P) {
     for (;; ++ell) {
         const int bc = (ell - 1) % 3, bn = ell % 3, bo = (ell + 1) % 3;
         const int sc = (ell - 1) & 3, sn = ell & 3, so = (ell + 2) & 3, sz = (ell + 1) & 3;
-        const int qlen = ld_volatile_i32(&ctl->qlen[sc]);
-        const long long frontier = (long long)*(volatile unsigned long long *)&ctl->newv[sc];
-        const long long fedges = (long long)*(volatile unsigned long long *)&ctl->fedges[sc];
+        // One warp per block reads the level's counters (every thread reading the
+        // same control-block words would pile ~20K requests onto one L2 line),
+        // decides the mode and publishes both through shared memory.
+        if (threadIdx.x < 32) {
+            long long c4[4] = {0, 0, 0, 0};
+            if (threadIdx.x == 0) {
+                c4[0] = ld_volatile_i32(&ctl->qlen[sc]);
+                c4[1] = (long long)*(volatile unsigned long long *)&ctl->newv[sc];
+                c4[2] = (long long)*(volatile unsigned long long *)&ctl->fedges[sc];
+                c4[3] = ell >= 2 ? ld_volatile_i32(&ctl->sqlen[so]) : 0;
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) c4[i] = __shfl_sync(FULL_MASK, c4[i], 0);
+            const long long unv = (long long)P.n - (visited + c4[1]);
+            const int m = c4[0] > 0 ? decide_mode(P, ell, c4[1], c4[2], unv, (int)c4[0]) : 0;
+            if (threadIdx.x == 0) {
+                s_lvl[0] = c4[0];
+                s_lvl[1] = c4[1];
+                s_lvl[2] = c4[2];
+                s_lvl[3] = c4[3];
+                s_mode = m;
+            }
+        }
+        __syncthreads();
+        const int qlen = (int)s_lvl[0];
+        const long long frontier = s_lvl[1];
+        const long long fedges = s_lvl[2];
+        const int sql_old = (int)s_lvl[3];
+        const int mode = s_mode;
+        __syncthreads();   // s_lvl / s_mode are rewritten at the next level start
         visited += frontier;
         const long long unvisited = (long long)P.n - visited;
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (blockIdx.x == 0 && threadIdx.x == 32) {
             const long long t = (long long)global_ns();
             if (ell >= 2 && ell - 2 < P.log_cap) {
                 P.log[ell - 2].t_ns = t - P.log[ell - 2].t_ns;
@@ -479,7 +615,7 @@ __global__ void __launch_bounds__(BFS_MAX_THREADS, 1) k_bfs(BfsParams P) {
             if (qlen > 0 && ell - 1 < P.log_cap) {
                 blest_level_log rec;
                 rec.level = ell;
-                rec.mode = -1;
+                rec.mode = mode;
                 rec.frontier = frontier;
                 rec.frontier_edges = fedges;
                 rec.unvisited = unvisited;
@@ -491,38 +627,17 @@ __global__ void __launch_bounds__(BFS_MAX_THREADS, 1) k_bfs(BfsParams P) {
             }
         }
         if (qlen == 0) break;
-        if (threadIdx.x < 32) {
-            const int m = decide_mode(P, ell, frontier, fedges, unvisited, qlen);
-            if (threadIdx.x == 0) s_mode = m;
-        }
-        __syncthreads();
-        const int mode = s_mode;
-        if (blockIdx.x == 0 && threadIdx.x == 0 && ell - 1 < P.log_cap) P.log[ell - 1].mode = mode;
-
-        // housekeeping for the buffers of level ell-2 and the counters of ell+1
-        if (ell >= 2) {
-            const int sql = ld_volatile_i32(&ctl->sqlen[so]);
-            unsigned char *Fo = reinterpret_cast<unsigned char *>(P.F[bo]);
-            const int *SQo = P.SQ[bo];
-            for (int k = tid; k < sql; k += nthreads) Fo[SQo[k]] = 0;
-        }
-        if (tid == 0) {
-            ctl->qlen[sz] = 0;
-            ctl->sqlen[sz] = 0;
-            ctl->newv[sz] = 0;
-            ctl->fedges[sz] = 0;
-            ctl->scan_v[sz] = 0;
-            ctl->scan_a[sz] = 0;
-        }
 
         if (mode == BLEST_MODE_PUSH_EAGER_CC || mode == BLEST_MODE_PUSH_EAGER_TC) {
             push_dispatch<true>(P, mode == BLEST_MODE_PUSH_EAGER_TC, ell, bc, bn, sn, qlen, bsel);
+            housekeeping(P, ell, bo, sql_old, sz, tid, nthreads);
             if (!grid_barrier(ctl, epoch, P.budget_ns)) return;
         } else {
             if (mode == BLEST_MODE_BOTTOM_UP)
                 bottom_up_level(P, bc, sn, s_found);
             else
                 push_dispatch<false>(P, mode == BLEST_MODE_PUSH_LAZY_TC, ell, bc, bn, sn, qlen, bsel);
+            housekeeping(P, ell, bo, sql_old, sz, tid, nthreads);
             if (!grid_barrier(ctl, epoch, P.budget_ns)) return;
             finalize_level(P, ell, bn, sn);
             if (!grid_barrier(ctl, epoch, P.budget_ns)) return;
@@ -570,7 +685,7 @@ blest_status bfs_prepare(blest_graph *h) {
     if ((bs = dev_alloc_t(h, &h->w.Vn, (size_t)W + 1)) != BLEST_OK) return bs;
     for (int i = 0; i < 3; ++i) {
         if ((bs = dev_alloc_t(h, &h->w.F[i], (size_t)W + 1)) != BLEST_OK) return bs;
-        if ((bs = dev_alloc_t(h, &h->w.Q[i], (size_t)(h->Nv > 0 ? h->Nv : 1))) != BLEST_OK) return bs;
+        if ((bs = dev_alloc_t(h, &h->w.Q[i], (size_t)(h->Nv > 0 ? h->Nv : 1))) != BLEST_OK) return bs;  // int2
         if ((bs = dev_alloc_t(h, &h->w.SQ[i], (size_t)h->Ns + 1)) != BLEST_OK) return bs;
     }
     if ((bs = dev_alloc_t(h, &h->w.ctl, 1)) != BLEST_OK) return bs;
@@ -663,14 +778,15 @@ blest_status bfs_run(blest_graph *h, int32_t source, int32_t *dev_out) {
 namespace {
 
 constexpr long long NOALLOC_MAX_N = 1ll << 20;     // vertices
-constexpr long long NOALLOC_MAX_NV = 1ll << 18;    // VSSs
+constexpr long long NOALLOC_MAX_NV = 1ll << 17;    // VSSs
 constexpr long long NOALLOC_W = NOALLOC_MAX_N / 32;           // bitvector words
 constexpr long long NOALLOC_NS = NOALLOC_MAX_N / 8 + 1;       // slice sets + 1
 constexpr size_t NOALLOC_CTL_BYTES = 256;
 constexpr size_t NOALLOC_BITS_BYTES = 5ull * (NOALLOC_W + 1) * 4;
-constexpr size_t NOALLOC_Q_BYTES = 3ull * NOALLOC_MAX_NV * 4;
+constexpr size_t NOALLOC_Q_BYTES = 3ull * NOALLOC_MAX_NV * 8;   // int2 queue entries
 constexpr size_t NOALLOC_SQ_BYTES = 3ull * NOALLOC_NS * 4;
-constexpr size_t NOALLOC_BYTES = NOALLOC_CTL_BYTES + NOALLOC_BITS_BYTES + NOALLOC_Q_BYTES + NOALLOC_SQ_BYTES + 1024;
+// every sub-array starts on a 256-byte boundary (11 arrays after the control block)
+constexpr size_t NOALLOC_BYTES = NOALLOC_CTL_BYTES + NOALLOC_BITS_BYTES + NOALLOC_Q_BYTES + NOALLOC_SQ_BYTES + 12 * 256;
 static_assert(sizeof(Ctl) <= NOALLOC_CTL_BYTES, "control block fits its slot");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
@@ -721,17 +837,23 @@ extern "C" blest_status blest_bfs_noalloc(const blest_bvss_view *g, int32_t sour
 
     const long long n = g->n, W = (n + 31) / 32, Ns = g->num_slice_sets;
     const long long nv = g->num_vss > 0 ? g->num_vss : 1;
-    unsigned char *p = base;
-    Ctl *ctl = (Ctl *)p;
-    p += NOALLOC_CTL_BYTES;
+    // carve the scratch: control block, 5 bitvectors, 3 queues of 8-byte
+    // entries, 3 slice-set queues, each on a 256-byte boundary
+    size_t off = 0;
+    auto carve = [&](size_t bytes) -> unsigned char * {
+        unsigned char *q = base + off;
+        off = (off + bytes + 255) & ~(size_t)255;
+        return q;
+    };
+    Ctl *ctl = (Ctl *)carve(NOALLOC_CTL_BYTES);
     BfsParams P;
     memset(&P, 0, sizeof P);
-    P.Vc = (unsigned *)p; p += (W + 1) * 4;
-    P.Vn = (unsigned *)p; p += (W + 1) * 4;
-    for (int i = 0; i < 3; ++i) { P.F[i] = (unsigned *)p; p += (W + 1) * 4; }
-    for (int i = 0; i < 3; ++i) { P.Q[i] = (int *)p; p += nv * 4; }
-    for (int i = 0; i < 3; ++i) { P.SQ[i] = (int *)p; p += (Ns + 1) * 4; }
-    if ((size_t)(p - base) > NOALLOC_BYTES) return BLEST_ERR_INTERNAL;
+    P.Vc = (unsigned *)carve((size_t)(W + 1) * 4);
+    P.Vn = (unsigned *)carve((size_t)(W + 1) * 4);
+    for (int i = 0; i < 3; ++i) P.F[i] = (unsigned *)carve((size_t)(W + 1) * 4);
+    for (int i = 0; i < 3; ++i) P.Q[i] = (int2 *)carve((size_t)nv * 8);
+    for (int i = 0; i < 3; ++i) P.SQ[i] = (int *)carve((size_t)(Ns + 1) * 4);
+    if (off > NOALLOC_BYTES) return BLEST_ERR_INTERNAL;
     P.n = (int)n;
     P.W = (int)W;
     P.rowIds = (const int4 *)g->row_ids;

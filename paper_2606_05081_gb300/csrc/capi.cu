@@ -232,6 +232,19 @@ extern "C" blest_status blest_set_engine(blest_handle h, int32_t tc) {
     return BLEST_OK;
 }
 
+extern "C" blest_status blest_set_launch(blest_handle h, int32_t block_threads, int32_t vss_batch) {
+    if (!h || h->many) return BLEST_ERR_INVALID;
+    if (block_threads != 256 && block_threads != 512 && block_threads != 1024) return BLEST_ERR_INVALID;
+    if (vss_batch != 1 && vss_batch != 2 && vss_batch != 4) return BLEST_ERR_INVALID;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return BLEST_ERR_CUDA;
+    const int g = bfs_grid_for(block_threads, nullptr);
+    if (g <= 0) return BLEST_ERR_CUDA;
+    h->block = block_threads;
+    h->grid = g;
+    h->vss_batch = vss_batch;
+    return BLEST_OK;
+}
+
 extern "C" blest_status blest_set_schedule(blest_handle h, const int32_t *modes, int32_t len) {
     if (!h || !modes || len <= 0 || len > (1 << 20)) return BLEST_ERR_INVALID;
     std::vector<int32_t> m((size_t)len);

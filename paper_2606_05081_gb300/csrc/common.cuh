@@ -92,22 +92,24 @@ __device__ __forceinline__ bool grid_barrier(Ctl *ctl, unsigned &epoch, uint64_t
     if (threadIdx.x == 0) {
         epoch += 1;
         const unsigned long long target = (unsigned long long)epoch * gridDim.x;
-        __threadfence();
-        atomicAdd(&ctl->bar, 1ull);
+        // release: the block's writes (ordered before by bar.sync) become visible
+        // no later than the arrival; the acquire loads below order what follows
+        asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(&ctl->bar), "l"(1ull) : "memory");
         const uint64_t t0 = global_ns();
         int ok = 1;
         unsigned spins = 0;
         while (ld_acquire_u64(&ctl->bar) < target) {
-            if (ld_volatile_i32(&ctl->err) != 0) { ok = 0; break; }
-            if ((++spins & 63u) == 0 && global_ns() - t0 > budget_ns) {
-                atomicCAS(&ctl->err, 0, (int)BLEST_ERR_TIMEOUT);
-                atomicCAS(&ctl->timeout_where, 0, (int)epoch);
-                ok = 0;
-                break;
+            if ((++spins & 63u) == 0) {
+                if (ld_volatile_i32(&ctl->err) != 0) { ok = 0; break; }
+                if (global_ns() - t0 > budget_ns) {
+                    atomicCAS(&ctl->err, 0, (int)BLEST_ERR_TIMEOUT);
+                    atomicCAS(&ctl->timeout_where, 0, (int)epoch);
+                    ok = 0;
+                    break;
+                }
             }
-            __nanosleep(20);
+            if (spins > 256) __nanosleep(32);
         }
-        __threadfence();
         if (ld_volatile_i32(&ctl->err) != 0) ok = 0;
         s_ok = ok;
     }

@@ -29,7 +29,7 @@ struct BfsWork {
     int *L = nullptr;                 // n (reordered ids)
     unsigned *Vc = nullptr, *Vn = nullptr;
     unsigned *F[3] = {nullptr, nullptr, nullptr};
-    int *Q[3] = {nullptr, nullptr, nullptr};
+    int2 *Q[3] = {nullptr, nullptr, nullptr};   // {VSS id, slice set}
     int *SQ[3] = {nullptr, nullptr, nullptr};
     Ctl *ctl = nullptr;
     blest_level_log *log = nullptr;

@@ -144,13 +144,12 @@ __device__ void ms_stage1(const MsParams &P, int qlen, const int *Qc, int dl, in
 }
 
 template <int KW>
-__device__ void ms_stage2(const MsParams &P, int ell, int dl, int qn) {
+__device__ void ms_stage2(const MsParams &P, int ell, int dl, int qn, int dcount) {
     constexpr int G = 32 / KW;
     const int lane = lane_id();
     const int g = lane / KW, w = lane % KW;
     const int gwarp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
-    const int dcount = ld_volatile_i32(&P.ctl->dlen[dl]);
     const int *dlist = P.dlist[dl];
     for (int base = gwarp * G; base < dcount; base += nwarps * G) {
         const int i = base + g;
@@ -241,7 +240,10 @@ __global__ void __launch_bounds__(MS_BLOCK, 1) k_msbfs(MsParams P) {
     if (!ms_barrier(ctl, epoch, P.budget_ns)) return;
     {
         // enqueue the source slice sets and clear their flags
-        const int cnt = ld_volatile_i32(&ctl->dlen[1]);
+        __shared__ int s_c0;
+        if (threadIdx.x == 0) s_c0 = ld_volatile_i32(&ctl->dlen[1]);
+        __syncthreads();
+        const int cnt = s_c0;
         const int gwarp = (int)(tid >> 5), nwarps = (int)(nthreads >> 5);
         for (int b = gwarp * 32; b < cnt; b += nwarps * 32) {
             const int i = b + lane_id();
@@ -256,15 +258,24 @@ __global__ void __launch_bounds__(MS_BLOCK, 1) k_msbfs(MsParams P) {
     if (!ms_barrier(ctl, epoch, P.budget_ns)) return;
 
     int ell = 1;
+    __shared__ int s_cnt;
     for (;; ++ell) {
         const int qc = (ell - 1) & 1, qn = ell & 1, dl = ell & 1;
-        const int qlen = ld_volatile_i32(&ctl->qlen[qc]);
+        // one thread per block reads the shared counter (see k_bfs)
+        if (threadIdx.x == 0) s_cnt = ld_volatile_i32(&ctl->qlen[qc]);
+        __syncthreads();
+        const int qlen = s_cnt;
+        __syncthreads();
         if (qlen == 0) break;
         if (tid == 0) ctl->qlen[qn] = 0;
         ms_stage1<KW>(P, qlen, P.Q[qc], dl, s_rows, s_m);
         if (!ms_barrier(ctl, epoch, P.budget_ns)) return;
+        if (threadIdx.x == 0) s_cnt = ld_volatile_i32(&ctl->dlen[dl]);
+        __syncthreads();
+        const int dcount = s_cnt;
+        __syncthreads();
         if (tid == 0) ctl->dlen[dl ^ 1] = 0;
-        ms_stage2<KW>(P, ell, dl, qn);
+        ms_stage2<KW>(P, ell, dl, qn, dcount);
         if (!ms_barrier(ctl, epoch, P.budget_ns)) return;
     }
     if (tid == 0) ctl->nlevels = ell - 1;

@@ -76,7 +76,7 @@ def test_noalloc_refuses_graphs_beyond_the_scratch_limit(blest):
         rc = blest._lib.blest_bfs_noalloc(ctypes.byref(big), 0, out.data_ptr(), None)
         assert rc == blest.ERR_UNSUPPORTED
         big = blest.BvssView.from_buffer_copy(view)
-        big.num_vss = (1 << 18) + 1
+        big.num_vss = (1 << 17) + 1
         rc = blest._lib.blest_bfs_noalloc(ctypes.byref(big), 0, out.data_ptr(), None)
         assert rc == blest.ERR_UNSUPPORTED
         host = np.empty(g.n, np.int32)     # levels must be device memory
