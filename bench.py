@@ -141,8 +141,8 @@ def algorithmic_bytes(log, n: int, reached: int) -> float:
       lazy / bottom-up level: stage 2 reads V_curr and V_next (8 B per 32
         vertices) and writes V_curr and F for changed words (8 B per new vertex
         at most); bottom-up stage 1 reads V_curr and the in-neighbour mask
-        (8 B per 32 vertices), two row pointers per probed vertex (16 B) and
-        4 B per in-neighbour id read;
+        (8 B per 32 vertices), the 16-byte head (first four in-neighbours) of
+        each probed vertex and 4 B per further in-neighbour id read;
       every newly visited vertex: its level (4 B) and its degree (4 B);
       init: 4 B per vertex of levels and 5 bitvectors (20 B per 32 vertices).
     The caller adds 8 B per vertex for the un-permute of a reordered graph."""

@@ -120,7 +120,7 @@ typedef struct blest_level_log {
     int64_t queue;           /* |Q_curr|: VSSs scheduled */
     int64_t t_ns;            /* device time of the level (globaltimer) */
     int64_t scanned_vertices;/* bottom-up levels: unvisited vertices probed */
-    int64_t scanned_arcs;    /* bottom-up levels: in-neighbour ids read */
+    int64_t scanned_arcs;    /* bottom-up levels: in-neighbour ids read beyond each row's first four */
 } blest_level_log;
 
 /* Fill *opts with the defaults documented above. */

@@ -35,6 +35,7 @@ struct BfsParams {
     const int *__restrict__ col;
     const int *__restrict__ deg;
     const unsigned *__restrict__ nz;  // bit u set iff u has an in-neighbour (bottom-up levels)
+    const int4 *__restrict__ head;    // first four in-neighbours of each vertex
     int *L;
     unsigned *Vc, *Vn;
     unsigned *F[3];
@@ -326,7 +327,6 @@ __device__ void bottom_up_level(const BfsParams &P, int bc, int slot, unsigned *
         // two compacted vertices per lane per round: idx = b + lane and b + 32 + lane
         for (int b = 0; b < total; b += 64) {
             int u[2];
-            long long p[2], e[2];
             bool act[2], hit[2];
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
@@ -345,43 +345,47 @@ __device__ void bottom_up_level(const BfsParams &P, int bc, int slot, unsigned *
                 const int ej = __shfl_sync(FULL_MASK, excl, j);
                 u[k] = act[k] ? ((base + j) << 5) + nth_set_bit(uj, idx - ej) : 0;
             }
+            // round 1: the first four in-neighbours (rows sorted by descending
+            // degree) come from one coalesced 16-byte head load per vertex
+            int4 hd[2];
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
-                p[k] = act[k] ? __ldg(&P.rp[u[k]]) : 0;
-                e[k] = act[k] ? __ldg(&P.rp[u[k] + 1]) : 0;
+                hd[k] = act[k] ? __ldg(&P.head[u[k]]) : make_int4(-1, -1, -1, -1);
                 if (act[k]) sv += 1;
             }
-            // first probe round of both vertices together, then the rare longer scans
-            int v[2][4];
             unsigned fw[2][4];
 #pragma unroll
             for (int k = 0; k < 2; ++k)
 #pragma unroll
-                for (int q = 0; q < 4; ++q) v[k][q] = (p[k] + q < e[k]) ? __ldg(&P.col[p[k] + q]) : -1;
+                for (int q = 0; q < 4; ++q) {
+                    const int vq = pick(hd[k], q);
+                    fw[k][q] = vq >= 0 ? Fc[vq >> 5] : 0u;
+                }
 #pragma unroll
             for (int k = 0; k < 2; ++k)
 #pragma unroll
-                for (int q = 0; q < 4; ++q) fw[k][q] = v[k][q] >= 0 ? Fc[v[k][q] >> 5] : 0u;
+                for (int q = 0; q < 4; ++q) {
+                    const int vq = pick(hd[k], q);
+                    hit[k] |= (vq >= 0) && ((fw[k][q] >> (vq & 31)) & 1u);
+                }
+            // rows longer than four: the rest of the row, four ids per round
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
-                sa += (unsigned long long)((e[k] - p[k]) < 4 ? (e[k] - p[k] > 0 ? e[k] - p[k] : 0) : 4);
+                if (act[k] && !hit[k] && hd[k].w >= 0) {
+                    long long p = __ldg(&P.rp[u[k]]) + 4;
+                    const long long e = __ldg(&P.rp[u[k] + 1]);
+                    while (!hit[k] && p < e) {
+                        sa += (unsigned long long)((e - p) < 4 ? (e - p) : 4);
+                        int w4[4];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) hit[k] |= (v[k][q] >= 0) && ((fw[k][q] >> (v[k][q] & 31)) & 1u);
-                p[k] += 4;
-            }
+                        for (int q = 0; q < 4; ++q) w4[q] = (p + q < e) ? __ldg(&P.col[p + q]) : -1;
+                        unsigned f4[4];
 #pragma unroll
-            for (int k = 0; k < 2; ++k) {
-                while (act[k] && !hit[k] && p[k] < e[k]) {
-                    sa += (unsigned long long)((e[k] - p[k]) < 4 ? (e[k] - p[k]) : 4);
-                    int w4[4];
+                        for (int q = 0; q < 4; ++q) f4[q] = w4[q] >= 0 ? Fc[w4[q] >> 5] : 0u;
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) w4[q] = (p[k] + q < e[k]) ? __ldg(&P.col[p[k] + q]) : -1;
-                    unsigned f4[4];
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) f4[q] = w4[q] >= 0 ? Fc[w4[q] >> 5] : 0u;
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) hit[k] |= (w4[q] >= 0) && ((f4[q] >> (w4[q] & 31)) & 1u);
-                    p[k] += 4;
+                        for (int q = 0; q < 4; ++q) hit[k] |= (w4[q] >= 0) && ((f4[q] >> (w4[q] & 31)) & 1u);
+                        p += 4;
+                    }
                 }
                 if (act[k] && hit[k]) atomicOr(&found[(u[k] >> 5) - base], 1u << (u[k] & 31));
             }
@@ -737,6 +741,7 @@ blest_status bfs_run(blest_graph *h, int32_t source, int32_t *dev_out) {
     P.sched_len = h->sched_len;
     P.mlp = h->d_mlp;
     P.nz = h->g.nz;
+    P.head = h->g.head;
     P.batch = h->vss_batch;
     P.avg_deg = h->n ? (float)((double)h->nnz / (double)h->n) : 0.f;
     P.budget_ns = (unsigned long long)h->timeout_ms * 1000000ull;

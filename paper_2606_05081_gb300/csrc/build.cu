@@ -220,6 +220,32 @@ __global__ void k_tcsr_tail(const unsigned long long *__restrict__ k, int64_t m,
         rp[r] = m;
 }
 
+// Bottom-up rows sorted by descending degree of the in-neighbour (hubs are
+// the likeliest frontier members, so they are probed first; levels do not
+// depend on the probe order).  key = row << 31 | (2^31 - 1 - degree).
+__global__ void k_bu_keys(const long long *__restrict__ rp, const int *__restrict__ col, int64_t n,
+                          const int *__restrict__ deg, unsigned long long *keys, unsigned *vals) {
+    const int lane = lane_id();
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t j = gw; j < n; j += nw)
+        for (long long p = rp[j] + lane; p < rp[j + 1]; p += 32) {
+            const int v = col[p];
+            keys[p] = ((unsigned long long)j << 31) | (unsigned long long)(0x7FFFFFFF - deg[v]);
+            vals[p] = (unsigned)v;
+        }
+}
+
+// head[u] = the first four in-neighbours of u (-1 where the row is shorter)
+__global__ void k_bu_head(const long long *__restrict__ rp, const int *__restrict__ col, int64_t n, int4 *head) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += stride) {
+        const long long a = rp[u], d = rp[u + 1] - a;
+        head[u] = make_int4(d > 0 ? col[a] : -1, d > 1 ? col[a + 1] : -1, d > 2 ? col[a + 2] : -1,
+                            d > 3 ? col[a + 3] : -1);
+    }
+}
+
 __global__ void k_inverse_perm(const int *__restrict__ new_of_old, int64_t n, int *old_of_new) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
@@ -425,6 +451,32 @@ blest_status build_graph(blest_graph *h, const int64_t *row_ptr, const int32_t *
         h->g.col = col;
     }
     BUILD_TRY(cudaGetLastError());
+    // rows by descending neighbour degree, and the 4-neighbour head of each row
+    {
+        long long nb = 0;
+        BUILD_TRY(cudaMemcpyAsync(&nb, h->g.rp + n, sizeof(long long), cudaMemcpyDeviceToHost, st));
+        BUILD_TRY(cudaStreamSynchronize(st));
+        if (nb > 0) {
+            unsigned long long *kk = pool.get<unsigned long long>((size_t)nb + 1);
+            unsigned long long *ka = pool.get<unsigned long long>((size_t)nb + 1);
+            unsigned *vv = pool.get<unsigned>((size_t)nb + 1);
+            unsigned *va = pool.get<unsigned>((size_t)nb + 1);
+            long long *hist = pool.get<long long>(radix_hist_elems(nb));
+            long long *stmp2 = pool.get<long long>(scan_tmp_elems((int64_t)radix_hist_elems(nb)) + 16);
+            int *colbu = nullptr;
+            POOL_CHECK(pool);
+            if ((bs = dev_alloc_t(h, &colbu, (size_t)nb)) != BLEST_OK) return bs;
+            k_bu_keys<<<grid_for(n * 32, TB, 1 << 16), TB, 0, st>>>(h->g.rp, h->g.col, n, deg, kk, vv);
+            BUILD_TRY(radix_sort_u64(kk, vv, ka, va, nb, B + 31, hist, stmp2, st));
+            BUILD_TRY(cudaMemcpyAsync(colbu, vv, (size_t)nb * 4, cudaMemcpyDeviceToDevice, st));
+            h->g.col = colbu;
+            pool.release(kk); pool.release(ka); pool.release(vv); pool.release(va);
+            pool.release(hist); pool.release(stmp2);
+        }
+        if ((bs = dev_alloc_t(h, &h->g.head, (size_t)n)) != BLEST_OK) return bs;
+        k_bu_head<<<grid_for(n, TB, 1 << 16), TB, 0, st>>>(h->g.rp, h->g.col, n, h->g.head);
+        BUILD_TRY(cudaGetLastError());
+    }
     BUILD_TRY(cudaEventRecord(e1, st));
     BUILD_TRY(cudaEventSynchronize(e1));
     float ms = 0.f;

@@ -20,6 +20,7 @@ struct DevGraph {
     int *col = nullptr;
     int *deg = nullptr;        // out-degree in the reordered id space (features, TEPS)
     unsigned *nz = nullptr;    // bit u set iff u has an in-neighbour (bottom-up skips the rest)
+    int4 *head = nullptr;      // first four in-neighbours of each vertex (bottom-up first probe)
     // permutation (nullptr when no reordering): new_of_old, old_of_new
     int *new_of_old = nullptr;
     int *old_of_new = nullptr;
