@@ -65,6 +65,8 @@ WORKLOADS = {
     "rmat24_jaccard": ["rmat24_jaccard"],
 }
 DEFAULT_WORKLOAD = "sssp_pair"
+# the other rows of the path, each with its own JSON line
+EXTRA_WORKLOADS = ["msbfs_rmat22", "closeness_rmat18", "closeness_grid2048_part", "bfs_many_ba10k"]
 NUM_SOURCES = 64
 METRIC = "GTEPS (harm. mean/source), single-source BFS"
 
@@ -261,7 +263,7 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS) + EXTRA_WORKLOADS)
     ap.add_argument("--impl", default="blest", choices=["blest", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sources", type=int, default=NUM_SOURCES)
@@ -283,6 +285,11 @@ def main():
             dist.destroy_process_group()
         return
     args.warmup = max(args.warmup, 3)
+    if args.workload in EXTRA_WORKLOADS:
+        run_extra(args, rank, world, local)
+        if dist:
+            dist.destroy_process_group()
+        return
 
     import torch
     import paper_2606_05081_gb300 as blest
@@ -445,6 +452,121 @@ def main():
         r.h.close()
     if dist:
         dist.destroy_process_group()
+
+
+def _events(torch):
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def run_extra(args, rank, world, local):
+    """Multi-source BFS (§6.1), closeness (§6.2) and batched small graphs:
+    device time with CUDA events on the library's stream, inputs resident."""
+    import torch
+    import paper_2606_05081_gb300 as blest
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    hbm, peak_kind = peaks()
+    line = {"n_gpus": world, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic"}
+    if args.workload == "msbfs_rmat22":
+        g = gg.rmat(22, 16, seed=3)
+        h = blest.build(g.n, g.row_ptr, g.col)
+        h.set_stream(stream.cuda_stream, True)
+        deg = torch.from_numpy(np.diff(g.row_ptr)).to(dev)
+        res = {}
+        for k in (64, 256, 1024):
+            srcs = gg.sources(g, k, 22 + k)
+            out = torch.empty((k, g.n), dtype=torch.int32, device=dev)
+            sd = torch.from_numpy(srcs).to(dev)
+            for _ in range(args.warmup):
+                h.msbfs(sd, out)
+            h.sync()
+            a, b = _events(torch)
+            a.record(stream)
+            for _ in range(args.steps):
+                h.msbfs(sd, out)
+            b.record(stream)
+            torch.cuda.synchronize()
+            h.sync()
+            ms = a.elapsed_time(b) / args.steps
+            reached = out >= 0
+            arcs = int((reached.to(torch.int64) * deg[None, :]).sum().item())
+            floor = 8.0 * k * g.n      # -1 initialisation and one level write per (source, vertex)
+            res[k] = {"ms": ms, "gteps": arcs / 2 / (ms * 1e-3) / 1e9,
+                      "level_floor_gbs": floor / (ms * 1e-3) / 1e9}
+            del out
+        line.update({"metric": "GTEPS (aggregate over sources), multi-source BFS", "value": res[1024]["gteps"],
+                     "unit": "GTEPS", "ms_per_step": res[1024]["ms"],
+                     "config": {"workload": args.workload, "graph": "RMAT scale 22, edge factor 16", "n": g.n,
+                                "nnz": g.nnz, "kappa": [64, 256, 1024], "levels": "int32, source-major"},
+                     "per_kappa": res,
+                     "roofline": {"bound": "hbm", "achieved": res[1024]["level_floor_gbs"], "peak": hbm,
+                                  "unit": "GB/s", "frac": res[1024]["level_floor_gbs"] / hbm, "traffic": None,
+                                  "peak_kind": peak_kind,
+                                  "bytes": "level-array floor only: 8 B per (source, vertex)"},
+                     "gpu_launches": args.steps * 3})
+    elif args.workload.startswith("closeness"):
+        if args.workload == "closeness_rmat18":
+            g = gg.rmat(18, 16, seed=4)
+            first, count = 0, g.n
+            desc = "RMAT scale 18, edge factor 16, all sources"
+        else:
+            g = gg.grid(2048, 2048, 0.05, 0.001, seed=4)
+            first, count = 0, 8 * 1024
+            desc = "2048x2048 road-like grid, sources 0..8191 (8 of the 4096 batches of 1024)"
+        h = blest.build(g.n, g.row_ptr, g.col)
+        h.set_stream(stream.cuda_stream, False)
+        far = torch.empty(g.n, dtype=torch.int64, device=dev)
+        reach = torch.empty(g.n, dtype=torch.int64, device=dev)
+        h.closeness_range(first, min(1024, count), far, reach)
+        torch.cuda.synchronize()
+        a, b = _events(torch)
+        a.record(stream)
+        h.closeness_range(first, count, far, reach)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        # traversed edges: each source reaches its component; sum over targets of reach = pairs
+        pairs = int(reach.sum().item())
+        mean_deg = g.nnz / g.n
+        line.update({"metric": "BFS per second and GTEPS (aggregate), all-source closeness",
+                     "value": count / (ms * 1e-3), "unit": "BFS/s", "ms_per_step": ms,
+                     "gteps_est": pairs * mean_deg / 2 / (ms * 1e-3) / 1e9,
+                     "config": {"workload": args.workload, "graph": desc, "n": g.n, "nnz": g.nnz,
+                                "sources": count, "batch": 1024},
+                     "full_run_estimate_s": (g.n / count) * ms * 1e-3,
+                     "gpu_launches": (count + 1023) // 1024})
+    else:
+        b = gg.ba_batch(10000, 1000, 100000, 4, seed=3)
+        srcs = np.zeros(b.g, np.int32)            # vertex 0 of every graph
+        h = blest.build_many(b)
+        h.set_stream(stream.cuda_stream, True)
+        out = torch.empty(int(b.vtx_off[-1]), dtype=torch.int32, device=dev)
+        for _ in range(args.warmup):
+            h.bfs_many(srcs, out)
+        h.sync()
+        a, e = _events(torch)
+        a.record(stream)
+        for _ in range(args.steps):
+            h.bfs_many(srcs, out)
+        e.record(stream)
+        torch.cuda.synchronize()
+        h.sync()
+        ms = a.elapsed_time(e) / args.steps
+        # traversed arcs: out-degrees of the reached vertices of every graph
+        degs = np.concatenate([np.diff(b.row_ptr[b.vtx_off[i] + i: b.vtx_off[i + 1] + i + 1]) for i in range(b.g)])
+        reached = (out >= 0).cpu().numpy()
+        arcs = int(degs[reached].sum())
+        line.update({"metric": "GTEPS (aggregate), batched BFS over 10,000 BA graphs", "value": arcs / 2 / (ms * 1e-3) / 1e9,
+                     "unit": "GTEPS", "ms_per_step": ms,
+                     "config": {"workload": args.workload,
+                                "graph": "10,000 Barabasi-Albert graphs, n log-uniform in [1e3, 1e5], m = 4",
+                                "total_vertices": int(b.vtx_off[-1]), "total_arcs": arcs, "source": "vertex 0"},
+                     "gpu_launches": args.steps})
+    if rank == 0:
+        print(json.dumps(line), flush=True)
 
 
 if __name__ == "__main__":
