@@ -80,7 +80,7 @@ enum {
 
 typedef struct blest_build_opts {
     int32_t reorder;         /* BLEST_REORDER_*; default NONE */
-    int32_t sigma;           /* slice width; 8 (default) */
+    int32_t sigma;           /* slice width: 8 (default), 16 or 32 (§3.1) */
     int32_t directed;        /* 0: CSR is symmetric (undirected); 1: directed */
     int32_t jaccard_window;  /* W of Algorithm 1; default 65536, multiple of sigma */
     int32_t probe_switch;    /* 1 (default): the 3-source switching probe of §7.1 runs at build */
@@ -91,6 +91,10 @@ typedef struct blest_build_opts {
     int32_t timeout_ms;      /* budget of each device-side wait; default 5000 */
     int32_t block_threads;   /* CTA size of the persistent kernels: 256, 512 or 1024; 0 = 512 */
     int32_t vss_batch;       /* VSSs a warp keeps in flight in top-down levels: 1, 2, 4; 0 = 2 */
+    int32_t tau;             /* slices per VSS.  0 = 32 * (32 / sigma), the warp-wide VSS of §3.1
+                                (sigma 8: 128, 16: 64, 32: 32).  sigma = 8 also takes 32: a VSS
+                                spans 8 lanes and a warp works on four at once (for graphs whose
+                                slice sets hold few slices, e.g. road-like grids) */
 } blest_build_opts;
 
 /* Build-time facts about a handle. */
@@ -108,6 +112,7 @@ typedef struct blest_info {
     int32_t block_threads;
     double build_ms;         /* device time of the build */
     int64_t device_bytes;    /* device memory held by the handle */
+    int32_t tau;             /* slices per VSS */
 } blest_info;
 
 /* One record per BFS level of the last single-source BFS. */
@@ -121,6 +126,10 @@ typedef struct blest_level_log {
     int64_t t_ns;            /* device time of the level (globaltimer) */
     int64_t scanned_vertices;/* bottom-up levels: unvisited vertices probed */
     int64_t scanned_arcs;    /* bottom-up levels: in-neighbour ids read beyond each row's first four */
+    int64_t slots;           /* BVSS slots scheduled: tau * queue (the active-slice input of the
+                                learned policy) */
+    int64_t t_stage1_ns;     /* device time of stage 1 alone (lazy and bottom-up levels; equals t_ns
+                                for eager levels) */
 } blest_level_log;
 
 /* Fill *opts with the defaults documented above. */
@@ -129,7 +138,10 @@ void blest_default_opts(blest_build_opts *opts);
 /* Build a handle from a CSR graph (§3.1 BVSS construction, §4 reordering).
  * n >= 1.  opts may be NULL (defaults).  The handle owns all device memory
  * and must be released with blest_destroy.  Returns INVALID for a malformed
- * CSR, UNSUPPORTED for sigma != 8 or n >= 2^31. */
+ * CSR or a sigma / tau pair other than (8, 32), (8, 128), (16, 64),
+ * (32, 32); UNSUPPORTED for n >= 2^31, for engine_tc = 1 with a layout other
+ * than sigma = 8, tau = 128 (the Fig. 3 fragment layout), or when the BVSS
+ * would need 2^31 or more row-id slots. */
 blest_status blest_build(int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
                          const blest_build_opts *opts, blest_handle *out);
 
@@ -139,7 +151,9 @@ blest_status blest_bfs(blest_handle h, int32_t source, int32_t *levels);
 
 /* Multi-source BFS (§6.1, Algorithm 5): k sources (1 <= k <= 1024,
  * duplicates allowed) as bit lanes.  levels: k*n int32, levels[c*n + v] is
- * the distance from sources[c] to v. */
+ * the distance from sources[c] to v.  Needs sigma = 8 (getVI of §6.1 groups
+ * the eight vertices of a slice set); UNSUPPORTED otherwise, and so are the
+ * closeness calls below. */
 blest_status blest_msbfs(blest_handle h, const int32_t *sources, int32_t k, int32_t *levels);
 
 /* Exact closeness centrality by all-source BFS in 1024-lane batches (§6.2).
@@ -160,7 +174,8 @@ blest_status blest_closeness_range(blest_handle h, int64_t first, int64_t count,
 /* Many small graphs in one handle: graph i has vertices [vtx_off[i],
  * vtx_off[i+1]) (local ids from 0) and arcs [edge_off[i], edge_off[i+1]);
  * its local row pointer is row_ptr[vtx_off[i] + i .. vtx_off[i+1] + i]
- * (offsets relative to edge_off[i]).  Undirected graphs only. */
+ * (offsets relative to edge_off[i]).  Undirected graphs only; the BVSS is
+ * the default sigma = 8, tau = 128 one (other sigma / tau: UNSUPPORTED). */
 blest_status blest_build_many(int32_t g, const int64_t *vtx_off, const int64_t *edge_off,
                               const int64_t *row_ptr, const int32_t *col_idx_local,
                               const blest_build_opts *opts, blest_handle *out);
@@ -174,7 +189,10 @@ blest_status blest_bfs_many(blest_handle h, const int32_t *sources, int32_t *lev
 blest_status blest_set_policy(blest_handle h, int32_t policy, int32_t fixed_mode);
 
 /* Hit-test engine of the heuristic policy's top-down levels: 1 = b1 MMA
- * (Fig. 3 layout, the paper's), 0 = CUDA cores. */
+ * (Fig. 3 layout, the paper's), 0 = CUDA cores.  The MMA needs sigma = 8,
+ * tau = 128 (UNSUPPORTED otherwise); on other layouts a fixed policy or
+ * schedule that names a tensor-core mode runs its CUDA-core twin, and the
+ * level log records the mode that ran. */
 blest_status blest_set_engine(blest_handle h, int32_t tc);
 
 /* Launch shape of the single-source kernel: block_threads in {256, 512,
@@ -197,9 +215,11 @@ blest_status blest_last_timings(blest_handle h, blest_level_log *buf, int64_t ca
 blest_status blest_get_info(blest_handle h, blest_info *info);
 
 /* Copy the device BVSS arrays (§3.1) to caller buffers (host or device):
- * rowIds N_v*32*theta int32, masks N_v*32 uint32, realPtrs N_s+1 int32,
- * virtualToReal N_v int32.  Any pointer may be NULL.  Ids are in the
- * reordered space (see blest_get_perm). */
+ * rowIds N_v*tau int32 (slice k of VSS v at v*tau + k), masks N_v*tau/theta
+ * uint32 (theta = 32/sigma slices per word, slice c of a word in bits
+ * [c*sigma, (c+1)*sigma)), realPtrs N_s+1 int32, virtualToReal N_v int32.
+ * Any pointer may be NULL.  Ids are in the reordered space (see
+ * blest_get_perm). */
 blest_status blest_get_bvss(blest_handle h, int32_t *row_ids, uint32_t *masks, int32_t *real_ptrs,
                             int32_t *virtual_to_real);
 
@@ -229,7 +249,7 @@ const char *blest_status_string(blest_status s);
 #define BLEST_MLP_NW 1457
 
 /* Raw features of level-log records, exactly as the BFS kernel computes
- * them: out[n*6] = log1p of (frontier, frontier_edges, unvisited, 128*queue,
+ * them: out[n*6] = log1p of (frontier, frontier_edges, unvisited, slots,
  * level, avg_deg). */
 blest_status blest_mlp_features(const blest_level_log *recs, int64_t n, float avg_deg, float *out);
 
@@ -274,7 +294,7 @@ blest_status blest_mlp_predict(const float *weights, const float *features, int6
  *    the device status. */
 typedef struct blest_bvss_view {
     int64_t n;                       /* vertices */
-    int64_t num_slice_sets;          /* N_s = ceil(n / 8) */
+    int64_t num_slice_sets;          /* N_s = ceil(n / 8): sigma = 8, tau = 128 layout only */
     int64_t num_vss;                 /* N_v */
     const int32_t *row_ids;          /* device, N_v*128 (blest_get_bvss layout) */
     const uint32_t *masks;           /* device, N_v*32 */

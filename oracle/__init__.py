@@ -128,7 +128,7 @@ def closeness(g, nthreads: int = 0):
 
 
 # --------------------------------------------------------------- BVSS (§3.1)
-def bvss(g, sigma: int = 8) -> dict:
+def bvss(g, sigma: int = 8, tau: int | None = None) -> dict:
     """The BVSS arrays of §3.1, built from their definition.
 
     A is the transposed adjacency (§2): A[i][j] = 1 iff (j, i) is an arc, so
@@ -137,17 +137,22 @@ def bvss(g, sigma: int = 8) -> dict:
     a nonzero there, each with a sigma-bit mask (bit j - s*sigma, least
     significant bit first, the convention of Fig. 1).  Slices of a slice set
     are kept in ascending row order (a choice; the paper leaves the order
-    open).  Each slice set is cut into VSSs of at most tau = 32*theta slices
-    (theta = 32/sigma); the last VSS of a set is padded with zero masks and
-    row id 0.  Slice k of VSS v sits at slot v*tau + k, so lane l of a warp
-    owns slots v*tau + l*theta + c, c < theta, and its 32-bit mask word
-    holds mask c in bits [c*sigma, (c+1)*sigma).  realPtrs (N_s + 1) maps a
-    slice set to its VSS range; virtualToReal (N_v) maps back.  Slice sets
-    with no slice get no VSS.
+    open).  A 32-bit word holds theta = 32/sigma masks.  Each slice set is
+    cut into VSSs of at most tau slices -- by default tau = 32*theta, one
+    word per lane of a warp; tau = 32 with sigma = 8 gives VSSs of eight
+    lane words -- and the last VSS of a set is padded with zero masks and
+    row id 0.  Slice k of VSS v sits at slot v*tau + k, so lane word l of
+    the VSS owns slots v*tau + l*theta + c, c < theta, and holds mask c in
+    bits [c*sigma, (c+1)*sigma).  realPtrs (N_s + 1) maps a slice set to its
+    VSS range; virtualToReal (N_v) maps back.  Slice sets with no slice get
+    no VSS.
     """
     assert sigma in (8, 16, 32)
     theta = 32 // sigma
-    tau = 32 * theta
+    if tau is None:
+        tau = 32 * theta
+    assert tau % theta == 0 and tau in (32, 64, 128)
+    lanes = tau // theta
     n = g.n
     Ns = (n + sigma - 1) // sigma
     deg = np.diff(g.row_ptr).astype(np.int64)
@@ -175,9 +180,9 @@ def bvss(g, sigma: int = 8) -> dict:
     mslot = np.zeros(Nv * tau, np.uint64)
     mslot[slot] = smask
     shifts = (np.arange(theta, dtype=np.uint64) * np.uint64(sigma))
-    masks = np.bitwise_or.reduce(mslot.reshape(Nv * 32, theta) << shifts, axis=1) if Nv else \
+    masks = np.bitwise_or.reduce(mslot.reshape(Nv * lanes, theta) << shifts, axis=1) if Nv else \
         np.zeros(0, np.uint64)
-    return dict(sigma=sigma, theta=theta, tau=tau, n=n, Ns=Ns, Nv=Nv,
+    return dict(sigma=sigma, theta=theta, tau=tau, lanes=lanes, n=n, Ns=Ns, Nv=Nv,
                 rowIds=rowIds.astype(np.int32), masks=masks.astype(np.uint32),
                 slot_masks=mslot.astype(np.uint32),
                 realPtrs=realPtrs.astype(np.int32), v2r=v2r.astype(np.int32),
@@ -186,15 +191,15 @@ def bvss(g, sigma: int = 8) -> dict:
 
 def update_divergence(b: dict) -> float:
     """U_div of §4.2: for each VSS, each of its theta columns (the slices a
-    lane holds at position c) has a column divergence = population standard
-    deviation of the row ids whose masks are nonzero; the set divergence
-    averages it over the non-empty columns; U_div averages the set
-    divergence over all N_v VSSs."""
-    Nv, theta = b["Nv"], b["theta"]
+    lane word holds at position c, over the VSS's lane words) has a column
+    divergence = population standard deviation of the row ids whose masks
+    are nonzero; the set divergence averages it over the non-empty columns;
+    U_div averages the set divergence over all N_v VSSs."""
+    Nv, theta, lanes = b["Nv"], b["theta"], b["lanes"]
     if Nv == 0:
         return 0.0
-    R = b["rowIds"].astype(np.float64).reshape(Nv, 32, theta)
-    M = (b["slot_masks"].reshape(Nv, 32, theta) != 0)
+    R = b["rowIds"].astype(np.float64).reshape(Nv, lanes, theta)
+    M = (b["slot_masks"].reshape(Nv, lanes, theta) != 0)
     cnt = M.sum(axis=1)                                        # [Nv, theta]
     safe = np.maximum(cnt, 1)
     mean = (R * M).sum(axis=1) / safe

@@ -26,14 +26,14 @@ OFF_B3 = OFF_W3 + OUT * H
 NW = OFF_B3 + OUT
 
 
-def raw_features(frontier, fedges, unvisited, queue, level, avg_deg):
+def raw_features(frontier, fedges, unvisited, slots, level, avg_deg):
     """The six inputs: log1p of frontier vertices, frontier out-arcs,
-    unvisited vertices, active BVSS slices (128 per scheduled VSS), level
+    unvisited vertices, active BVSS slots (tau per scheduled VSS), level
     index and average degree."""
     return np.stack([np.log1p(np.asarray(frontier, np.float64)),
                      np.log1p(np.asarray(fedges, np.float64)),
                      np.log1p(np.maximum(np.asarray(unvisited, np.float64), 0)),
-                     np.log1p(128.0 * np.asarray(queue, np.float64)),
+                     np.log1p(np.asarray(slots, np.float64)),
                      np.log1p(np.asarray(level, np.float64)),
                      np.log1p(np.broadcast_to(np.asarray(avg_deg, np.float64), np.shape(frontier)))], axis=-1)
 

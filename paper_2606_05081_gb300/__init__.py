@@ -37,7 +37,7 @@ class BuildOpts(ctypes.Structure):
                 ("jaccard_window", ctypes.c_int32), ("probe_switch", ctypes.c_int32),
                 ("engine_tc", ctypes.c_int32), ("eta", ctypes.c_float), ("udiv_threshold", ctypes.c_double),
                 ("timeout_ms", ctypes.c_int32), ("block_threads", ctypes.c_int32),
-                ("vss_batch", ctypes.c_int32)]
+                ("vss_batch", ctypes.c_int32), ("tau", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -46,14 +46,14 @@ class Info(ctypes.Structure):
                 ("update_divergence", ctypes.c_double), ("lazy", ctypes.c_int32),
                 ("switching", ctypes.c_int32), ("reorder", ctypes.c_int32), ("sigma", ctypes.c_int32),
                 ("grid_blocks", ctypes.c_int32), ("block_threads", ctypes.c_int32),
-                ("build_ms", ctypes.c_double), ("device_bytes", ctypes.c_int64)]
+                ("build_ms", ctypes.c_double), ("device_bytes", ctypes.c_int64), ("tau", ctypes.c_int32)]
 
 
 class LevelLog(ctypes.Structure):
     _fields_ = [("level", ctypes.c_int32), ("mode", ctypes.c_int32), ("frontier", ctypes.c_int64),
                 ("frontier_edges", ctypes.c_int64), ("unvisited", ctypes.c_int64), ("queue", ctypes.c_int64),
                 ("t_ns", ctypes.c_int64), ("scanned_vertices", ctypes.c_int64),
-                ("scanned_arcs", ctypes.c_int64)]
+                ("scanned_arcs", ctypes.c_int64), ("slots", ctypes.c_int64), ("t_stage1_ns", ctypes.c_int64)]
 
 
 class BvssView(ctypes.Structure):
@@ -262,13 +262,14 @@ class Graph:
 
     def bvss(self) -> dict:
         inf = self.info()
-        nv, ns = inf["num_vss"], inf["num_slice_sets"]
-        rows = np.empty(nv * 128, np.int32)
-        masks = np.empty(nv * 32, np.uint32)
+        nv, ns, tau = inf["num_vss"], inf["num_slice_sets"], inf["tau"]
+        theta = 32 // inf["sigma"]
+        rows = np.empty(nv * tau, np.int32)
+        masks = np.empty(nv * tau // theta, np.uint32)
         real = np.empty(ns + 1, np.int32)
         v2r = np.empty(nv, np.int32)
         _check(_lib.blest_get_bvss(self._h, _ptr(rows), _ptr(masks), _ptr(real), _ptr(v2r)), "blest_get_bvss")
-        return dict(rowIds=rows, masks=masks, realPtrs=real, v2r=v2r, Nv=nv, Ns=ns)
+        return dict(rowIds=rows, masks=masks, realPtrs=real, v2r=v2r, Nv=nv, Ns=ns, sigma=inf["sigma"], tau=tau)
 
     def perm(self) -> np.ndarray:
         p = np.empty(self.n, np.int32)

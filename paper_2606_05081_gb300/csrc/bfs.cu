@@ -1,19 +1,23 @@
 // Single-source BFS over BVSS: one persistent cooperative kernel runs every
 // level (§5.3 kernel fusion) and picks, per level, one of
 //   push eager  (Algorithm 2): visited check, atomic OR on the next frontier,
-//                the first setter of a slice-set byte enqueues its VSSs;
+//                the first setter of a slice-set field enqueues its VSSs;
 //   push lazy   (Algorithm 3 stage 1): fire-and-forget OR into V_next, then
 //                stage 2 sweeps V_curr xor V_next, sets levels and enqueues;
 //   bottom-up   (Algorithm 4 stage 1): each unvisited vertex scans its
 //                in-neighbours for a frontier vertex, then stage 2;
 // the per-VSS hit test (Eq. 2) runs either on tensor cores with the
-// m8n8k128 b1 AND.POPC layout of Fig. 3 or on CUDA cores (AND + byte test).
+// m8n8k128 b1 AND.POPC layout of Fig. 3 or on CUDA cores (AND + field test).
+//
+// The kernel is instantiated per BVSS layout: slice width SIGMA (8, 16, 32)
+// and LPV lane words per VSS (32: the warp-wide VSS of §3.1, tau = 32 *
+// theta; 8: a narrow VSS of tau = 32 slices, four per warp pass).
 //
 // State between levels is the same whatever mode ran (levels L, visited
 // bits V_curr = V_next, exact frontier bits F, VSS queue Q, slice-set queue
 // SQ), so modes mix freely.  F, Q and SQ rotate over three buffers and the
 // per-level counters over four slots; the buffer of level l-2 is cleared
-// sparsely (only the slice-set bytes it holds) while level l runs, so a
+// sparsely (only the slice-set fields it holds) while level l runs, so a
 // top-down eager level needs a single grid barrier and no O(n) clearing.
 #include <cstdio>
 #include <cstring>
@@ -27,7 +31,7 @@ constexpr int BFS_MAX_THREADS = 1024;
 
 struct BfsParams {
     int n, W;
-    const int4 *__restrict__ rowIds;
+    const int *__restrict__ rowIds;
     const unsigned *__restrict__ masks;
     const int *__restrict__ realPtrs;
     const int *__restrict__ v2r;
@@ -50,17 +54,38 @@ struct BfsParams {
     const int *schedule;
     int sched_len;
     const float *mlp;
-    int batch;              // VSSs in flight per warp in top-down levels (1, 2, 4)
+    int batch;              // VSS passes a warp keeps in flight in top-down levels (1, 2, 4)
     float avg_deg;
     unsigned long long budget_ns;
     const int *new_of_old;  // non-null: out[v] = L[new_of_old[v]]
     int *out;
 };
 
+// Compile-time facts of a BVSS layout.
+template <int SIGMA, int LPV>
+struct Lay {
+    static constexpr int THETA = 32 / SIGMA;           // slices per lane word
+    static constexpr int TAU = LPV * THETA;            // slices per VSS
+    static constexpr int G = 32 / LPV;                 // VSSs per warp pass
+    static constexpr int LOGS = SIGMA == 8 ? 3 : (SIGMA == 16 ? 4 : 5);
+    static constexpr unsigned FMASK = SIGMA == 32 ? 0xFFFFFFFFu : ((1u << SIGMA) - 1u);
+    static constexpr bool TC_OK = SIGMA == 8 && LPV == 32;   // the Fig. 3 fragment layout
+};
+
+// CUDA-core hit test: bit c set iff slice c of the lane word shares a bit
+// with the slice set's frontier field alpha (popc(mask_c & alpha) > 0).
+template <int SIGMA>
 __device__ __forceinline__ unsigned hits_cc(unsigned m, unsigned alpha) {
-    const unsigned x = m & (alpha * 0x01010101u);
-    return (unsigned)((x & 0xFFu) != 0) | ((unsigned)((x & 0xFF00u) != 0) << 1) |
-           ((unsigned)((x & 0xFF0000u) != 0) << 2) | ((unsigned)((x >> 24) != 0) << 3);
+    if constexpr (SIGMA == 8) {
+        const unsigned x = m & (alpha * 0x01010101u);
+        return (unsigned)((x & 0xFFu) != 0) | ((unsigned)((x & 0xFF00u) != 0) << 1) |
+               ((unsigned)((x & 0xFF0000u) != 0) << 2) | ((unsigned)((x >> 24) != 0) << 3);
+    } else if constexpr (SIGMA == 16) {
+        const unsigned x = m & (alpha * 0x00010001u);
+        return (unsigned)((x & 0xFFFFu) != 0) | ((unsigned)((x >> 16) != 0) << 1);
+    } else {
+        return (unsigned)((m & alpha) != 0);
+    }
 }
 
 // Fig. 3 layout: fragA = two packed sigma-bit masks in the low 16 bits;
@@ -82,51 +107,84 @@ __device__ __forceinline__ unsigned hits_tc(unsigned m, unsigned alpha, unsigned
            ((unsigned)(d3 != 0) << 3);
 }
 
+// the theta row ids of lane word `word` (one 4-, 8- or 16-byte load)
+template <int THETA>
+__device__ __forceinline__ void load_rows(const int *__restrict__ rowIds, size_t word, int (&r)[4]) {
+    if constexpr (THETA == 4) {
+        const int4 v = __ldg(reinterpret_cast<const int4 *>(rowIds) + word);
+        r[0] = v.x; r[1] = v.y; r[2] = v.z; r[3] = v.w;
+    } else if constexpr (THETA == 2) {
+        const int2 v = __ldg(reinterpret_cast<const int2 *>(rowIds) + word);
+        r[0] = v.x; r[1] = v.y; r[2] = 0; r[3] = 0;
+    } else {
+        r[0] = __ldg(rowIds + word); r[1] = 0; r[2] = 0; r[3] = 0;
+    }
+}
+
 __device__ __forceinline__ int pick(const int4 &r, int c) {
     return c == 0 ? r.x : (c == 1 ? r.y : (c == 2 ? r.z : r.w));
 }
 
-// Warp-aggregated enqueue of up to 4 slice sets per lane (bit c of `want`
-// set => slice set ss[c]): their VSS ranges go to Q, the set ids to SQ.
-__device__ __forceinline__ void enqueue_sets(const BfsParams &P, unsigned want, const int ss[4], int2 *Q, int *SQ,
-                                             int slot) {
-    const int lane = lane_id();
-    if (!__any_sync(FULL_MASK, want != 0)) return;
-    int a[4], len[4];
-    int tot = 0, nset = 0;
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        a[c] = 0;
-        len[c] = 0;
-        if (want >> c & 1u) {
-            a[c] = __ldg(&P.realPtrs[ss[c]]);
-            len[c] = __ldg(&P.realPtrs[ss[c] + 1]) - a[c];
-            tot += len[c];
-            ++nset;
-        }
-    }
-    const int incl = warp_incl_scan(tot);
-    const int sincl = warp_incl_scan(nset);
-    int qbase = 0, sbase = 0;
-    if (lane == 31) {
-        qbase = incl ? atomicAdd(&P.ctl->qlen[slot], incl) : 0;
-        sbase = atomicAdd(&P.ctl->sqlen[slot], sincl);
-    }
-    qbase = __shfl_sync(FULL_MASK, qbase, 31) + incl - tot;
-    sbase = __shfl_sync(FULL_MASK, sbase, 31) + sincl - nset;
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        if (want >> c & 1u) {
-            SQ[sbase++] = ss[c];
-            for (int k = 0; k < len[c]; ++k) Q[qbase + k] = make_int2(a[c] + k, ss[c]);
-            qbase += len[c];
-        }
-    }
+// the SIGMA frontier bits of slice set ss (its field of the bitvector)
+template <int SIGMA>
+__device__ __forceinline__ unsigned ld_field(const unsigned *F, int ss) {
+    if constexpr (SIGMA == 8) return (unsigned)reinterpret_cast<const unsigned char *>(F)[ss];
+    else if constexpr (SIGMA == 16) return (unsigned)reinterpret_cast<const unsigned short *>(F)[ss];
+    else return F[ss];
 }
 
-// Same, with the VSS ranges [a[c], a[c] + len[c]) already loaded.
-__device__ __forceinline__ void enqueue_ranges(const BfsParams &P, unsigned want, const int ss[4], const int a[4],
-                                               const int len[4], int2 *Q, int *SQ, int slot) {
+template <int SIGMA>
+__device__ __forceinline__ void clear_field(unsigned *F, int ss) {
+    if constexpr (SIGMA == 8) reinterpret_cast<unsigned char *>(F)[ss] = 0;
+    else if constexpr (SIGMA == 16) reinterpret_cast<unsigned short *>(F)[ss] = 0;
+    else F[ss] = 0u;
+}
+
+// Queue appends are staged per warp in shared memory and reserved in the
+// global queues once per STG_Q entries: every warp reserving its own few
+// entries with one atomic on the same two counters serialises tens of
+// thousands of same-address atomics per level in one L2 slice.
+constexpr int STG_Q = 256;   // staged VSS entries per warp
+constexpr int STG_S = 128;   // staged slice-set ids per warp (>= 32 lanes x 4 sets)
+constexpr int STG_BYTES = STG_Q * 8 + STG_S * 4;
+
+struct Stage {
+    int2 *q;     // this warp's staging area in shared memory
+    int *sq;
+    int qn, sqn; // staged counts (warp-uniform)
+};
+
+__device__ __forceinline__ void stage_flush(const BfsParams &P, Stage &st, int2 *Q, int *SQ, int slot) {
+    const int lane = lane_id();
+    __syncwarp();
+    if (st.qn) {
+        int base = 0;
+        if (lane == 0) base = atomicAdd(&P.ctl->qlen[slot], st.qn);
+        base = __shfl_sync(FULL_MASK, base, 0);
+        for (int k = lane; k < st.qn; k += 32) Q[base + k] = st.q[k];
+    }
+    if (st.sqn) {
+        int base = 0;
+        if (lane == 0) base = atomicAdd(&P.ctl->sqlen[slot], st.sqn);
+        base = __shfl_sync(FULL_MASK, base, 0);
+        for (int k = lane; k < st.sqn; k += 32) SQ[base + k] = st.sq[k];
+    }
+    __syncwarp();
+    st.qn = 0;
+    st.sqn = 0;
+}
+
+// Warp-aggregated enqueue of up to 4 slice sets per lane (bit c of `want`
+// set => slice set ss[c], whose VSSs are [a[c], a[c] + len[c])): the VSS
+// ranges go to Q, the set ids to SQ, both through the warp's staging area.
+// Short ranges are written by their own lane; a long range (the slice set
+// of a hub vertex spans thousands of VSSs) by the whole warp, so no lane
+// issues a long serial run of stores; a batch larger than the staging area
+// reserves its own space in Q.
+constexpr int ENQ_LANE_MAX = 8;
+
+__device__ __forceinline__ void enqueue_ranges(const BfsParams &P, Stage &st, unsigned want, const int ss[4],
+                                               const int a[4], const int len[4], int2 *Q, int *SQ, int slot) {
     const int lane = lane_id();
     if (!__any_sync(FULL_MASK, want != 0)) return;
     int tot = 0, nset = 0;
@@ -135,21 +193,71 @@ __device__ __forceinline__ void enqueue_ranges(const BfsParams &P, unsigned want
         if (want >> c & 1u) { tot += len[c]; ++nset; }
     const int incl = warp_incl_scan(tot);
     const int sincl = warp_incl_scan(nset);
-    int qbase = 0, sbase = 0;
-    if (lane == 31) {
-        qbase = incl ? atomicAdd(&P.ctl->qlen[slot], incl) : 0;
-        sbase = atomicAdd(&P.ctl->sqlen[slot], sincl);
+    const int T = __shfl_sync(FULL_MASK, incl, 31);
+    const int S = __shfl_sync(FULL_MASK, sincl, 31);
+    if ((T <= STG_Q && st.qn + T > STG_Q) || st.sqn + S > STG_S) stage_flush(P, st, Q, SQ, slot);
+    int2 *dst;
+    int qbase;
+    if (T > STG_Q) {
+        int g = 0;
+        if (lane == 31) g = atomicAdd(&P.ctl->qlen[slot], T);
+        dst = Q + __shfl_sync(FULL_MASK, g, 31);
+        qbase = incl - tot;
+    } else {
+        dst = st.q;
+        qbase = st.qn + incl - tot;
+        st.qn += T;
     }
-    qbase = __shfl_sync(FULL_MASK, qbase, 31) + incl - tot;
-    sbase = __shfl_sync(FULL_MASK, sbase, 31) + sincl - nset;
+    int sbase = st.sqn + sincl - nset;
+    st.sqn += S;
+    int pos[4];
+    unsigned big = 0;
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
+        pos[c] = qbase;
         if (want >> c & 1u) {
-            SQ[sbase++] = ss[c];
-            for (int k = 0; k < len[c]; ++k) Q[qbase + k] = make_int2(a[c] + k, ss[c]);
+            st.sq[sbase++] = ss[c];
+            if (len[c] <= ENQ_LANE_MAX) {
+                for (int k = 0; k < len[c]; ++k) dst[qbase + k] = make_int2(a[c] + k, ss[c]);
+            } else {
+                big |= 1u << c;
+            }
             qbase += len[c];
         }
     }
+    unsigned lanes = __ballot_sync(FULL_MASK, big != 0);
+    while (lanes) {
+        const int j = __ffs(lanes) - 1;
+        lanes &= lanes - 1u;
+        const unsigned bj = __shfl_sync(FULL_MASK, big, j);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int aj = __shfl_sync(FULL_MASK, a[c], j);
+            const int lj = __shfl_sync(FULL_MASK, len[c], j);
+            const int pj = __shfl_sync(FULL_MASK, pos[c], j);
+            const int sj = __shfl_sync(FULL_MASK, ss[c], j);
+            if (bj >> c & 1u)   // warp-uniform
+                for (int k = lane; k < lj; k += 32) dst[pj + k] = make_int2(aj + k, sj);
+        }
+    }
+    __syncwarp();
+}
+
+// Same, loading the VSS ranges of the slice sets first.
+__device__ __forceinline__ void enqueue_sets(const BfsParams &P, Stage &st, unsigned want, const int ss[4], int2 *Q,
+                                             int *SQ, int slot) {
+    if (!__any_sync(FULL_MASK, want != 0)) return;
+    int a[4], len[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        a[c] = 0;
+        len[c] = 0;
+        if (want >> c & 1u) {
+            a[c] = __ldg(&P.realPtrs[ss[c]]);
+            len[c] = __ldg(&P.realPtrs[ss[c] + 1]) - a[c];
+        }
+    }
+    enqueue_ranges(P, st, want, ss, a, len, Q, SQ, slot);
 }
 
 __device__ __forceinline__ void flush_counts(const BfsParams &P, int slot, unsigned long long nv,
@@ -164,54 +272,61 @@ __device__ __forceinline__ void flush_counts(const BfsParams &P, int slot, unsig
 
 // ---------------------------------------------------------------- push
 // Eager (Algorithm 2) or lazy (Algorithm 3 stage 1) top-down level.  A warp
-// keeps B VSSs in flight: it loads the B queue entries, then their slices
-// and masks, then their frontier bytes, before using any of them, so the
-// dependent-load chain is paid once per B VSSs.
-template <bool EAGER, bool TC, int B>
-__device__ void push_level(const BfsParams &P, int ell, int bc, int bn, int slot, int qlen, unsigned bsel) {
+// pass covers G VSSs (one per lane group of LPV lanes); a warp keeps B passes
+// in flight: it loads the B*G queue entries, then their slices and masks,
+// then their frontier fields, before using any of them, so the
+// dependent-load chain is paid once per B*G VSSs.
+template <bool EAGER, bool TC, int B, int SIGMA, int LPV>
+__device__ void push_level(const BfsParams &P, Stage &st, int ell, int bc, int bn, int slot, int qlen,
+                           unsigned bsel) {
+    using LY = Lay<SIGMA, LPV>;
+    constexpr int THETA = LY::THETA, G = LY::G;
     const int lane = lane_id();
+    const int grp = lane / LPV, sl = lane % LPV;
     const int gwarp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
     const unsigned *Fc = P.F[bc];
     unsigned *Fn = P.F[bn];
     const int2 *Qc = P.Q[bc];
     unsigned long long nv = 0, fe = 0;
-    for (int w0 = gwarp * B; w0 < qlen; w0 += nwarps * B) {
+    for (int w0 = gwarp * B * G; w0 < qlen; w0 += nwarps * B * G) {
         int vss[B], ss[B];
-        int4 r[B];
+        int r[B][4];
         unsigned m[B], alpha[B];
-        // lane b < B fetches queue entry w0 + b (VSS and slice set); shuffles spread them
-        const int2 mine = (lane < B && w0 + lane < qlen) ? Qc[w0 + lane] : make_int2(-1, 0);
+        // lane j < B*G fetches queue entry w0 + j (VSS and slice set); shuffles spread them
+        const int2 mine = (lane < B * G && w0 + lane < qlen) ? Qc[w0 + lane] : make_int2(-1, 0);
 #pragma unroll
         for (int b = 0; b < B; ++b) {
-            vss[b] = __shfl_sync(FULL_MASK, mine.x, b);
-            ss[b] = __shfl_sync(FULL_MASK, mine.y, b);
+            vss[b] = __shfl_sync(FULL_MASK, mine.x, b * G + grp);
+            ss[b] = __shfl_sync(FULL_MASK, mine.y, b * G + grp);
         }
-        // slices, masks and frontier bytes of the B VSSs are independent loads
+        // slices, masks and frontier fields of the VSSs are independent loads
 #pragma unroll
         for (int b = 0; b < B; ++b) {
             if (vss[b] >= 0) {
-                r[b] = __ldg(&P.rowIds[(size_t)vss[b] * 32 + lane]);
-                m[b] = __ldg(&P.masks[(size_t)vss[b] * 32 + lane]);
-                alpha[b] = ld_byte(Fc, ss[b]);
+                load_rows<THETA>(P.rowIds, (size_t)vss[b] * LPV + sl, r[b]);
+                m[b] = __ldg(&P.masks[(size_t)vss[b] * LPV + sl]);
+                alpha[b] = ld_field<SIGMA>(Fc, ss[b]);
             } else {
-                r[b] = make_int4(0, 0, 0, 0);
+                r[b][0] = r[b][1] = r[b][2] = r[b][3] = 0;
                 m[b] = 0u;
                 alpha[b] = 0u;
             }
         }
 #pragma unroll
         for (int b = 0; b < B; ++b) {
-            if (vss[b] < 0) continue;   // warp-uniform
-            const unsigned hits = TC ? hits_tc(m[b], alpha[b], bsel) : hits_cc(m[b], alpha[b]);
+            if (w0 + b * G >= qlen) continue;   // warp-uniform: no group has an entry
+            unsigned hits;
+            if constexpr (TC) hits = hits_tc(m[b], alpha[b], bsel);
+            else hits = hits_cc<SIGMA>(m[b], alpha[b]);
             if (EAGER) {
                 // phase 1: visited words of the hit rows (independent loads)
                 int u[4];
                 unsigned vw[4];
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
-                    u[c] = pick(r[b], c);
-                    vw[c] = (hits >> c & 1u) ? P.Vc[u[c] >> 5] : 0xFFFFFFFFu;
+                    u[c] = r[b][c];
+                    vw[c] = (c < THETA && (hits >> c & 1u)) ? P.Vc[u[c] >> 5] : 0xFFFFFFFFu;
                 }
                 // phase 2: claim the unvisited ones.  Lanes whose rows share a frontier
                 // word OR their bits together and one of them issues the atomic (rows
@@ -220,7 +335,7 @@ __device__ void push_level(const BfsParams &P, int ell, int bc, int bn, int slot
                 int dg[4], a[4], len[4], sso[4];
                 unsigned cand = 0;
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
+                for (int c = 0; c < THETA; ++c) {
                     const bool cd = !(vw[c] >> (u[c] & 31) & 1u);
                     const int key = cd ? (u[c] >> 5) : -1;
                     const unsigned peers = __match_any_sync(FULL_MASK, key);
@@ -233,7 +348,7 @@ __device__ void push_level(const BfsParams &P, int ell, int bc, int bn, int slot
                     dg[c] = 0;
                     a[c] = 0;
                     len[c] = 0;
-                    sso[c] = u[c] >> 3;
+                    sso[c] = u[c] >> LY::LOGS;
                     if (cd) {
                         cand |= 1u << c;
                         dg[c] = __ldg(&P.deg[u[c]]);
@@ -241,12 +356,21 @@ __device__ void push_level(const BfsParams &P, int ell, int bc, int bn, int slot
                         len[c] = __ldg(&P.realPtrs[sso[c] + 1]);
                     }
                 }
+#pragma unroll
+                for (int c = THETA; c < 4; ++c) { a[c] = 0; len[c] = 0; sso[c] = 0; }
                 // phase 3: winners set their level; visited bits are OR-ed once per word;
-                // the first claim of a slice-set byte enqueues its VSSs (once per set)
+                // the first claim of a slice-set field enqueues its VSSs (once per set)
                 unsigned want = 0;
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    const bool win = (cand >> c & 1u) && !(old[c] >> (u[c] & 31) & 1u);
+                for (int c = 0; c < THETA; ++c) {
+                    bool win = (cand >> c & 1u) && !(old[c] >> (u[c] & 31) & 1u);
+                    if constexpr (G > 1) {
+                        // VSSs of different slice sets in one pass can hold the same row at the
+                        // same slot position; both saw the bit clear in one aggregated atomic,
+                        // so the lowest such lane alone wins
+                        const unsigned dup = __match_any_sync(FULL_MASK, win ? u[c] : -1);
+                        if (win && lane != __ffs(dup) - 1) win = false;
+                    }
                     const int key = win ? (u[c] >> 5) : -1;
                     const unsigned peers = __match_any_sync(FULL_MASK, key);
                     const unsigned bits = __reduce_or_sync(peers, win ? (1u << (u[c] & 31)) : 0u);
@@ -260,17 +384,18 @@ __device__ void push_level(const BfsParams &P, int ell, int bc, int bn, int slot
                         P.L[u[c]] = ell;
                         nv += 1;
                         fe += (unsigned long long)dg[c];
-                        if (lane == __ffs(speers) - 1 && ((old[c] >> (u[c] & 24)) & 0xFFu) == 0) want |= 1u << c;
+                        const int fo = u[c] & (31 & ~(SIGMA - 1));   // the set's field in the word
+                        if (lane == __ffs(speers) - 1 && ((old[c] >> fo) & LY::FMASK) == 0) want |= 1u << c;
                     }
                     len[c] -= a[c];
                 }
-                enqueue_ranges(P, want, sso, a, len, P.Q[bn], P.SQ[bn], slot);
+                enqueue_ranges(P, st, want, sso, a, len, P.Q[bn], P.SQ[bn], slot);
             } else {
                 // lazy marking: one fire-and-forget OR per distinct V_next word
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
+                for (int c = 0; c < THETA; ++c) {
                     const bool hit = hits >> c & 1u;
-                    const int u = pick(r[b], c);
+                    const int u = r[b][c];
                     const int key = hit ? (u >> 5) : -1;
                     const unsigned peers = __match_any_sync(FULL_MASK, key);
                     const unsigned bits = __reduce_or_sync(peers, hit ? (1u << (u & 31)) : 0u);
@@ -279,7 +404,10 @@ __device__ void push_level(const BfsParams &P, int ell, int bc, int bn, int slot
             }
         }
     }
-    if (EAGER) flush_counts(P, slot, nv, fe);
+    if (EAGER) {
+        stage_flush(P, st, P.Q[bn], P.SQ[bn], slot);
+        flush_counts(P, slot, nv, fe);
+    }
 }
 
 // ------------------------------------------------------------ bottom-up
@@ -406,8 +534,12 @@ __device__ void bottom_up_level(const BfsParams &P, int bc, int slot, unsigned *
 // --------------------------------------------------- stage 2 (finalize)
 // Algorithm 3 stage 2.  Lane = word for the V_curr / V_next sweep and the
 // F writes; then, word by word over the words that changed, lane = vertex
-// for the level stores and degree loads, so both are coalesced.
-__device__ void finalize_level(const BfsParams &P, int ell, int bn, int slot) {
+// for the level stores and degree loads, so both are coalesced.  A word
+// holds theta = 32/SIGMA slice-set fields; a changed field enqueues its set.
+template <int SIGMA>
+__device__ void finalize_level(const BfsParams &P, Stage &st, int ell, int bn, int slot) {
+    constexpr int THETA = 32 / SIGMA;
+    constexpr unsigned FMASK = SIGMA == 32 ? 0xFFFFFFFFu : ((1u << SIGMA) - 1u);
     const int lane = lane_id();
     const int gwarp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
@@ -456,30 +588,32 @@ __device__ void finalize_level(const BfsParams &P, int ell, int bn, int slot) {
             }
         }
         unsigned want = 0;
-        int sso[4];
+        int sso[4] = {0, 0, 0, 0};
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            sso[c] = t * 4 + c;
-            if ((diff >> (8 * c)) & 0xFFu) want |= 1u << c;
+        for (int c = 0; c < THETA; ++c) {
+            sso[c] = t * THETA + c;
+            if ((diff >> (SIGMA * c)) & FMASK) want |= 1u << c;
         }
-        enqueue_sets(P, want, sso, P.Q[bn], P.SQ[bn], slot);
+        enqueue_sets(P, st, want, sso, P.Q[bn], P.SQ[bn], slot);
       }
     }
+    stage_flush(P, st, P.Q[bn], P.SQ[bn], slot);
     flush_counts(P, slot, nv, fe);
 }
 
 // -------------------------------------------------------- mode decision
 // Called by a full warp; all lanes return the same mode.  Every block
 // evaluates it on the same inputs, so every block picks the same mode.
+template <bool TC_OK>
 __device__ __forceinline__ int decide_mode(const BfsParams &P, int ell, long long frontier, long long fedges,
-                                           long long unvisited, int qlen) {
+                                           long long unvisited, long long slots, int qlen) {
     int mode;
     if (P.policy == BLEST_POLICY_FIXED) {
         mode = P.fixed_mode;
     } else if (P.policy == BLEST_POLICY_SCHEDULE && P.sched_len > 0) {
         mode = P.schedule[(ell - 1) % P.sched_len];
     } else if (P.policy == BLEST_POLICY_LEARNED && P.mlp) {
-        mode = mlp_choose_warp(P.mlp, frontier, fedges, unvisited, qlen, ell, P.avg_deg);
+        mode = mlp_choose_warp(P.mlp, frontier, fedges, unvisited, slots, ell, P.avg_deg);
     } else {
         // §5.2/§7.1: lazy updates when U_div exceeds the threshold; Eq. 5
         // switches to bottom-up when #unvisited < eta * |Q_curr|.
@@ -488,20 +622,24 @@ __device__ __forceinline__ int decide_mode(const BfsParams &P, int ell, long lon
         if (P.switching && (double)unvisited < (double)P.eta * (double)qlen) mode = BLEST_MODE_BOTTOM_UP;
     }
     if (mode < 0 || mode >= BLEST_NUM_MODES) mode = BLEST_MODE_PUSH_EAGER_CC;
+    // layouts without the Fig. 3 fragment run the CUDA-core twin of a tensor-core mode
+    if (!TC_OK && mode == BLEST_MODE_PUSH_EAGER_TC) mode = BLEST_MODE_PUSH_EAGER_CC;
+    if (!TC_OK && mode == BLEST_MODE_PUSH_LAZY_TC) mode = BLEST_MODE_PUSH_LAZY_CC;
     return mode;
 }
 
 // Buffers of level ell-2 are cleared sparsely and the counters of level
 // ell+1 zeroed.  Runs after the level's stage-1 work, on the grid's last
 // threads, so it stays off the path of the warps that own queue entries.
+template <int SIGMA>
 __device__ __forceinline__ void housekeeping(const BfsParams &P, int ell, int bo, int sql, int sz, int tid,
                                              int nthreads) {
     Ctl *ctl = P.ctl;
     const int rt = nthreads - 1 - tid;
     if (ell >= 2) {
-        unsigned char *Fo = reinterpret_cast<unsigned char *>(P.F[bo]);
+        unsigned *Fo = P.F[bo];
         const int *SQo = P.SQ[bo];
-        for (int k = rt; k < sql; k += nthreads) Fo[SQo[k]] = 0;
+        for (int k = rt; k < sql; k += nthreads) clear_field<SIGMA>(Fo, SQo[k]);
     }
     if (rt == 0) {
         ctl->qlen[sz] = 0;
@@ -513,25 +651,30 @@ __device__ __forceinline__ void housekeeping(const BfsParams &P, int ell, int bo
     }
 }
 
-template <bool EAGER>
-__device__ __forceinline__ void push_dispatch(const BfsParams &P, bool tc, int ell, int bc, int bn, int sn, int qlen,
-                                              unsigned bsel) {
-    // eager levels keep at most two VSSs in flight (their per-slice state
+template <bool EAGER, int SIGMA, int LPV>
+__device__ __forceinline__ void push_dispatch(const BfsParams &P, Stage &st, bool tc, int ell, int bc, int bn, int sn,
+                                              int qlen, unsigned bsel) {
+    // eager levels keep at most two passes in flight (their per-slice state
     // would not fit the 64-register budget of a 1024-thread CTA for four)
-    if (tc) {
-        if (!EAGER && P.batch >= 4) push_level<EAGER, true, EAGER ? 2 : 4>(P, ell, bc, bn, sn, qlen, bsel);
-        else if (P.batch >= 2) push_level<EAGER, true, 2>(P, ell, bc, bn, sn, qlen, bsel);
-        else push_level<EAGER, true, 1>(P, ell, bc, bn, sn, qlen, bsel);
-    } else {
-        if (!EAGER && P.batch >= 4) push_level<EAGER, false, EAGER ? 2 : 4>(P, ell, bc, bn, sn, qlen, bsel);
-        else if (P.batch >= 2) push_level<EAGER, false, 2>(P, ell, bc, bn, sn, qlen, bsel);
-        else push_level<EAGER, false, 1>(P, ell, bc, bn, sn, qlen, bsel);
+    if constexpr (Lay<SIGMA, LPV>::TC_OK) {
+        if (tc) {
+            if (!EAGER && P.batch >= 4) push_level<EAGER, true, EAGER ? 2 : 4, SIGMA, LPV>(P, st, ell, bc, bn, sn, qlen, bsel);
+            else if (P.batch >= 2) push_level<EAGER, true, 2, SIGMA, LPV>(P, st, ell, bc, bn, sn, qlen, bsel);
+            else push_level<EAGER, true, 1, SIGMA, LPV>(P, st, ell, bc, bn, sn, qlen, bsel);
+            return;
+        }
     }
+    if (!EAGER && P.batch >= 4) push_level<EAGER, false, EAGER ? 2 : 4, SIGMA, LPV>(P, st, ell, bc, bn, sn, qlen, bsel);
+    else if (P.batch >= 2) push_level<EAGER, false, 2, SIGMA, LPV>(P, st, ell, bc, bn, sn, qlen, bsel);
+    else push_level<EAGER, false, 1, SIGMA, LPV>(P, st, ell, bc, bn, sn, qlen, bsel);
 }
 
+template <int SIGMA, int LPV>
 __global__ void __launch_bounds__(BFS_MAX_THREADS, 1) k_bfs(BfsParams P) {
+    using LY = Lay<SIGMA, LPV>;
     __shared__ unsigned s_found[BFS_MAX_THREADS];
     __shared__ float s_mlp[MLP_NW];
+    extern __shared__ __align__(16) unsigned char s_stage[];   // STG_BYTES per warp
     if (P.policy == BLEST_POLICY_LEARNED && P.mlp) {
         for (int i = threadIdx.x; i < MLP_NW; i += blockDim.x) s_mlp[i] = P.mlp[i];
         __syncthreads();
@@ -543,6 +686,11 @@ __global__ void __launch_bounds__(BFS_MAX_THREADS, 1) k_bfs(BfsParams P) {
     const unsigned bsel = (lane % 9 == 0) ? 1u : ((lane % 9 == 4) ? 256u : 0u);
     Ctl *ctl = P.ctl;
     unsigned epoch = 0;
+    Stage st;
+    st.q = reinterpret_cast<int2 *>(s_stage + (size_t)(threadIdx.x >> 5) * STG_BYTES);
+    st.sq = reinterpret_cast<int *>(s_stage + (size_t)(threadIdx.x >> 5) * STG_BYTES + STG_Q * 8);
+    st.qn = 0;
+    st.sqn = 0;
     __shared__ int s_mode;
     __shared__ long long s_lvl[4];
 
@@ -559,7 +707,7 @@ __global__ void __launch_bounds__(BFS_MAX_THREADS, 1) k_bfs(BfsParams P) {
         P.F[2][w] = 0u;
     }
     {
-        const int ss = src >> 3;
+        const int ss = src >> LY::LOGS;
         const int a = __ldg(&P.realPtrs[ss]), e = __ldg(&P.realPtrs[ss + 1]);
         for (int k = tid; k < e - a; k += nthreads) P.Q[0][k] = make_int2(a + k, ss);
         if (tid == 0) {
@@ -591,7 +739,9 @@ __global__ void __launch_bounds__(BFS_MAX_THREADS, 1) k_bfs(BfsParams P) {
 #pragma unroll
             for (int i = 0; i < 4; ++i) c4[i] = __shfl_sync(FULL_MASK, c4[i], 0);
             const long long unv = (long long)P.n - (visited + c4[1]);
-            const int m = c4[0] > 0 ? decide_mode(P, ell, c4[1], c4[2], unv, (int)c4[0]) : 0;
+            const int m = c4[0] > 0 ? decide_mode<LY::TC_OK>(P, ell, c4[1], c4[2], unv, c4[0] * LY::TAU,
+                                                             (int)c4[0])
+                                    : 0;
             if (threadIdx.x == 0) {
                 s_lvl[0] = c4[0];
                 s_lvl[1] = c4[1];
@@ -609,12 +759,16 @@ __global__ void __launch_bounds__(BFS_MAX_THREADS, 1) k_bfs(BfsParams P) {
         __syncthreads();   // s_lvl / s_mode are rewritten at the next level start
         visited += frontier;
         const long long unvisited = (long long)P.n - visited;
-        if (blockIdx.x == 0 && threadIdx.x == 32) {
+        const bool logger = blockIdx.x == 0 && threadIdx.x == 32;
+        if (logger) {
             const long long t = (long long)global_ns();
             if (ell >= 2 && ell - 2 < P.log_cap) {
-                P.log[ell - 2].t_ns = t - P.log[ell - 2].t_ns;
-                P.log[ell - 2].scanned_vertices = (long long)*(volatile unsigned long long *)&ctl->scan_v[sc];
-                P.log[ell - 2].scanned_arcs = (long long)*(volatile unsigned long long *)&ctl->scan_a[sc];
+                blest_level_log &prev = P.log[ell - 2];
+                prev.t_ns = t - prev.t_ns;
+                if (prev.mode == BLEST_MODE_PUSH_EAGER_CC || prev.mode == BLEST_MODE_PUSH_EAGER_TC)
+                    prev.t_stage1_ns = prev.t_ns;
+                prev.scanned_vertices = (long long)*(volatile unsigned long long *)&ctl->scan_v[sc];
+                prev.scanned_arcs = (long long)*(volatile unsigned long long *)&ctl->scan_a[sc];
             }
             if (qlen > 0 && ell - 1 < P.log_cap) {
                 blest_level_log rec;
@@ -627,23 +781,28 @@ __global__ void __launch_bounds__(BFS_MAX_THREADS, 1) k_bfs(BfsParams P) {
                 rec.t_ns = t;
                 rec.scanned_vertices = 0;
                 rec.scanned_arcs = 0;
+                rec.slots = (long long)qlen * LY::TAU;
+                rec.t_stage1_ns = 0;
                 P.log[ell - 1] = rec;
             }
         }
         if (qlen == 0) break;
 
         if (mode == BLEST_MODE_PUSH_EAGER_CC || mode == BLEST_MODE_PUSH_EAGER_TC) {
-            push_dispatch<true>(P, mode == BLEST_MODE_PUSH_EAGER_TC, ell, bc, bn, sn, qlen, bsel);
-            housekeeping(P, ell, bo, sql_old, sz, tid, nthreads);
+            push_dispatch<true, SIGMA, LPV>(P, st, mode == BLEST_MODE_PUSH_EAGER_TC, ell, bc, bn, sn, qlen, bsel);
+            housekeeping<SIGMA>(P, ell, bo, sql_old, sz, tid, nthreads);
             if (!grid_barrier(ctl, epoch, P.budget_ns)) return;
         } else {
             if (mode == BLEST_MODE_BOTTOM_UP)
                 bottom_up_level(P, bc, sn, s_found);
             else
-                push_dispatch<false>(P, mode == BLEST_MODE_PUSH_LAZY_TC, ell, bc, bn, sn, qlen, bsel);
-            housekeeping(P, ell, bo, sql_old, sz, tid, nthreads);
+                push_dispatch<false, SIGMA, LPV>(P, st, mode == BLEST_MODE_PUSH_LAZY_TC, ell, bc, bn, sn, qlen,
+                                                 bsel);
+            housekeeping<SIGMA>(P, ell, bo, sql_old, sz, tid, nthreads);
             if (!grid_barrier(ctl, epoch, P.budget_ns)) return;
-            finalize_level(P, ell, bn, sn);
+            if (logger && ell - 1 < P.log_cap)
+                P.log[ell - 1].t_stage1_ns = (long long)global_ns() - P.log[ell - 1].t_ns;
+            finalize_level<SIGMA>(P, st, ell, bn, sn);
             if (!grid_barrier(ctl, epoch, P.budget_ns)) return;
         }
     }
@@ -653,17 +812,38 @@ __global__ void __launch_bounds__(BFS_MAX_THREADS, 1) k_bfs(BfsParams P) {
         for (int v = tid; v < P.n; v += nthreads) P.out[v] = P.L[__ldg(&P.new_of_old[v])];
 }
 
+// the kernel instance of a (sigma, tau) layout (nullptr for other pairs)
+const void *bfs_kernel_for(int sigma, int tau) {
+    if (sigma == 8 && tau == 128) return (const void *)k_bfs<8, 32>;
+    if (sigma == 8 && tau == 32) return (const void *)k_bfs<8, 8>;
+    if (sigma == 16 && tau == 64) return (const void *)k_bfs<16, 32>;
+    if (sigma == 32 && tau == 32) return (const void *)k_bfs<32, 32>;
+    return nullptr;
+}
+
 }  // namespace
 
-int bfs_grid_for(int block, int *num_sms) {
+// dynamic shared memory of a k_bfs launch: the warps' queue staging areas
+static size_t bfs_smem(int block) { return (size_t)(block / 32) * STG_BYTES; }
+
+static int bfs_grid_for_layout(int sigma, int tau, int block, int *num_sms) {
+    const void *kern = bfs_kernel_for(sigma, tau);
+    if (!kern) return 0;
     int dev = 0;
     cudaGetDevice(&dev);
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)bfs_smem(BFS_MAX_THREADS)) != cudaSuccess)
+        return 0;
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bfs, block, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, bfs_smem(block));
     if (num_sms) *num_sms = sms;
     return per_sm * sms;
+}
+
+int bfs_grid_for(const blest_graph *h, int block, int *num_sms) {
+    return bfs_grid_for_layout(h->sigma, h->tau, block, num_sms);
 }
 
 // nz[w] bit b set iff vertex 32w+b has an in-neighbour (a nonempty row of
@@ -702,7 +882,7 @@ blest_status bfs_prepare(blest_graph *h) {
     if (h->g.new_of_old)
         if ((bs = dev_alloc_t(h, &h->w.out_tmp, (size_t)n)) != BLEST_OK) return bs;
     int sms = 0;
-    h->grid = bfs_grid_for(h->block, &sms);
+    h->grid = bfs_grid_for(h, h->block, &sms);
     h->num_sms = sms;
     if (h->grid <= 0) return BLEST_ERR_CUDA;
     return BLEST_OK;
@@ -714,6 +894,8 @@ blest_status bfs_run(blest_graph *h, int32_t source, int32_t *dev_out) {
     memset(&P, 0, sizeof P);
     P.n = (int)h->n;
     P.W = (int)((h->n + 31) / 32);
+    const void *kern = bfs_kernel_for(h->sigma, h->tau);
+    if (!kern) return BLEST_ERR_INTERNAL;
     P.rowIds = h->g.rowIds;
     P.masks = h->g.masks;
     P.realPtrs = h->g.realPtrs;
@@ -756,7 +938,7 @@ blest_status bfs_run(blest_graph *h, int32_t source, int32_t *dev_out) {
     cudaError_t e = cudaMemsetAsync(h->w.ctl, 0, sizeof(Ctl), h->stream);
     if (e != cudaSuccess) return BLEST_ERR_CUDA;
     void *args[] = {&P};
-    e = cudaLaunchCooperativeKernel((const void *)k_bfs, dim3(h->grid), dim3(h->block), args, 0, h->stream);
+    e = cudaLaunchCooperativeKernel(kern, dim3(h->grid), dim3(h->block), args, bfs_smem(h->block), h->stream);
     if (e != cudaSuccess) {
         blest_internal_record_cuda_error(e, "cudaLaunchCooperativeKernel(k_bfs)", __FILE__, __LINE__);
         return BLEST_ERR_CUDA;
@@ -812,7 +994,7 @@ blest_status noalloc_setup(int dev, unsigned char **base, int *grid) {
             return BLEST_ERR_CUDA;
         }
         int sms = 0;
-        const int g = bfs_grid_for(512, &sms);
+        const int g = bfs_grid_for_layout(8, 128, 512, &sms);
         if (g <= 0) return BLEST_ERR_CUDA;
         g_noalloc_grid[dev] = g;
         g_noalloc_addr[dev] = (unsigned char *)p;
@@ -861,7 +1043,7 @@ extern "C" blest_status blest_bfs_noalloc(const blest_bvss_view *g, int32_t sour
     if (off > NOALLOC_BYTES) return BLEST_ERR_INTERNAL;
     P.n = (int)n;
     P.W = (int)W;
-    P.rowIds = (const int4 *)g->row_ids;
+    P.rowIds = g->row_ids;
     P.masks = g->masks;
     P.realPtrs = g->real_ptrs;
     P.v2r = g->virtual_to_real;
@@ -881,7 +1063,7 @@ extern "C" blest_status blest_bfs_noalloc(const blest_bvss_view *g, int32_t sour
     P.out = nullptr;
     if (cudaMemsetAsync(ctl, 0, sizeof(Ctl), s) != cudaSuccess) return BLEST_ERR_CUDA;
     void *args[] = {&P};
-    cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_bfs, dim3(grid), dim3(512), args, 0, s);
+    cudaError_t e = cudaLaunchCooperativeKernel(bfs_kernel_for(8, 128), dim3(grid), dim3(512), args, bfs_smem(512), s);
     if (e != cudaSuccess) {
         blest_internal_record_cuda_error(e, "cudaLaunchCooperativeKernel(k_bfs, no-alloc)", __FILE__, __LINE__);
         return BLEST_ERR_CUDA;

@@ -35,10 +35,11 @@ __global__ void k_validate(const long long *__restrict__ rp, const int *__restri
 }
 
 // ---- expand arcs j -> i (self loops dropped) into sort keys.
-// BVSS key: (new_j / 8) << B | new_i, payload new_j % 8.
+// BVSS key: (new_j / sigma) << B | new_i, payload new_j % sigma.
 // Transpose key (optional): new_i << B | new_j.
 __global__ void k_expand(const long long *__restrict__ rp, const int *__restrict__ col, int64_t n,
-                         const int *__restrict__ perm, int B, unsigned long long *bkeys, unsigned *bvals,
+                         const int *__restrict__ perm, int B, int log_sigma, unsigned long long *bkeys,
+                         unsigned *bvals,
                          unsigned long long *tkeys, int *deg, unsigned long long *loops) {
     const int lane = lane_id();
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -56,8 +57,8 @@ __global__ void k_expand(const long long *__restrict__ rp, const int *__restrict
                 continue;
             }
             const unsigned long long in = perm ? (unsigned long long)perm[i] : (unsigned long long)i;
-            bkeys[p] = ((jn >> 3) << B) | in;
-            bvals[p] = (unsigned)(jn & 7ull);
+            bkeys[p] = ((jn >> log_sigma) << B) | in;
+            bvals[p] = (unsigned)(jn & ((1ull << log_sigma) - 1ull));
             if (tkeys) tkeys[p] = (in << B) | jn;
             ++kept;
         }
@@ -102,10 +103,10 @@ __global__ void k_set_ranges(const unsigned long long *__restrict__ skey, int64_
 }
 
 __global__ void k_nvss(const long long *__restrict__ start, const long long *__restrict__ end, int64_t Ns,
-                       long long *nv) {
+                       int tau, long long *nv) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < Ns; s += stride)
-        nv[s] = (end[s] - start[s] + 127) / 128;
+        nv[s] = (end[s] - start[s] + tau - 1) / tau;
 }
 
 __global__ void k_real_ptrs(const long long *__restrict__ rp64, int64_t Ns, int *realPtrs, int *v2r) {
@@ -117,64 +118,76 @@ __global__ void k_real_ptrs(const long long *__restrict__ rp64, int64_t Ns, int 
     }
 }
 
-// one thread per lane word: slots vss*128 + lane*4 + c, c < 4
+// One thread per lane word: word g of VSS g / lanes holds the theta slices
+// at slots (g / lanes) * tau + (g % lanes) * theta + c, c < theta.
 __global__ void k_place(const unsigned long long *__restrict__ skey, const unsigned *__restrict__ smask,
                         const long long *__restrict__ start, const long long *__restrict__ end,
                         const int *__restrict__ realPtrs, const int *__restrict__ v2r, int64_t Nv, int B,
-                        int4 *rowIds, unsigned *masks) {
+                        int sigma, int tau, int *rowIds, unsigned *masks) {
     const unsigned long long rmask = (B >= 64) ? ~0ull : ((1ull << B) - 1ull);
+    const int theta = 32 / sigma, lanes = tau / theta;
+    const unsigned fmask = sigma == 32 ? 0xFFFFFFFFu : ((1u << sigma) - 1u);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < Nv * 32; g += stride) {
-        const int64_t vss = g >> 5;
-        const int l = (int)(g & 31);
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < Nv * lanes; g += stride) {
+        const int64_t vss = g / lanes;
+        const int l = (int)(g % lanes);
         const int ss = v2r[vss];
         const long long st = start[ss], cnt = end[ss] - st;
-        const long long r0 = (long long)(vss - realPtrs[ss]) * 128 + l * 4;
-        int rows[4];
+        const long long r0 = (long long)(vss - realPtrs[ss]) * tau + (long long)l * theta;
         unsigned word = 0;
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
+        for (int c = 0; c < theta; ++c) {
             const long long r = r0 + c;
+            int row = 0;
             if (r < cnt) {
-                rows[c] = (int)(skey[st + r] & rmask);
-                word |= (smask[st + r] & 0xFFu) << (8 * c);
-            } else {
-                rows[c] = 0;
+                row = (int)(skey[st + r] & rmask);
+                word |= (smask[st + r] & fmask) << (sigma * c);
             }
+            rowIds[g * theta + c] = row;
         }
-        rowIds[g] = make_int4(rows[0], rows[1], rows[2], rows[3]);
         masks[g] = word;
     }
 }
 
-// U_div per VSS (§4.2): mean over non-empty columns of the population std of
-// the row ids whose masks are nonzero.  One warp per VSS.
-__global__ void k_udiv(const int4 *__restrict__ rowIds, const unsigned *__restrict__ masks, int64_t Nv,
-                       double *per_vss, unsigned long long *bits) {
+// U_div per VSS (§4.2): mean over non-empty columns (slot position c of the
+// lane words) of the population std of the row ids whose masks are nonzero.
+// A warp takes 32 / lanes VSSs at once, one lane group each.
+__global__ void k_udiv(const int *__restrict__ rowIds, const unsigned *__restrict__ masks, int64_t Nv, int sigma,
+                       int tau, double *per_vss, unsigned long long *bits) {
     const int lane = lane_id();
+    const int theta = 32 / sigma, lanes = tau / theta, G = 32 / lanes;
+    const int grp = lane / lanes, l = lane % lanes;
+    const unsigned fmask = sigma == 32 ? 0xFFFFFFFFu : ((1u << sigma) - 1u);
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     unsigned long long mybits = 0;
-    for (int64_t v = gw; v < Nv; v += nw) {
-        const int4 r = rowIds[v * 32 + lane];
-        const unsigned m = masks[v * 32 + lane];
+    for (int64_t v0 = gw * G; v0 < Nv; v0 += nw * G) {
+        const int64_t v = v0 + grp;
+        const bool valid = v < Nv;
+        const int64_t wi = v * lanes + l;
+        const unsigned m = valid ? masks[wi] : 0u;
         mybits += __popc(m);
-        const int rr[4] = {r.x, r.y, r.z, r.w};
         double tot = 0.0;
         int ncols = 0;
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const bool ok = ((m >> (8 * c)) & 0xFFu) != 0;
-            const double x = (double)rr[c];
-            const int cnt = warp_sum(ok ? 1 : 0);
-            if (cnt == 0) continue;
-            const double mean = warp_sum(ok ? x : 0.0) / (double)cnt;
+        for (int c = 0; c < theta; ++c) {
+            const bool ok = ((m >> (sigma * c)) & fmask) != 0;
+            const double x = ok ? (double)rowIds[wi * theta + c] : 0.0;
+            int cnt = ok ? 1 : 0;
+            double sx = x;
+            for (int o = lanes / 2; o > 0; o >>= 1) {
+                cnt += __shfl_xor_sync(FULL_MASK, cnt, o, lanes);
+                sx += __shfl_xor_sync(FULL_MASK, sx, o, lanes);
+            }
+            // every lane takes part in the shuffles; empty columns add nothing
+            const double mean = cnt ? sx / (double)cnt : 0.0;
             const double d = ok ? (x - mean) : 0.0;
-            const double var = warp_sum(d * d) / (double)cnt;
-            tot += sqrt(var);
-            ++ncols;
+            double sq = d * d;
+            for (int o = lanes / 2; o > 0; o >>= 1) sq += __shfl_xor_sync(FULL_MASK, sq, o, lanes);
+            if (cnt) {
+                tot += sqrt(sq / (double)cnt);
+                ++ncols;
+            }
         }
-        if (lane == 0) per_vss[v] = ncols ? tot / (double)ncols : 0.0;
+        if (valid && l == 0) per_vss[v] = ncols ? tot / (double)ncols : 0.0;
     }
     mybits = warp_sum(mybits);
     if (lane == 0 && mybits) atomicAdd(bits, mybits);
@@ -334,7 +347,9 @@ blest_status build_graph(blest_graph *h, const int64_t *row_ptr, const int32_t *
     }
 
     const int B = ceil_log2_i64(n) > 0 ? ceil_log2_i64(n) : 1;
-    const int64_t Ns = (n + 7) / 8;
+    const int sigma = h->sigma, tau = h->tau, theta = 32 / sigma, lanes = tau / theta;
+    const int log_sigma = sigma == 8 ? 3 : (sigma == 16 ? 4 : 5);
+    const int64_t Ns = (n + sigma - 1) / sigma;
     const int SB = ceil_log2_i64(Ns) > 0 ? ceil_log2_i64(Ns) : 1;
     const bool need_t = h->directed || perm != nullptr;
     const int64_t M = nnz_in;
@@ -349,7 +364,8 @@ blest_status build_graph(blest_graph *h, const int64_t *row_ptr, const int32_t *
     h->g.deg = deg;
     BUILD_TRY(cudaMemsetAsync(d_loops, 0, sizeof(unsigned long long), st));
     BUILD_TRY(cudaMemsetAsync(deg, 0, (size_t)n * sizeof(int), st));
-    k_expand<<<grid_for(n * 32, TB, 1 << 16), TB, 0, st>>>(rp_in, col_in, n, perm, B, bk, bv, tk, deg, d_loops);
+    k_expand<<<grid_for(n * 32, TB, 1 << 16), TB, 0, st>>>(rp_in, col_in, n, perm, B, log_sigma, bk, bv, tk, deg,
+                                                            d_loops);
     BUILD_TRY(cudaGetLastError());
     unsigned long long loops = 0;
     BUILD_TRY(cudaMemcpyAsync(&loops, d_loops, sizeof(loops), cudaMemcpyDeviceToHost, st));
@@ -392,22 +408,23 @@ blest_status build_graph(blest_graph *h, const int64_t *row_ptr, const int32_t *
     BUILD_TRY(cudaMemsetAsync(start, 0, ((size_t)Ns + 1) * sizeof(long long), st));
     BUILD_TRY(cudaMemsetAsync(end, 0, ((size_t)Ns + 1) * sizeof(long long), st));
     k_set_ranges<<<grid_for(S, TB, 1 << 16), TB, 0, st>>>(skey, S, B, start, end);
-    k_nvss<<<grid_for(Ns, TB, 1 << 16), TB, 0, st>>>(start, end, Ns, nv);
+    k_nvss<<<grid_for(Ns, TB, 1 << 16), TB, 0, st>>>(start, end, Ns, tau, nv);
     BUILD_TRY(scan_exclusive_i64(nv, nv, Ns, stmp, st));
     long long Nv = 0;
     BUILD_TRY(cudaMemcpyAsync(&Nv, nv + Ns, sizeof(long long), cudaMemcpyDeviceToHost, st));
     BUILD_TRY(cudaStreamSynchronize(st));
-    if (Nv >= ((long long)1 << 31) / 32) return BLEST_ERR_UNSUPPORTED;
+    if (Nv * tau >= ((long long)1 << 31)) return BLEST_ERR_UNSUPPORTED;
     h->Ns = Ns;
     h->Nv = Nv;
     if ((bs = dev_alloc_t(h, &h->g.realPtrs, (size_t)Ns + 1)) != BLEST_OK) return bs;
     if ((bs = dev_alloc_t(h, &h->g.v2r, (size_t)(Nv > 0 ? Nv : 1))) != BLEST_OK) return bs;
-    if ((bs = dev_alloc_t(h, &h->g.rowIds, (size_t)(Nv > 0 ? Nv : 1) * 32)) != BLEST_OK) return bs;
-    if ((bs = dev_alloc_t(h, &h->g.masks, (size_t)(Nv > 0 ? Nv : 1) * 32)) != BLEST_OK) return bs;
+    if ((bs = dev_alloc_t(h, &h->g.rowIds, (size_t)(Nv > 0 ? Nv : 1) * tau)) != BLEST_OK) return bs;
+    if ((bs = dev_alloc_t(h, &h->g.masks, (size_t)(Nv > 0 ? Nv : 1) * lanes)) != BLEST_OK) return bs;
     k_real_ptrs<<<grid_for(Ns + 1, TB, 1 << 16), TB, 0, st>>>(nv, Ns, h->g.realPtrs, h->g.v2r);
     if (Nv > 0)
-        k_place<<<grid_for(Nv * 32, TB, 1 << 16), TB, 0, st>>>(skey, smask, start, end, h->g.realPtrs,
-                                                                  h->g.v2r, Nv, B, h->g.rowIds, h->g.masks);
+        k_place<<<grid_for(Nv * lanes, TB, 1 << 16), TB, 0, st>>>(skey, smask, start, end, h->g.realPtrs,
+                                                                     h->g.v2r, Nv, B, sigma, tau, h->g.rowIds,
+                                                                     h->g.masks);
     BUILD_TRY(cudaGetLastError());
 
     // ---- U_div and distinct arc count
@@ -421,7 +438,8 @@ blest_status build_graph(blest_graph *h, const int64_t *row_ptr, const int32_t *
         POOL_CHECK(pool);
         BUILD_TRY(cudaMemsetAsync(bits, 0, sizeof(unsigned long long), st));
         if (Nv > 0) {
-            k_udiv<<<grid_for(Nv * 32, TB, 1 << 16), TB, 0, st>>>(h->g.rowIds, h->g.masks, Nv, pv, bits);
+            k_udiv<<<grid_for(Nv * lanes, TB, 1 << 16), TB, 0, st>>>(h->g.rowIds, h->g.masks, Nv, sigma, tau, pv,
+                                                                        bits);
             k_dsum_partial<<<(unsigned)nparts, TB, 0, st>>>(pv, Nv, chunk, part);
             k_dsum_partial<<<1, TB, 0, st>>>(part, nparts, nparts, one);
         } else {

@@ -138,7 +138,10 @@ extern "C" blest_status blest_build(int64_t n, const int64_t *row_ptr, const int
     blest_default_opts(&o);
     if (opts) o = *opts;
     if (o.sigma == 0) o.sigma = 8;
-    if (o.sigma != 8) return BLEST_ERR_UNSUPPORTED;
+    if (o.sigma != 8 && o.sigma != 16 && o.sigma != 32) return BLEST_ERR_INVALID;
+    if (o.tau == 0) o.tau = 32 * (32 / o.sigma);
+    if (!bvss_layout_ok(o.sigma, o.tau)) return BLEST_ERR_INVALID;
+    if (o.engine_tc && !(o.sigma == 8 && o.tau == 128)) return BLEST_ERR_UNSUPPORTED;
     if (o.block_threads == 0) o.block_threads = 512;
     if (o.block_threads != 256 && o.block_threads != 512 && o.block_threads != 1024) return BLEST_ERR_INVALID;
     if (o.vss_batch == 0) o.vss_batch = 2;
@@ -146,11 +149,12 @@ extern "C" blest_status blest_build(int64_t n, const int64_t *row_ptr, const int
     if (o.timeout_ms <= 0) o.timeout_ms = 5000;
     if (o.reorder < 0 || o.reorder > BLEST_REORDER_AUTO) return BLEST_ERR_INVALID;
     if (o.jaccard_window <= 0) o.jaccard_window = 65536;
-    if (o.jaccard_window % 8) return BLEST_ERR_INVALID;
+    if (o.jaccard_window % o.sigma) return BLEST_ERR_INVALID;
 
     blest_graph *h = new blest_graph();
     h->n = n;
     h->sigma = o.sigma;
+    h->tau = o.tau;
     h->directed = o.directed ? 1 : 0;
     h->engine_tc = o.engine_tc ? 1 : 0;
     h->eta = o.eta > 0 ? o.eta : 10.f;
@@ -228,6 +232,7 @@ extern "C" blest_status blest_set_policy(blest_handle h, int32_t policy, int32_t
 
 extern "C" blest_status blest_set_engine(blest_handle h, int32_t tc) {
     if (!h || (tc != 0 && tc != 1)) return BLEST_ERR_INVALID;
+    if (tc && !(h->sigma == 8 && h->tau == 128)) return BLEST_ERR_UNSUPPORTED;
     h->engine_tc = tc;
     return BLEST_OK;
 }
@@ -237,7 +242,7 @@ extern "C" blest_status blest_set_launch(blest_handle h, int32_t block_threads, 
     if (block_threads != 256 && block_threads != 512 && block_threads != 1024) return BLEST_ERR_INVALID;
     if (vss_batch != 1 && vss_batch != 2 && vss_batch != 4) return BLEST_ERR_INVALID;
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return BLEST_ERR_CUDA;
-    const int g = bfs_grid_for(block_threads, nullptr);
+    const int g = bfs_grid_for(h, block_threads, nullptr);
     if (g <= 0) return BLEST_ERR_CUDA;
     h->block = block_threads;
     h->grid = g;
@@ -303,6 +308,7 @@ extern "C" blest_status blest_get_info(blest_handle h, blest_info *info) {
     info->switching = h->switching;
     info->reorder = h->reorder;
     info->sigma = h->sigma;
+    info->tau = h->tau;
     info->grid_blocks = h->grid;
     info->block_threads = h->block;
     info->build_ms = h->build_ms;
@@ -315,9 +321,10 @@ extern "C" blest_status blest_get_bvss(blest_handle h, int32_t *row_ids, uint32_
     if (!h || h->many) return BLEST_ERR_INVALID;
     cudaStreamSynchronize(h->stream);
     const size_t nv = (size_t)h->Nv;
-    if (row_ids && nv && cudaMemcpy(row_ids, h->g.rowIds, nv * 128 * 4, cudaMemcpyDefault) != cudaSuccess)
+    const size_t tau = (size_t)h->tau, words = tau / (size_t)(32 / h->sigma);
+    if (row_ids && nv && cudaMemcpy(row_ids, h->g.rowIds, nv * tau * 4, cudaMemcpyDefault) != cudaSuccess)
         return BLEST_ERR_CUDA;
-    if (masks && nv && cudaMemcpy(masks, h->g.masks, nv * 32 * 4, cudaMemcpyDefault) != cudaSuccess)
+    if (masks && nv && cudaMemcpy(masks, h->g.masks, nv * words * 4, cudaMemcpyDefault) != cudaSuccess)
         return BLEST_ERR_CUDA;
     if (real_ptrs && cudaMemcpy(real_ptrs, h->g.realPtrs, ((size_t)h->Ns + 1) * 4, cudaMemcpyDefault) != cudaSuccess)
         return BLEST_ERR_CUDA;

@@ -10,8 +10,11 @@
 #include "common.cuh"
 
 struct DevGraph {
-    // BVSS (§3.1), sigma = 8: rowIds int4[N_v*32], masks u32[N_v*32]
-    int4 *rowIds = nullptr;
+    // BVSS (§3.1): rowIds int32[N_v*tau] (slice k of VSS v at v*tau + k;
+    // lane word l owns slots l*theta .. l*theta + theta - 1, one vector load),
+    // masks u32[N_v*tau/theta] (slice c of a word in bits [c*sigma, (c+1)*sigma)),
+    // theta = 32/sigma
+    int *rowIds = nullptr;
     unsigned *masks = nullptr;
     int *realPtrs = nullptr;   // N_s + 1
     int *v2r = nullptr;        // N_v
@@ -47,6 +50,7 @@ struct blest_graph {
     int64_t n = 0, nnz = 0;
     int64_t Ns = 0, Nv = 0, num_slices = 0;
     int sigma = 8;
+    int tau = 128;                    // slices per VSS
     int directed = 0;
     int reorder = 0;
     double udiv = 0.0;
@@ -106,4 +110,9 @@ blest_status build_graph(blest_graph *h, const int64_t *row_ptr, const int32_t *
 // BFS (bfs.cu)
 blest_status bfs_prepare(blest_graph *h);
 blest_status bfs_run(blest_graph *h, int32_t source, int32_t *levels_dev_out);
-int bfs_grid_for(int block, int *num_sms);
+int bfs_grid_for(const blest_graph *h, int block, int *num_sms);
+
+// the (sigma, tau) pairs the kernels are built for: (8, 32), (8, 128), (16, 64), (32, 32)
+static inline bool bvss_layout_ok(int sigma, int tau) {
+    return (sigma == 8 && (tau == 32 || tau == 128)) || (sigma == 16 && tau == 64) || (sigma == 32 && tau == 32);
+}

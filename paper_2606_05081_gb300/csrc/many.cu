@@ -46,7 +46,7 @@ constexpr int MANY_BLOCK = 256;
 
 struct ManyParams {
     int G;
-    const int4 *__restrict__ rowIds;
+    const int *__restrict__ rowIds;   // sigma = 8, tau = 128: one int4 per lane word
     const unsigned *__restrict__ masks;
     const int *__restrict__ realPtrs;
     const int *__restrict__ v2r;
@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(MANY_BLOCK) k_many(ManyParams P) {
             for (int w = wid; w < qlen; w += nw) {
                 const int vss = Qb[cur][w];
                 const int ls = __ldg(&P.v2r[vss]) - (base >> 3);
-                const int4 r = __ldg(&P.rowIds[(size_t)vss * 32 + lane]);
+                const int4 r = __ldg(reinterpret_cast<const int4 *>(P.rowIds) + (size_t)vss * 32 + lane);
                 const unsigned m = __ldg(&P.masks[(size_t)vss * 32 + lane]);
                 const unsigned alpha = Fc[ls];
                 const unsigned hits = P.tc ? hits_tc_m(m, alpha, bsel) : hits_cc_m(m, alpha);
@@ -158,9 +158,33 @@ __global__ void __launch_bounds__(MANY_BLOCK) k_many(ManyParams P) {
                 int qb = 0;
                 if (lane == 31 && incl) qb = atomicAdd(&s_qlen[cur ^ 1], incl);
                 qb = __shfl_sync(FULL_MASK, qb, 31) + incl - tot;
+                // short ranges by their own lane, long ones (hub slice sets) by the whole warp
+                int pos[4];
+                unsigned big = 0;
 #pragma unroll
-                for (int c = 0; c < 4; ++c)
-                    for (int k = 0; k < want_len[c]; ++k) Qn[qb++] = want_a[c] + k;
+                for (int c = 0; c < 4; ++c) {
+                    pos[c] = qb;
+                    if (want_len[c] <= 8) {
+                        for (int k = 0; k < want_len[c]; ++k) Qn[qb + k] = want_a[c] + k;
+                    } else {
+                        big |= 1u << c;
+                    }
+                    qb += want_len[c];
+                }
+                unsigned bl = __ballot_sync(FULL_MASK, big != 0);
+                while (bl) {
+                    const int j = __ffs(bl) - 1;
+                    bl &= bl - 1u;
+                    const unsigned bj = __shfl_sync(FULL_MASK, big, j);
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const int aj = __shfl_sync(FULL_MASK, want_a[c], j);
+                        const int lj = __shfl_sync(FULL_MASK, want_len[c], j);
+                        const int pj = __shfl_sync(FULL_MASK, pos[c], j);
+                        if (bj >> c & 1u)
+                            for (int k = lane; k < lj; k += 32) Qn[pj + k] = aj + k;
+                    }
+                }
             }
             __syncthreads();
             // the current frontier becomes the next level's (cleared) target
@@ -247,7 +271,8 @@ extern "C" blest_status blest_build_many(int32_t g, const int64_t *vtx_off, cons
         o.reorder = BLEST_REORDER_NONE;  // the union keeps each graph's own numbering
         o.directed = 0;
         o.probe_switch = 0;
-        st = blest_build(n_u, (const int64_t *)d_rpu, d_colu, &o, &h);
+        if ((o.sigma != 0 && o.sigma != 8) || (o.tau != 0 && o.tau != 128)) st = BLEST_ERR_UNSUPPORTED;
+        else st = blest_build(n_u, (const int64_t *)d_rpu, d_colu, &o, &h);
     }
     cudaFree(d_rpu);
     cudaFree(d_colu);

@@ -148,7 +148,7 @@ __global__ void k_mlp_features(const blest_level_log *__restrict__ recs, int n, 
     if (s >= n) return;
     float x[MLP_IN];
     const blest_level_log r = recs[s];
-    mlp_raw_features(x, r.frontier, r.frontier_edges, r.unvisited, r.queue, r.level, avg_deg);
+    mlp_raw_features(x, r.frontier, r.frontier_edges, r.unvisited, r.slots, r.level, avg_deg);
 #pragma unroll
     for (int i = 0; i < MLP_IN; ++i) out[(size_t)s * MLP_IN + i] = x[i];
 }

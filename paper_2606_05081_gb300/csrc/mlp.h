@@ -8,7 +8,7 @@
 //   W1 [32][6]    b1 [32]                W2 [32][32]  b2 [32]
 //   W3 [5][32]    b3 [5]
 // Features, in order: log1p(frontier vertices), log1p(frontier out-arcs),
-// log1p(unvisited vertices), log1p(active BVSS slices = 128 * |Q|),
+// log1p(unvisited vertices), log1p(active BVSS slots = tau * |Q|),
 // log1p(level index), log1p(average degree).
 #pragma once
 #include <cuda_runtime.h>
@@ -27,12 +27,12 @@
 #define MLP_NW (MLP_OFF_B3 + MLP_OUT)
 
 __host__ __device__ inline void mlp_raw_features(float *x, long long frontier, long long fedges,
-                                                 long long unvisited, long long qlen, int level,
+                                                 long long unvisited, long long slots, int level,
                                                  float avg_deg) {
     x[0] = log1pf((float)frontier);
     x[1] = log1pf((float)fedges);
     x[2] = log1pf((float)(unvisited > 0 ? unvisited : 0));
-    x[3] = log1pf(128.f * (float)qlen);
+    x[3] = log1pf((float)slots);
     x[4] = log1pf((float)level);
     x[5] = log1pf(avg_deg);
 }
@@ -77,8 +77,8 @@ __device__ __forceinline__ int mlp_argmin_warp(float y) {
 
 // Called by all 32 lanes of one warp; every lane returns the chosen mode.
 __device__ __forceinline__ int mlp_choose_warp(const float *__restrict__ w, long long frontier, long long fedges,
-                                               long long unvisited, long long qlen, int level, float avg_deg) {
+                                               long long unvisited, long long slots, int level, float avg_deg) {
     float x[MLP_IN];
-    mlp_raw_features(x, frontier, fedges, unvisited, qlen, level, avg_deg);
+    mlp_raw_features(x, frontier, fedges, unvisited, slots, level, avg_deg);
     return mlp_argmin_warp(mlp_forward_warp(w, x));
 }

@@ -56,7 +56,8 @@ constexpr int MS_BLOCK = 512;
 
 struct MsParams {
     int n, rho, k;
-    const int4 *__restrict__ rowIds;
+    int lpv;                      // lane words per VSS: 32 (tau = 128) or 8 (tau = 32)
+    const int *__restrict__ rowIds;
     const unsigned *__restrict__ masks;
     const int *__restrict__ realPtrs;
     const int *__restrict__ v2r;
@@ -92,7 +93,19 @@ __device__ __forceinline__ void ms_enqueue(const MsParams &P, bool want, int ss,
     int base = 0;
     if (lane == 31 && incl) base = atomicAdd(&P.ctl->qlen[slot], incl);
     base = __shfl_sync(FULL_MASK, base, 31) + incl - len;
-    for (int i = 0; i < len; ++i) Q[base + i] = a + i;
+    // short ranges by their own lane, long ones (hub slice sets) by the whole warp
+    const bool big = len > 8;
+    if (!big)
+        for (int i = 0; i < len; ++i) Q[base + i] = a + i;
+    unsigned lanes = __ballot_sync(FULL_MASK, big);
+    while (lanes) {
+        const int j = __ffs(lanes) - 1;
+        lanes &= lanes - 1u;
+        const int aj = __shfl_sync(FULL_MASK, a, j);
+        const int lj = __shfl_sync(FULL_MASK, len, j);
+        const int bj = __shfl_sync(FULL_MASK, base, j);
+        for (int i = lane; i < lj; i += 32) Q[bj + i] = aj + i;
+    }
 }
 
 template <int KW>
@@ -108,8 +121,13 @@ __device__ void ms_stage1(const MsParams &P, int qlen, const int *Qc, int dl, in
     for (int it = gwarp; it < qlen; it += nwarps) {
         const int vss = Qc[it];
         const int ss = __ldg(&P.v2r[vss]);
-        const int4 r = __ldg(&P.rowIds[(size_t)vss * 32 + lane]);
-        const unsigned m = __ldg(&P.masks[(size_t)vss * 32 + lane]);
+        const bool own = lane < P.lpv;
+        const int4 r = own ? __ldg(reinterpret_cast<const int4 *>(P.rowIds) + (size_t)vss * P.lpv + lane)
+                           : make_int4(0, 0, 0, 0);
+        const unsigned m = own ? __ldg(&P.masks[(size_t)vss * P.lpv + lane]) : 0u;
+        // slots past the last lane word with a slice are padding: the loop stops there
+        const unsigned words = __ballot_sync(FULL_MASK, m != 0);
+        const int nslots = words ? 4 * (32 - __clz(words)) : 0;
         __syncwarp();
         rows[lane * 4 + 0] = r.x;
         rows[lane * 4 + 1] = r.y;
@@ -125,7 +143,7 @@ __device__ void ms_stage1(const MsParams &P, int qlen, const int *Qc, int dl, in
         for (int j = 0; j < 8; ++j) f[j] = aw ? P.F[(size_t)get_vi(ss * 8 + j, P.rho) * KW + w] : 0u;
         __syncwarp();
 #pragma unroll 2
-        for (int t = 0; t < 128 / G; ++t) {
+        for (int t = 0; t < (nslots + G - 1) / G; ++t) {
             const int kk = t * G + g;
             const unsigned m8 = m8s[kk];
             unsigned hit = 0;
@@ -353,6 +371,7 @@ static blest_status ms_launch(blest_graph *h, int k, int *levels_dev, long long 
     P.n = (int)h->n;
     P.rho = (int)h->Ns;
     P.k = k;
+    P.lpv = h->tau / 4;
     P.rowIds = h->g.rowIds;
     P.masks = h->g.masks;
     P.realPtrs = h->g.realPtrs;
@@ -399,6 +418,7 @@ static int kappa_for(int k) { return k <= 64 ? 64 : (k <= 256 ? 256 : 1024); }
 
 extern "C" blest_status blest_msbfs(blest_handle h, const int32_t *sources, int32_t k, int32_t *levels) {
     if (!h || h->many || !sources || !levels || k < 1 || k > 1024) return BLEST_ERR_INVALID;
+    if (h->sigma != 8) return BLEST_ERR_UNSUPPORTED;   // getVI groups the 8 vertices of a slice set
     std::vector<int32_t> src((size_t)k);
     if (cudaMemcpy(src.data(), sources, (size_t)k * 4, cudaMemcpyDefault) != cudaSuccess) return BLEST_ERR_CUDA;
     for (int32_t s : src)
@@ -448,7 +468,7 @@ static blest_status closeness_batches(blest_graph *h, int64_t first, int64_t cou
 static blest_status closeness_common(blest_graph *h, int64_t first, int64_t count, int64_t *far, double *cc,
                                      int64_t *reach) {
     if (!h || h->many) return BLEST_ERR_INVALID;
-    if (h->directed) return BLEST_ERR_UNSUPPORTED;
+    if (h->directed || h->sigma != 8) return BLEST_ERR_UNSUPPORTED;
     if (first < 0 || count < 0 || first + count > h->n) return BLEST_ERR_INVALID;
     blest_status st = ms_prepare(h, 1024);
     if (st != BLEST_OK) return st;

@@ -235,6 +235,7 @@ struct JacParams {
     const int *by_degree_id;
     int64_t n;
     int W;
+    int sigma;            // columns per slice set
     int nwin;
     int *inter;           // per block: W
     int *qlist;           // per block: W
@@ -254,7 +255,7 @@ __device__ __forceinline__ long long lower_bound_row(const int *col, long long a
 
 __global__ void __launch_bounds__(1024, 1) k_jaccard(JacParams P) {
     extern __shared__ unsigned s_assigned[];          // W bits
-    __shared__ int s_j, s_qcount, s_rsize, s_ptr, s_chosen[8];
+    __shared__ int s_j, s_qcount, s_rsize, s_ptr, s_chosen[32];
     __shared__ unsigned long long s_bnum[32], s_bden[32];
     __shared__ int s_bj[32];
     const int tid = threadIdx.x, nthr = blockDim.x;
@@ -271,10 +272,10 @@ __global__ void __launch_bounds__(1024, 1) k_jaccard(JacParams P) {
         for (int i = tid; i < W; i += nthr) inter[i] = 0;
         if (tid == 0) { s_qcount = 0; s_ptr = 0; }
         __syncthreads();
-        const int nss = (wn + 7) / 8;
+        const int nss = (wn + P.sigma - 1) / P.sigma;
         for (int s = 0; s < nss; ++s) {
-            const int64_t ss = ws + (int64_t)s * 8;
-            const int64_t se = (ss + 8 < we) ? ss + 8 : we;
+            const int64_t ss = ws + (int64_t)s * P.sigma;
+            const int64_t se = (ss + P.sigma < we) ? ss + P.sigma : we;
             int nch = 0;
             for (int64_t slot = ss; slot < se; ++slot) {
                 // ---- choose the column for this slot
@@ -534,6 +535,7 @@ static blest_status jaccard_order(blest_graph *h, Tmp &T, const long long *rp, c
     P.by_degree_id = (const int *)ids;
     P.n = n;
     P.W = W;
+    P.sigma = h->sigma;
     P.nwin = nwin;
     P.inter = inter;
     P.qlist = qlist;

@@ -39,26 +39,30 @@ def _graphs():
 
 
 GRAPHS = _graphs()
+# (sigma, tau): the warp-wide VSS of each slice width, and the narrow sigma = 8 VSS
+LAYOUTS = [(8, 128), (8, 32), (16, 64), (32, 32)]
 
 
-@pytest.fixture(scope="module", params=sorted(GRAPHS))
+@pytest.fixture(scope="module", params=[(g, s, t) for g in sorted(GRAPHS) for s, t in LAYOUTS],
+                ids=lambda p: f"{p[0]}-s{p[1]}t{p[2]}")
 def case(request, blest):
-    g = GRAPHS[request.param]()
-    h = blest.build_graph(g)
-    yield request.param, g, h
+    name, sigma, tau = request.param
+    g = GRAPHS[name]()
+    h = blest.build_graph(g, sigma=sigma, tau=tau)
+    yield name, g, h
     h.close()
 
 
 def test_bvss_matches_oracle(case):
     name, g, h = case
-    ref = oracle.bvss(g, 8)
+    info = h.info()
+    ref = oracle.bvss(g, info["sigma"], info["tau"])
     got = h.bvss()
     assert got["Nv"] == ref["Nv"] and got["Ns"] == ref["Ns"]
     assert np.array_equal(got["realPtrs"], ref["realPtrs"])
     assert np.array_equal(got["v2r"], ref["v2r"])
     assert np.array_equal(got["rowIds"], ref["rowIds"])
     assert np.array_equal(got["masks"], ref["masks"])
-    info = h.info()
     assert info["nnz"] == g.nnz and info["num_slices"] == ref["num_slices"]
     u = oracle.update_divergence(ref)
     assert abs(info["update_divergence"] - u) <= 1e-12 * max(1.0, abs(u))
@@ -102,11 +106,13 @@ def test_device_output_and_level_log(case, blest):
     depth = int(ref.max())
     counts = np.bincount(ref[ref >= 0])
     deg = np.diff(g.row_ptr)
-    b = oracle.bvss(g, 8)
+    info = h.info()
+    sigma, tau = info["sigma"], info["tau"]
+    b = oracle.bvss(g, sigma, tau)
     per_set = np.diff(b["realPtrs"])
     # one record per level whose input queue is non-empty: levels 1..depth,
     # plus the level that scans the deepest frontier when it owns any VSS
-    last_q = int(per_set[np.unique(np.flatnonzero(ref == depth) // 8)].sum())
+    last_q = int(per_set[np.unique(np.flatnonzero(ref == depth) // sigma)].sum())
     assert len(log) == depth + (1 if last_q > 0 else 0)
     visited = 0
     for k, rec in enumerate(log):
@@ -116,8 +122,10 @@ def test_device_output_and_level_log(case, blest):
         assert rec["frontier_edges"] == int(deg[frontier].sum())
         visited += counts[k]
         assert rec["unvisited"] == g.n - visited
-        assert rec["queue"] == int(per_set[np.unique(frontier // 8)].sum())
+        assert rec["queue"] == int(per_set[np.unique(frontier // sigma)].sum())
+        assert rec["slots"] == rec["queue"] * tau
         assert 0 <= rec["mode"] < 5 and rec["t_ns"] >= 0
+        assert 0 <= rec["t_stage1_ns"] <= rec["t_ns"]
 
 
 def test_edge_cases(blest):
@@ -194,3 +202,43 @@ def test_rmat16_64_sources_bit_exact(blest):
         for k, s in enumerate(srcs):
             h.bfs(int(s), out)
             assert np.array_equal(out.cpu().numpy(), ref[k]), k
+
+
+def test_layout_options_are_checked(blest):
+    g = gg.rmat(9, seed=3)
+    for sigma, tau in [(8, 64), (16, 32), (16, 128), (32, 64), (12, 0)]:
+        with pytest.raises(blest.BlestError) as e:
+            blest.build_graph(g, sigma=sigma, tau=tau)
+        assert e.value.code == blest.ERR_INVALID, (sigma, tau)
+    # the b1 MMA hit test needs the Fig. 3 layout
+    with pytest.raises(blest.BlestError) as e:
+        blest.build_graph(g, sigma=8, tau=32, engine_tc=1)
+    assert e.value.code == blest.ERR_UNSUPPORTED
+    with blest.build_graph(g, sigma=16) as h:
+        assert h.info()["tau"] == 64
+        with pytest.raises(blest.BlestError) as e:
+            h.set_engine(True)
+        assert e.value.code == blest.ERR_UNSUPPORTED
+        # a fixed tensor-core mode runs its CUDA-core twin and the log says so
+        h.set_policy(blest.POLICY_FIXED, blest.MODE_PUSH_LAZY_TC)
+        s = int(gg.sources(g, 1, 3)[0])
+        assert np.array_equal(h.bfs(s), oracle.bfs(g, s))
+        assert {r["mode"] for r in h.level_log()} == {blest.MODE_PUSH_LAZY_CC}
+        # multi-source BFS and closeness group the 8 vertices of a slice set
+        with pytest.raises(blest.BlestError) as e:
+            h.msbfs(np.array([s], np.int32))
+        assert e.value.code == blest.ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("sigma,tau", LAYOUTS)
+def test_reordered_layouts_bit_exact(blest, sigma, tau):
+    """RCM and JaccardWithWindows (slice sets of sigma columns) under every
+    layout: levels equal the oracle's on the original graph."""
+    for g, reorder in [(gg.grid(61, 67, 0.05, 0.001, seed=8), blest.REORDER_RCM),
+                       (gg.rmat(12, seed=9), blest.REORDER_JACCARD)]:
+        with blest.build_graph(g, sigma=sigma, tau=tau, reorder=reorder, jaccard_window=1024) as h:
+            assert h.info()["reorder"] == reorder
+            for s in gg.sources(g, 3, 4):
+                for mode in (0, 2, 4):
+                    h.set_policy(blest.POLICY_FIXED, mode)
+                    assert np.array_equal(h.bfs(int(s)), oracle.bfs(g, int(s))), (reorder, mode, s)

@@ -27,14 +27,15 @@ MAKERS = {
 }
 
 
+@pytest.mark.parametrize("tau", [128, 32])
 @pytest.mark.parametrize("name", sorted(MAKERS))
 @pytest.mark.parametrize("k", [1, 37, 64, 200, 256, 700, 1024])
-def test_msbfs_levels(blest, name, k):
+def test_msbfs_levels(blest, name, k, tau):
     g = MAKERS[name]()
     rs = np.random.RandomState(k)
     srcs = rs.randint(0, g.n, size=k).astype(np.int32)   # duplicates allowed
     ref = oracle.bfs_many(g, srcs)
-    with blest.build_graph(g) as h:
+    with blest.build_graph(g, tau=tau) as h:
         got = h.msbfs(srcs)
         assert got.shape == ref.shape
         bad = np.argwhere(got != ref)
@@ -55,10 +56,11 @@ def test_msbfs_device_output(blest):
                                    lambda: gg.disjoint_union(gg.rmat(9, seed=1), gg.path(50),
                                                              gg.from_edges(3, [], [], True)),
                                    lambda: gg.star(2500), lambda: gg.lattice(33, 65)])
-def test_closeness_all_sources(blest, maker):
+@pytest.mark.parametrize("tau", [128, 32])
+def test_closeness_all_sources(blest, maker, tau):
     g = maker()
     far_r, reach_r, cc_r = oracle.closeness(g)
-    with blest.build_graph(g) as h:
+    with blest.build_graph(g, tau=tau) as h:
         far, cc, reach = h.closeness()
     assert np.array_equal(far, far_r)
     assert np.array_equal(reach, reach_r)

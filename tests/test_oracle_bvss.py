@@ -11,10 +11,11 @@ import oracle
 GOLD = os.path.join(os.path.dirname(__file__), "golden")
 
 
-def _brute_bvss(g, sigma):
+def _brute_bvss(g, sigma, tau=None):
     """Tiny-input brute force: dictionary of slice sets built arc by arc."""
     theta = 32 // sigma
-    tau = 32 * theta
+    tau = tau or 32 * theta
+    lanes = tau // theta
     Ns = (g.n + sigma - 1) // sigma
     sets = [dict() for _ in range(Ns)]
     for j in range(g.n):
@@ -29,7 +30,7 @@ def _brute_bvss(g, sigma):
             chunk = items[v * tau:(v + 1) * tau]
             chunk = chunk + [(0, 0)] * (tau - len(chunk))
             rows += [r for r, _ in chunk]
-            for l in range(32):
+            for l in range(lanes):
                 w = 0
                 for c in range(theta):
                     w |= chunk[l * theta + c][1] << (sigma * c)
@@ -39,24 +40,24 @@ def _brute_bvss(g, sigma):
     return np.array(rows, np.int64), np.array(masks, np.uint64), np.array(real), np.array(v2r)
 
 
-@pytest.mark.parametrize("sigma", [8, 16, 32])
+@pytest.mark.parametrize("sigma,tau", [(8, None), (16, None), (32, None), (8, 32)])
 @pytest.mark.parametrize("maker", [lambda: gg.er(70, 300, seed=1, directed=True),
                                    lambda: gg.rmat(8, seed=2), lambda: gg.star(300),
                                    lambda: gg.path(1)])
-def test_bvss_matches_brute_force(sigma, maker):
+def test_bvss_matches_brute_force(sigma, tau, maker):
     g = maker()
-    b = oracle.bvss(g, sigma)
-    rows, masks, real, v2r = _brute_bvss(g, sigma)
+    b = oracle.bvss(g, sigma, tau)
+    rows, masks, real, v2r = _brute_bvss(g, sigma, tau)
     assert np.array_equal(b["rowIds"], rows)
     assert np.array_equal(b["masks"].astype(np.uint64), masks)
     assert np.array_equal(b["realPtrs"], real)
     assert np.array_equal(b["v2r"], v2r)
 
 
-@pytest.mark.parametrize("sigma", [8, 16, 32])
-def test_bvss_invariants(sigma):
+@pytest.mark.parametrize("sigma,tau", [(8, None), (16, None), (32, None), (8, 32)])
+def test_bvss_invariants(sigma, tau):
     g = gg.rmat(13, seed=5)
-    b = oracle.bvss(g, sigma)
+    b = oracle.bvss(g, sigma, tau)
     tau, theta, Nv, Ns = b["tau"], b["theta"], b["Nv"], b["Ns"]
     sm = b["slot_masks"].reshape(Nv, tau)
     rows = b["rowIds"].reshape(Nv, tau)
@@ -142,20 +143,32 @@ def test_udiv_arithmetic_progression():
     assert abs(oracle.update_divergence(b) - expect) < 1e-12
 
 
-def test_udiv_vs_numpy_std():
+@pytest.mark.parametrize("sigma,tau", [(8, None), (16, None), (32, None), (8, 32)])
+def test_udiv_vs_numpy_std(sigma, tau):
     g = gg.rmat(10, seed=9)
-    b = oracle.bvss(g, 8)
-    tau, Nv = b["tau"], b["Nv"]
+    b = oracle.bvss(g, sigma, tau)
+    tau, Nv, theta = b["tau"], b["Nv"], b["theta"]
     tot = 0.0
     for v in range(Nv):
         cols = []
-        for c in range(4):
-            idx = [v * tau + l * 4 + c for l in range(32)]
+        for c in range(theta):
+            idx = [v * tau + l * theta + c for l in range(tau // theta)]
             sel = [i for i in idx if b["slot_masks"][i] != 0]
             if sel:
                 cols.append(np.std(b["rowIds"][sel].astype(np.float64)))
         tot += np.mean(cols)
     assert abs(oracle.update_divergence(b) - tot / Nv) <= 1e-9 * max(1.0, tot / Nv)
+
+
+def test_udiv_narrow_vss_arithmetic_progression():
+    """tau = 32: the 128 slices of rows 0..127 fill four VSSs of eight lane
+    words; column c of VSS q holds rows 32q + c, 32q + c + 4, ..., 8 terms
+    with step 4, population std 4*sqrt((8^2-1)/12)."""
+    g = gg.from_edges(136, [128] * 128, list(range(128)), symmetrize=False)
+    b = oracle.bvss(g, 8, 32)
+    assert b["Nv"] == 4 and b["lanes"] == 8 and b["masks"].size == 32
+    expect = 4.0 * np.sqrt((8 ** 2 - 1) / 12.0)
+    assert abs(oracle.update_divergence(b) - expect) < 1e-12
 
 
 def test_udiv_scrambled_rmat_below_threshold():

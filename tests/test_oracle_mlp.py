@@ -90,7 +90,7 @@ def test_regret_definition():
 
 
 def test_raw_features():
-    f = mlp.raw_features([0, 10], [3, 7], [100, -5], [2, 0], [1, 4], 16.0)
+    f = mlp.raw_features([0, 10], [3, 7], [100, -5], [256, 0], [1, 4], 16.0)
     assert f.shape == (2, 6)
     assert np.allclose(f[0], np.log1p([0, 3, 100, 256, 1, 16]))
     assert f[1, 2] == 0.0
