@@ -66,7 +66,8 @@ WORKLOADS = {
 }
 DEFAULT_WORKLOAD = "sssp_pair"
 # the other rows of the path, each with its own JSON line
-EXTRA_WORKLOADS = ["msbfs_rmat22", "closeness_rmat18", "closeness_grid2048_part", "bfs_many_ba10k"]
+EXTRA_WORKLOADS = ["msbfs_rmat22", "closeness_rmat18", "closeness_grid2048_part", "bfs_many_ba10k",
+                   "switch_heldout"]
 NUM_SOURCES = 64
 METRIC = "GTEPS (harm. mean/source), single-source BFS"
 
@@ -135,11 +136,11 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def algorithmic_bytes(log, n: int, reached: int) -> float:
+def algorithmic_bytes(log, n: int, reached: int, sigma: int = 8, tau: int = 128) -> float:
     """Bytes one BFS must move, from the engine's per-level log (one pass over
     each array it touches; no credit for caching):
-      top-down level: |Q| * 649 B (512 rowIds + 128 masks + 4 virtualToReal +
-        4 queue entry + 1 frontier byte);
+      top-down level: |Q| * (4 tau rowIds + 4 tau/theta mask words + 8 queue
+        entry + sigma/8 frontier bytes), 649 B per VSS at sigma 8, tau 128;
       lazy / bottom-up level: stage 2 reads V_curr and V_next (8 B per 32
         vertices) and writes V_curr and F for changed words (8 B per new vertex
         at most); bottom-up stage 1 reads V_curr and the in-neighbour mask
@@ -149,12 +150,13 @@ def algorithmic_bytes(log, n: int, reached: int) -> float:
       init: 4 B per vertex of levels and 5 bitvectors (20 B per 32 vertices).
     The caller adds 8 B per vertex for the un-permute of a reordered graph."""
     W = (n + 31) // 32
+    per_vss = 4.0 * tau + 4.0 * tau / (32 // sigma) + 8.0 + sigma / 8.0
     b = 4.0 * n + 20.0 * W + 8.0 * reached
     for i, rec in enumerate(log):
         mode = rec["mode"]
         new = log[i + 1]["frontier"] if i + 1 < len(log) else 0
         if mode in (0, 1, 2, 3):
-            b += rec["queue"] * 649.0
+            b += rec["queue"] * per_vss
         if mode in (2, 3, 4):
             b += 8.0 * W + 8.0 * min(new, W)
         if mode == 4:
@@ -210,11 +212,13 @@ def run_reference(args, rank, world):
 
 
 class GraphRun:
-    """One bench graph: handle, sources, edge counts and per-arm timings."""
+    """One bench graph: the plain handle (default layout), the tuned handle
+    (the autotuner's layout; the plain one when tuning is off), sources,
+    edge counts and per-arm timings."""
 
     def __init__(self, name, args, rank, dev, torch, blest, stream):
         build_fn, bopts, desc = GRAPHS[name]
-        self.name, self.desc = name, desc
+        self.name, self.desc, self.bopts = name, desc, bopts
         t0 = time.time()
         self.g = g = build_fn()
         self.gen_s = time.time() - t0
@@ -226,6 +230,7 @@ class GraphRun:
         self.h = blest.build(g.n, rp_d, col_d, **bopts)
         self.build_s = time.time() - t0
         del rp_d, col_d
+        self.h_tuned = self.h
         self.info = self.h.info()
         self.stream = stream
         self.h.set_stream(stream.cuda_stream, True)
@@ -241,21 +246,33 @@ class GraphRun:
             self.reached.append(int(r.sum().item()))
         self.ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in self.srcs]
 
-    def step(self, record):
+    def build_layout(self, blest, sigma, tau, weights, policy):
+        h = blest.build(self.g.n, self.g.row_ptr, self.g.col, sigma=sigma, tau=tau, **self.bopts)
+        if weights is not None:
+            h.load_model(weights)
+        h.set_policy(policy)
+        return h
+
+    def step(self, h, record):
         for i, s in enumerate(self.srcs):
             if record:
                 self.ev[i][0].record(self.stream)
-            self.h.bfs(int(s), self.out)
+            h.bfs(int(s), self.out)
             if record:
                 self.ev[i][1].record(self.stream)
 
-    def logs(self):
+    def logs(self, h):
         out = []
         for s in self.srcs:
-            self.h.bfs(int(s), self.out)
-            self.h.sync()
-            out.append(self.h.level_log())
+            h.bfs(int(s), self.out)
+            h.sync()
+            out.append(h.level_log())
         return out
+
+    def close(self):
+        if self.h_tuned is not self.h:
+            self.h_tuned.close()
+        self.h.close()
 
 
 def main():
@@ -269,6 +286,8 @@ def main():
     ap.add_argument("--sources", type=int, default=NUM_SOURCES)
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (tuned arm = default launch)")
     ap.add_argument("--levels", action="store_true", help="per-level log of the first source to stderr")
+    ap.add_argument("--tau", type=int, default=0, help="VSS width of the multi-source and closeness builds "
+                    "(0 = 128)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -307,36 +326,41 @@ def main():
         if weights is not None:
             r.h.load_model(weights)
         if not args.no_tune:
-            r.h.set_policy(tuned_policy)
-            r.h.set_stream(None, False)
-            tune_info[r.name] = autotune.autotune(r.h, r.tune_srcs, reps=2, stream=stream)
-            r.h.set_stream(stream.cuda_stream, True)
+            r.h_tuned, tune_info[r.name] = autotune.autotune_layout(
+                lambda sg, ta, r=r: r.build_layout(blest, sg, ta, weights, tuned_policy), r.tune_srcs, reps=2,
+                stream=stream)
+        r.h_tuned.set_stream(stream.cuda_stream, True)
         ti = tune_info.get(r.name, {})
         r.tuned = (int(ti.get("block_threads", 512)), int(ti.get("vss_batch", 2)), bool(ti.get("engine_tc", 0)))
         if args.levels and rank == 0:
-            r.h.set_policy(tuned_policy)
-            for rec in r.logs()[0]:
+            r.h_tuned.set_policy(tuned_policy)
+            for rec in r.logs(r.h_tuned)[0]:
                 print(r.name, "level", json.dumps(rec), file=sys.stderr)
 
     arms = {"plain": (blest.POLICY_HEURISTIC, "default", True), "tuned": (tuned_policy, "tuned", None)}
 
     def set_arm(r, arm):
+        """The arm's handle, configured: plain = default layout and launch,
+        the paper's rule with the b1 MMA hit test; tuned = the autotuner's
+        layout and launch under the learned policy."""
         pol, launch, tc = arms[arm]
+        h = r.h if arm == "plain" else r.h_tuned
         if launch == "default":
-            r.h.set_launch(512, 2)
+            h.set_launch(512, 2)
         else:
-            r.h.set_launch(r.tuned[0], r.tuned[1])
-        r.h.set_engine(r.tuned[2] if tc is None else tc)
-        r.h.set_policy(pol)
+            h.set_launch(r.tuned[0], r.tuned[1])
+        h.set_engine(r.tuned[2] if tc is None else tc)
+        h.set_policy(pol)
+        return h
 
     results = {}
     with ClockSampler(local) as clk:
         for arm in arms:
             for r in runs:
-                set_arm(r, arm)
+                h = set_arm(r, arm)
                 for _ in range(args.warmup):
-                    r.step(False)
-                r.h.sync()
+                    r.step(h, False)
+                h.sync()
             torch.cuda.synchronize()
             if dist:
                 dist.barrier()
@@ -346,8 +370,7 @@ def main():
             t0e.record(stream)
             for k in range(args.steps):
                 for r in runs:
-                    set_arm(r, arm)
-                    r.step(True)
+                    r.step(set_arm(r, arm), True)
                 torch.cuda.synchronize()
                 for r in runs:
                     for i in range(len(r.srcs)):
@@ -356,6 +379,7 @@ def main():
             torch.cuda.synchronize()
             for r in runs:
                 r.h.sync()
+                r.h_tuned.sync()
             if dist:
                 dist.barrier()
             tot = t0e.elapsed_time(t1e)
@@ -363,7 +387,7 @@ def main():
                 tt = torch.tensor([tot], device=dev)
                 dist.all_reduce(tt, op=dist.ReduceOp.MAX)
                 tot = float(tt.item())
-            results[arm] = (psm, tot, {r.name: r.logs() for r in runs})
+            results[arm] = (psm, tot, {r.name: r.logs(set_arm(r, arm)) for r in runs})
 
     def gteps_of(psm_by_graph):
         rates = []
@@ -387,20 +411,21 @@ def main():
     alg_b, dev_s = 0.0, 0.0
     for r in runs:
         logs = results["tuned"][2][r.name]
-        alg_b += sum(algorithmic_bytes(lg, r.g.n, rc) + (8.0 * r.g.n if r.info["reorder"] else 0.0)
-                     for lg, rc in zip(logs, r.reached))
+        ti = r.h_tuned.info()
+        alg_b += sum(algorithmic_bytes(lg, r.g.n, rc, ti["sigma"], ti["tau"]) +
+                     (8.0 * r.g.n if r.info["reorder"] else 0.0) for lg, rc in zip(logs, r.reached))
         dev_s += float(results["tuned"][0][r.name].mean(axis=0).sum()) * 1e-3
     achieved = alg_b / dev_s / 1e9
 
     # end to end through the C ABI with host buffers, headline arm
     e2e_rates, d2h = [], 0
     for r in runs:
-        set_arm(r, "tuned")
-        r.h.set_stream(None, False)
+        h = set_arm(r, "tuned")
+        h.set_stream(None, False)
         host = torch.empty(r.g.n, dtype=torch.int32).pin_memory().numpy()
         for s, e in zip(r.srcs, r.edges):
             t0 = time.perf_counter()
-            r.h.bfs(int(s), host)
+            h.bfs(int(s), host)
             e2e_rates.append(e / (time.perf_counter() - t0) / 1e9)
         d2h += 4 * r.g.n * len(r.srcs)
     e2e = harmonic(e2e_rates)
@@ -414,7 +439,8 @@ def main():
             "gteps_tuned": per_graph[r.name], "gteps_plain": plain_per[r.name],
             "per_source_ms_median_tuned": float(np.median(results["tuned"][0][r.name])),
             "per_source_ms_median_plain": float(np.median(results["plain"][0][r.name])),
-            "tuned_launch": {"block_threads": r.tuned[0], "vss_batch": r.tuned[1], "engine_tc": int(r.tuned[2])},
+            "tuned_launch": {"block_threads": r.tuned[0], "vss_batch": r.tuned[1], "engine_tc": int(r.tuned[2]),
+                             "sigma": int(r.h_tuned.info()["sigma"]), "tau": int(r.h_tuned.info()["tau"])},
             "graph_gen_s": round(r.gen_s, 1), "build_s": round(r.build_s, 2),
             "build_ms_device": round(r.info["build_ms"], 1),
             "levels_source0_tuned": [[x["mode"], x["queue"], round(x["t_ns"] / 1e3, 1)]
@@ -449,7 +475,7 @@ def main():
     if rank == 0:
         print(json.dumps(line), flush=True)
     for r in runs:
-        r.h.close()
+        r.close()
     if dist:
         dist.destroy_process_group()
 
@@ -472,7 +498,7 @@ def run_extra(args, rank, world, local):
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic"}
     if args.workload == "msbfs_rmat22":
         g = gg.rmat(22, 16, seed=3)
-        h = blest.build(g.n, g.row_ptr, g.col)
+        h = blest.build(g.n, g.row_ptr, g.col, tau=args.tau)
         h.set_stream(stream.cuda_stream, True)
         deg = torch.from_numpy(np.diff(g.row_ptr)).to(dev)
         res = {}
@@ -516,7 +542,7 @@ def run_extra(args, rank, world, local):
             g = gg.grid(2048, 2048, 0.05, 0.001, seed=4)
             first, count = 0, 8 * 1024
             desc = "2048x2048 road-like grid, sources 0..8191 (8 of the 4096 batches of 1024)"
-        h = blest.build(g.n, g.row_ptr, g.col)
+        h = blest.build(g.n, g.row_ptr, g.col, tau=args.tau)
         h.set_stream(stream.cuda_stream, False)
         far = torch.empty(g.n, dtype=torch.int64, device=dev)
         reach = torch.empty(g.n, dtype=torch.int64, device=dev)
@@ -535,9 +561,11 @@ def run_extra(args, rank, world, local):
                      "value": count / (ms * 1e-3), "unit": "BFS/s", "ms_per_step": ms,
                      "gteps_est": pairs * mean_deg / 2 / (ms * 1e-3) / 1e9,
                      "config": {"workload": args.workload, "graph": desc, "n": g.n, "nnz": g.nnz,
-                                "sources": count, "batch": 1024},
+                                "sources": count, "batch": 1024, "tau": h.info()["tau"]},
                      "full_run_estimate_s": (g.n / count) * ms * 1e-3,
                      "gpu_launches": (count + 1023) // 1024})
+    elif args.workload == "switch_heldout":
+        line.update(run_heldout(args, torch, blest, dev, stream))
     else:
         b = gg.ba_batch(10000, 1000, 100000, 4, seed=3)
         srcs = np.zeros(b.g, np.int32)            # vertex 0 of every graph
@@ -567,6 +595,60 @@ def run_extra(args, rank, world, local):
                      "gpu_launches": args.steps})
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def run_heldout(args, torch, blest, dev, stream):
+    """The learned level-mode policy on graph families it was not trained on
+    (RMAT scale 25, Barabasi-Albert 2^24 m = 8, random geometric 2^24 with
+    average degree 10): per-level device times of every mode give the time
+    regret of the learned policy and of the paper's rule against the
+    per-level optimum; whole-BFS GTEPS of both policies on the same sources."""
+    from paper_2606_05081_gb300 import switch
+    w = switch.load_weights()
+    if w is None:
+        return {"metric": "switching regret", "value": None, "unavailable": "no trained weights"}
+    fams = [("rmat25", lambda: gg.rmat(25, 16, seed=25), "RMAT scale 25, edge factor 16"),
+            ("ba16m_m8", lambda: gg.ba(1 << 24, 8, seed=26), "Barabasi-Albert, 2^24 vertices, m = 8"),
+            ("rgg16m", lambda: gg.rgg(1 << 24, 10.0, seed=27), "random geometric, 2^24 points, average degree 10")]
+    per, regs = {}, []
+    for name, mk, desc in fams:
+        g = mk()
+        srcs = gg.sources(g, args.sources, 5)
+        h = blest.build(g.n, g.row_ptr, g.col)
+        h.set_stream(stream.cuda_stream, True)
+        h.load_model(w)
+        ev = switch.evaluate(h, srcs[:8], w, reps=2)
+        deg = np.diff(g.row_ptr)
+        out = torch.empty(g.n, dtype=torch.int32, device=dev)
+        rates = {}
+        for pol, tc in (("learned", False), ("heuristic", True)):
+            h.set_engine(tc)
+            h.set_policy(blest.POLICY_LEARNED if pol == "learned" else blest.POLICY_HEURISTIC)
+            r = []
+            for s in srcs:
+                h.bfs(int(s), out)
+                h.sync()
+                a, b = _events(torch)
+                a.record(stream)
+                h.bfs(int(s), out)
+                b.record(stream)
+                torch.cuda.synchronize()
+                h.sync()
+                lv = out.cpu().numpy()
+                r.append(deg[lv >= 0].sum() / 2 / (a.elapsed_time(b) * 1e-3) / 1e9)
+            rates[pol] = harmonic(r)
+        per[name] = {"graph": desc, "n": g.n, "nnz": g.nnz, "regret_learned": ev["regret_learned"],
+                     "regret_heuristic_tc": ev["regret_heuristic_tc"], "regret_heuristic_cc": ev["regret_heuristic_cc"],
+                     "ms_learned": ev["ms_learned"], "ms_heuristic_tc": ev["ms_heuristic_tc"],
+                     "ms_optimal": ev["ms_optimal"], "gteps_learned": rates["learned"],
+                     "gteps_heuristic_tc": rates["heuristic"]}
+        regs.append(ev["regret_learned"])
+        h.close()
+        del g
+    return {"metric": "switching regret of the learned policy (held-out families), mean", "value": float(np.mean(regs)),
+            "unit": "fraction over the per-level optimum", "higher_is_better": False,
+            "config": {"workload": "switch_heldout", "sources": args.sources, "regret_sources": 8},
+            "per_family": per, "gpu_launches": None}
 
 
 if __name__ == "__main__":

@@ -330,9 +330,11 @@ __device__ void push_level(const BfsParams &P, Stage &st, int ell, int bc, int b
                 }
                 // phase 2: claim the unvisited ones.  Lanes whose rows share a frontier
                 // word OR their bits together and one of them issues the atomic (rows
-                // of a VSS are often consecutive); degree and VSS-range loads ride along.
-                unsigned old[4];
-                int dg[4], a[4], len[4], sso[4];
+                // of a VSS are often consecutive).  All of a lane's atomics and its
+                // degree and VSS-range loads are issued before any result is used, so
+                // they cost one round trip together.
+                unsigned old[4], ov[4];
+                int dg[4], a[4], len[4], sso[4], leader[4];
                 unsigned cand = 0;
 #pragma unroll
                 for (int c = 0; c < THETA; ++c) {
@@ -340,21 +342,27 @@ __device__ void push_level(const BfsParams &P, Stage &st, int ell, int bc, int b
                     const int key = cd ? (u[c] >> 5) : -1;
                     const unsigned peers = __match_any_sync(FULL_MASK, key);
                     const unsigned bits = __reduce_or_sync(peers, cd ? (1u << (u[c] & 31)) : 0u);
-                    const int leader = __ffs(peers) - 1;
-                    unsigned o = 0u;
-                    if (cd && lane == leader) o = atomicOr(&Fn[key], bits);
-                    o = __shfl_sync(FULL_MASK, o, leader);
-                    old[c] = cd ? o : 0xFFFFFFFFu;
+                    leader[c] = __ffs(peers) - 1;
+                    ov[c] = 0u;
+                    if (cd && lane == leader[c]) ov[c] = atomicOr(&Fn[key], bits);
+                    if (cd) cand |= 1u << c;
+                }
+#pragma unroll
+                for (int c = 0; c < THETA; ++c) {
+                    sso[c] = u[c] >> LY::LOGS;
                     dg[c] = 0;
                     a[c] = 0;
                     len[c] = 0;
-                    sso[c] = u[c] >> LY::LOGS;
-                    if (cd) {
-                        cand |= 1u << c;
+                    if (cand >> c & 1u) {
                         dg[c] = __ldg(&P.deg[u[c]]);
                         a[c] = __ldg(&P.realPtrs[sso[c]]);
                         len[c] = __ldg(&P.realPtrs[sso[c] + 1]);
                     }
+                }
+#pragma unroll
+                for (int c = 0; c < THETA; ++c) {
+                    const unsigned o = __shfl_sync(FULL_MASK, ov[c], leader[c]);
+                    old[c] = (cand >> c & 1u) ? o : 0xFFFFFFFFu;
                 }
 #pragma unroll
                 for (int c = THETA; c < 4; ++c) { a[c] = 0; len[c] = 0; sso[c] = 0; }
@@ -654,19 +662,26 @@ __device__ __forceinline__ void housekeeping(const BfsParams &P, int ell, int bo
 template <bool EAGER, int SIGMA, int LPV>
 __device__ __forceinline__ void push_dispatch(const BfsParams &P, Stage &st, bool tc, int ell, int bc, int bn, int sn,
                                               int qlen, unsigned bsel) {
-    // eager levels keep at most two passes in flight (their per-slice state
-    // would not fit the 64-register budget of a 1024-thread CTA for four)
-    if constexpr (Lay<SIGMA, LPV>::TC_OK) {
-        if (tc) {
-            if (!EAGER && P.batch >= 4) push_level<EAGER, true, EAGER ? 2 : 4, SIGMA, LPV>(P, st, ell, bc, bn, sn, qlen, bsel);
-            else if (P.batch >= 2) push_level<EAGER, true, 2, SIGMA, LPV>(P, st, ell, bc, bn, sn, qlen, bsel);
-            else push_level<EAGER, true, 1, SIGMA, LPV>(P, st, ell, bc, bn, sn, qlen, bsel);
-            return;
+    // eager levels run one pass at a time (their atomics and loads already
+    // overlap within a pass, and a second pass's state would not fit the
+    // 64-register budget of a 1024-thread CTA); lazy levels keep 1, 2 or 4
+    if constexpr (EAGER) {
+        if constexpr (Lay<SIGMA, LPV>::TC_OK)
+            if (tc) { push_level<true, true, 1, SIGMA, LPV>(P, st, ell, bc, bn, sn, qlen, bsel); return; }
+        push_level<true, false, 1, SIGMA, LPV>(P, st, ell, bc, bn, sn, qlen, bsel);
+    } else {
+        if constexpr (Lay<SIGMA, LPV>::TC_OK) {
+            if (tc) {
+                if (P.batch >= 4) push_level<false, true, 4, SIGMA, LPV>(P, st, ell, bc, bn, sn, qlen, bsel);
+                else if (P.batch >= 2) push_level<false, true, 2, SIGMA, LPV>(P, st, ell, bc, bn, sn, qlen, bsel);
+                else push_level<false, true, 1, SIGMA, LPV>(P, st, ell, bc, bn, sn, qlen, bsel);
+                return;
+            }
         }
+        if (P.batch >= 4) push_level<false, false, 4, SIGMA, LPV>(P, st, ell, bc, bn, sn, qlen, bsel);
+        else if (P.batch >= 2) push_level<false, false, 2, SIGMA, LPV>(P, st, ell, bc, bn, sn, qlen, bsel);
+        else push_level<false, false, 1, SIGMA, LPV>(P, st, ell, bc, bn, sn, qlen, bsel);
     }
-    if (!EAGER && P.batch >= 4) push_level<EAGER, false, EAGER ? 2 : 4, SIGMA, LPV>(P, st, ell, bc, bn, sn, qlen, bsel);
-    else if (P.batch >= 2) push_level<EAGER, false, 2, SIGMA, LPV>(P, st, ell, bc, bn, sn, qlen, bsel);
-    else push_level<EAGER, false, 1, SIGMA, LPV>(P, st, ell, bc, bn, sn, qlen, bsel);
 }
 
 template <int SIGMA, int LPV>
@@ -676,7 +691,7 @@ __global__ void __launch_bounds__(BFS_MAX_THREADS, 1) k_bfs(BfsParams P) {
     __shared__ float s_mlp[MLP_NW];
     extern __shared__ __align__(16) unsigned char s_stage[];   // STG_BYTES per warp
     if (P.policy == BLEST_POLICY_LEARNED && P.mlp) {
-        for (int i = threadIdx.x; i < MLP_NW; i += blockDim.x) s_mlp[i] = P.mlp[i];
+        mlp_stage_weights(P.mlp, s_mlp);
         __syncthreads();
         P.mlp = s_mlp;
     }

@@ -153,9 +153,14 @@ __global__ void k_mlp_features(const blest_level_log *__restrict__ recs, int n, 
     for (int i = 0; i < MLP_IN; ++i) out[(size_t)s * MLP_IN + i] = x[i];
 }
 
-// one warp per sample, the in-kernel inference routine itself
+// one warp per sample, the in-kernel inference routine itself (weights
+// staged in shared memory exactly as the BFS kernel stages them)
 __global__ void k_mlp_predict(const float *__restrict__ w, const float *__restrict__ feats, int n, float *pred,
                               int *choice) {
+    __shared__ float sw[MLP_NW];
+    mlp_stage_weights(w, sw);
+    __syncthreads();
+    w = sw;
     const int s = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     if (s >= n) return;
     float x[MLP_IN];

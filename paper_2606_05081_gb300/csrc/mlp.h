@@ -37,9 +37,31 @@ __host__ __device__ inline void mlp_raw_features(float *x, long long frontier, l
     x[5] = log1pf(avg_deg);
 }
 
+// Shared-memory copy of the weights for the warp-cooperative forward pass:
+// the same MLP_NW values with W1, W2 and W3 stored transposed (input-major),
+// so the lanes of a warp read consecutive words (no bank conflicts).  Called
+// by every thread of the block; the caller synchronises afterwards.
+__device__ __forceinline__ void mlp_stage_weights(const float *__restrict__ w, float *s) {
+    for (int i = threadIdx.x; i < MLP_NW; i += blockDim.x) {
+        int d = i;
+        if (i >= MLP_OFF_W1 && i < MLP_OFF_B1) {            // W1[h][k] -> [k][h]
+            const int r = (i - MLP_OFF_W1) / MLP_IN, c = (i - MLP_OFF_W1) % MLP_IN;
+            d = MLP_OFF_W1 + c * MLP_H + r;
+        } else if (i >= MLP_OFF_W2 && i < MLP_OFF_B2) {     // W2[h][k] -> [k][h]
+            const int r = (i - MLP_OFF_W2) / MLP_H, c = (i - MLP_OFF_W2) % MLP_H;
+            d = MLP_OFF_W2 + c * MLP_H + r;
+        } else if (i >= MLP_OFF_W3 && i < MLP_OFF_B3) {     // W3[o][k] -> [k][o]
+            const int r = (i - MLP_OFF_W3) / MLP_H, c = (i - MLP_OFF_W3) % MLP_H;
+            d = MLP_OFF_W3 + c * MLP_OUT + r;
+        }
+        s[d] = w[i];
+    }
+}
+
 // Warp-cooperative forward pass on raw features x (all 32 lanes call it;
-// lane h owns hidden unit h of both layers).  Lane o < MLP_OUT returns the
-// prediction for mode o (other lanes return 0).
+// lane h owns hidden unit h of both layers), weights staged by
+// mlp_stage_weights.  Lane o < MLP_OUT returns the prediction for mode o
+// (other lanes return 0).  Sums run in input order with fused multiply-adds.
 __device__ __forceinline__ float mlp_forward_warp(const float *__restrict__ w, const float *xr) {
     const int lane = threadIdx.x & 31;
     float x[MLP_IN];
@@ -47,20 +69,17 @@ __device__ __forceinline__ float mlp_forward_warp(const float *__restrict__ w, c
     for (int i = 0; i < MLP_IN; ++i) x[i] = (xr[i] - w[MLP_OFF_MEAN + i]) * w[MLP_OFF_ISTD + i];
     float a1 = w[MLP_OFF_B1 + lane];
 #pragma unroll
-    for (int i = 0; i < MLP_IN; ++i) a1 = fmaf(w[MLP_OFF_W1 + lane * MLP_IN + i], x[i], a1);
+    for (int i = 0; i < MLP_IN; ++i) a1 = fmaf(w[MLP_OFF_W1 + i * MLP_H + lane], x[i], a1);
     const float h1 = tanhf(a1);
     float a2 = w[MLP_OFF_B2 + lane];
 #pragma unroll
-    for (int k = 0; k < MLP_H; ++k) a2 = fmaf(w[MLP_OFF_W2 + lane * MLP_H + k], __shfl_sync(0xFFFFFFFFu, h1, k), a2);
+    for (int k = 0; k < MLP_H; ++k) a2 = fmaf(w[MLP_OFF_W2 + k * MLP_H + lane], __shfl_sync(0xFFFFFFFFu, h1, k), a2);
     const float h2 = tanhf(a2);
-    float y = 0.f;
-    if (lane < MLP_OUT) y = w[MLP_OFF_B3 + lane];
+    const int o = lane < MLP_OUT ? lane : 0;
+    float y = w[MLP_OFF_B3 + o];
 #pragma unroll
-    for (int k = 0; k < MLP_H; ++k) {
-        const float hk = __shfl_sync(0xFFFFFFFFu, h2, k);
-        if (lane < MLP_OUT) y = fmaf(w[MLP_OFF_W3 + lane * MLP_H + k], hk, y);
-    }
-    return y;
+    for (int k = 0; k < MLP_H; ++k) y = fmaf(w[MLP_OFF_W3 + k * MLP_OUT + o], __shfl_sync(0xFFFFFFFFu, h2, k), y);
+    return lane < MLP_OUT ? y : 0.f;
 }
 
 // argmin over the MLP_OUT predictions (lowest index on ties); all lanes get it

@@ -12,8 +12,10 @@ per-level optimum of the paper's switching analysis, §7.1).
 
     python -m paper_2606_05081_gb300.switch train [--out PATH]
 
-trains on the standard training graphs (RMAT scales 16-24, a road-like
-grid, a Barabasi-Albert graph) and writes the weights next to this file.
+trains on the standard training graphs (RMAT scales 14-24, road-like
+grids, Barabasi-Albert graphs), each built with the warp-wide (tau = 128)
+and the narrow (tau = 32) sigma = 8 VSS, and writes the weights next to
+this file.
 """
 from __future__ import annotations
 
@@ -158,6 +160,9 @@ def save_weights(w, path: str = DEFAULT_WEIGHTS, meta: dict | None = None):
             json.dump(meta, f, indent=1)
 
 
+TRAIN_LAYOUTS = ((8, 128), (8, 32))
+
+
 def training_graphs():
     """The graph families of the single-source (RMAT, road-like grid) and
     batched (RMAT, Barabasi-Albert) workloads over the size range they are
@@ -188,14 +193,15 @@ def main(argv=None):
     Xs, Ys, names = [], [], []
     for name, make, opts in training_graphs():
         g = make()
-        h = build(g.n, g.row_ptr, g.col, **opts)
         srcs = gg.sources(g, args.sources, 100)
-        X, Y, M, _ = dataset([h], [srcs])
-        Xs.append(X)
-        Ys.append(Y)
-        names.append((name, int(len(X))))
-        h.close()
-        print(f"collected {name}: {len(X)} levels", file=sys.stderr)
+        for sigma, tau in TRAIN_LAYOUTS:
+            h = build(g.n, g.row_ptr, g.col, sigma=sigma, tau=tau, **opts)
+            X, Y, M, _ = dataset([h], [srcs])
+            Xs.append(X)
+            Ys.append(Y)
+            names.append((f"{name}_s{sigma}t{tau}", int(len(X))))
+            h.close()
+            print(f"collected {name} sigma {sigma} tau {tau}: {len(X)} levels", file=sys.stderr)
     X = np.concatenate(Xs)
     Y = np.concatenate(Ys)
     w, hist = train(X, Y, np.ones_like(Y), epochs=args.epochs)
