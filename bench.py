@@ -164,6 +164,37 @@ def algorithmic_bytes(log, n: int, reached: int, sigma: int = 8, tau: int = 128)
     return b
 
 
+KERNEL_SOURCES = ["paper_2606_05081_gb300/csrc/bfs.cu", "paper_2606_05081_gb300/csrc/common.cuh",
+                  "paper_2606_05081_gb300/csrc/mlp.h", "paper_2606_05081_gb300/csrc/handle.h"]
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_bfs_traffic.json")
+
+
+def kernel_sha() -> str:
+    import hashlib
+    hsh = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            hsh.update(fh.read())
+    return hsh.hexdigest()[:16]
+
+
+def measured_traffic(runs_layouts):
+    """Per-launch DRAM bytes of k_bfs (dram__bytes_read.sum + dram__bytes_write.sum
+    from ncu) for each (graph, sigma, tau) the step ran, averaged over its
+    graphs; None when a record is missing or was taken on other kernel
+    sources."""
+    if not os.path.exists(TRAFFIC_FILE):
+        return None
+    d = json.load(open(TRAFFIC_FILE))
+    if d.get("kernel_sha") != kernel_sha():
+        return None
+    recs = {(r["graph"], r["sigma"], r["tau"]): r["bytes_per_launch"] for r in d.get("records", [])}
+    vals = [recs.get(k) for k in runs_layouts]
+    if any(v is None for v in vals):
+        return None
+    return float(np.mean(vals))
+
+
 def harmonic(x):
     x = np.asarray(x, np.float64)
     return float(len(x) / np.sum(1.0 / x))
@@ -288,6 +319,9 @@ def main():
     ap.add_argument("--levels", action="store_true", help="per-level log of the first source to stderr")
     ap.add_argument("--tau", type=int, default=0, help="VSS width of the multi-source and closeness builds "
                     "(0 = 128)")
+    ap.add_argument("--layout", default=None, help="sigma,tau of the tuned arm when the autotuner is off")
+    ap.add_argument("--launch", default=None, help="block_threads,vss_batch of the tuned arm when the autotuner "
+                    "is off")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -329,6 +363,12 @@ def main():
             r.h_tuned, tune_info[r.name] = autotune.autotune_layout(
                 lambda sg, ta, r=r: r.build_layout(blest, sg, ta, weights, tuned_policy), r.tune_srcs, reps=2,
                 stream=stream)
+        elif args.layout:
+            sg, ta = (int(x) for x in args.layout.split(","))
+            r.h_tuned = r.build_layout(blest, sg, ta, weights, tuned_policy)
+        if args.no_tune and args.launch:
+            bt, bb = (int(x) for x in args.launch.split(","))
+            tune_info[r.name] = {"block_threads": bt, "vss_batch": bb, "engine_tc": 0, "fixed": True}
         r.h_tuned.set_stream(stream.cuda_stream, True)
         ti = tune_info.get(r.name, {})
         r.tuned = (int(ti.get("block_threads", 512)), int(ti.get("vss_batch", 2)), bool(ti.get("engine_tc", 0)))
@@ -458,7 +498,11 @@ def main():
                   "what": "hand-set rule (U_div lazy/eager, Eq. 5 switch), b1 MMA hit test, default launch"},
         "speedup_vs_plain": value / plain_value,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                     "traffic": None, "peak_kind": peak_kind, "kernel": "k_bfs (persistent, all levels)"},
+                     "traffic": measured_traffic([(r.name, r.h_tuned.info()["sigma"], r.h_tuned.info()["tau"])
+                                                  for r in runs]), "peak_kind": peak_kind,
+                     "kernel": "k_bfs (persistent, all levels)",
+                     "algorithmic_bytes_per_launch": alg_b / sum(len(r.srcs) for r in runs),
+                     "kernel_sha": kernel_sha()},
         "e2e": {"value": e2e, "unit": "GTEPS", "h2d_bytes_per_step": 4 * sum(len(r.srcs) for r in runs),
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": args.steps * sum(len(r.srcs) for r in runs) * len(arms),
