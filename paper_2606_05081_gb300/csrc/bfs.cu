@@ -243,23 +243,6 @@ __device__ __forceinline__ void enqueue_ranges(const BfsParams &P, Stage &st, un
     __syncwarp();
 }
 
-// Same, loading the VSS ranges of the slice sets first.
-__device__ __forceinline__ void enqueue_sets(const BfsParams &P, Stage &st, unsigned want, const int ss[4], int2 *Q,
-                                             int *SQ, int slot) {
-    if (!__any_sync(FULL_MASK, want != 0)) return;
-    int a[4], len[4];
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        a[c] = 0;
-        len[c] = 0;
-        if (want >> c & 1u) {
-            a[c] = __ldg(&P.realPtrs[ss[c]]);
-            len[c] = __ldg(&P.realPtrs[ss[c] + 1]) - a[c];
-        }
-    }
-    enqueue_ranges(P, st, want, ss, a, len, Q, SQ, slot);
-}
-
 __device__ __forceinline__ void flush_counts(const BfsParams &P, int slot, unsigned long long nv,
                                              unsigned long long fe) {
     nv = warp_sum(nv);
@@ -277,19 +260,27 @@ __device__ __forceinline__ void flush_counts(const BfsParams &P, int slot, unsig
 // then their frontier fields, before using any of them, so the
 // dependent-load chain is paid once per B*G VSSs.
 template <bool EAGER, bool TC, int B, int SIGMA, int LPV>
-__device__ void push_level(const BfsParams &P, Stage &st, int ell, int bc, int bn, int slot, int qlen,
+__device__ void push_level(const BfsParams &P, Stage &st, int *grab, int ell, int bc, int bn, int slot, int qlen,
                            unsigned bsel) {
     using LY = Lay<SIGMA, LPV>;
     constexpr int THETA = LY::THETA, G = LY::G;
     const int lane = lane_id();
     const int grp = lane / LPV, sl = lane % LPV;
-    const int gwarp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
     const unsigned *Fc = P.F[bc];
     unsigned *Fn = P.F[bn];
     const int2 *Qc = P.Q[bc];
     unsigned long long nv = 0, fe = 0;
-    for (int w0 = gwarp * B * G; w0 < qlen; w0 += nwarps * B * G) {
+    // passes of B*G queue entries, interleaved over the blocks; the warps of a
+    // block claim their block's next pass from a shared counter, so a warp
+    // whose passes hit many rows does not hold up the level
+    const int npass = (qlen + B * G - 1) / (B * G);
+    for (;;) {
+        int k = 0;
+        if (lane == 0) k = atomicAdd(grab, 1);
+        k = __shfl_sync(FULL_MASK, k, 0);
+        const int pass = (int)blockIdx.x + k * (int)gridDim.x;
+        if (pass >= npass) break;
+        const int w0 = pass * B * G;
         int vss[B], ss[B];
         int r[B][4];
         unsigned m[B], alpha[B];
@@ -438,15 +429,21 @@ __device__ __forceinline__ int nth_set_bit(unsigned x, int k) {
     return pos;
 }
 
-__device__ void bottom_up_level(const BfsParams &P, int bc, int slot, unsigned *s_found) {
+__device__ void bottom_up_level(const BfsParams &P, int *grab, int bc, int slot, unsigned *s_found) {
     const int lane = lane_id();
-    const int gwarp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
     unsigned *found = s_found + (threadIdx.x >> 5) * 32;
     const unsigned *Fc = P.F[bc];
     const int tail = P.n & 31;
     unsigned long long sv = 0, sa = 0;
-    for (int base = gwarp * 32; base < P.W; base += nwarps * 32) {
+    // 32-word groups interleaved over the blocks, claimed by the block's warps
+    const int ngroups = (P.W + 31) / 32;
+    for (;;) {
+        int k = 0;
+        if (lane == 0) k = atomicAdd(grab, 1);
+        k = __shfl_sync(FULL_MASK, k, 0);
+        const int grp = (int)blockIdx.x + k * (int)gridDim.x;
+        if (grp >= ngroups) break;
+        const int base = grp * 32;
         const int w = base + lane;
         unsigned vis = 0u, unv = 0u;
         if (w < P.W) {
@@ -545,26 +542,33 @@ __device__ void bottom_up_level(const BfsParams &P, int bc, int slot, unsigned *
 // for the level stores and degree loads, so both are coalesced.  A word
 // holds theta = 32/SIGMA slice-set fields; a changed field enqueues its set.
 template <int SIGMA>
-__device__ void finalize_level(const BfsParams &P, Stage &st, int ell, int bn, int slot) {
+__device__ void finalize_level(const BfsParams &P, Stage &st, int *grab, int ell, int bn, int slot) {
     constexpr int THETA = 32 / SIGMA;
     constexpr unsigned FMASK = SIGMA == 32 ? 0xFFFFFFFFu : ((1u << SIGMA) - 1u);
     const int lane = lane_id();
-    const int gwarp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
     unsigned *Fn = P.F[bn];
     unsigned long long nv = 0, fe = 0;
-    for (int base0 = gwarp * 32; base0 < P.W; base0 += 2 * nwarps * 32) {
-      // the visited words of both groups are loaded before either is used
+    // a claim covers two 32-word groups, i and i + half, whose visited words
+    // are loaded before either is used; claims are interleaved over the blocks
+    // and taken by the block's warps from a shared counter (the changed words
+    // cluster, so a fixed split leaves a few warps with most of the work)
+    const int ngroups = (P.W + 31) / 32, half = (ngroups + 1) / 2;
+    for (;;) {
+      int k = 0;
+      if (lane == 0) k = atomicAdd(grab, 1);
+      k = __shfl_sync(FULL_MASK, k, 0);
+      const int i = (int)blockIdx.x + k * (int)gridDim.x;
+      if (i >= half) break;
       unsigned nx[2], cu[2];
 #pragma unroll
       for (int g2 = 0; g2 < 2; ++g2) {
-          const int tt = base0 + g2 * nwarps * 32 + lane;
+          const int tt = (i + g2 * half) * 32 + lane;
           nx[g2] = tt < P.W ? P.Vn[tt] : 0u;
           cu[g2] = tt < P.W ? P.Vc[tt] : 0u;
       }
 #pragma unroll 1
       for (int g2 = 0; g2 < 2; ++g2) {
-        const int base = base0 + g2 * nwarps * 32;
+        const int base = (i + g2 * half) * 32;
         const int t = base + lane;
         unsigned diff = 0;
         if (t < P.W) {
@@ -575,34 +579,43 @@ __device__ void finalize_level(const BfsParams &P, Stage &st, int ell, int bn, i
                 nv += (unsigned long long)__popc(diff);
             }
         }
+        // the VSS ranges of the changed slice-set fields load while the level
+        // stores and degree loads below are in flight
+        unsigned want = 0;
+        int sso[4] = {0, 0, 0, 0}, ra[4] = {0, 0, 0, 0}, rl[4] = {0, 0, 0, 0};
+#pragma unroll
+        for (int c = 0; c < THETA; ++c) {
+            sso[c] = t * THETA + c;
+            if ((diff >> (SIGMA * c)) & FMASK) {
+                want |= 1u << c;
+                ra[c] = __ldg(&P.realPtrs[sso[c]]);
+                rl[c] = __ldg(&P.realPtrs[sso[c] + 1]);
+            }
+        }
         const unsigned changed = __ballot_sync(FULL_MASK, diff != 0);
         if (changed) {
-            // eight words per round: their degree loads are independent and in flight together
-#pragma unroll 1
-            for (int j0 = 0; j0 < 32; j0 += 8) {
-                if (!((changed >> j0) & 0xFFu)) continue;   // warp-uniform
-                unsigned long long d8 = 0;
+            // lane = vertex over the changed words, eight words per round; the
+            // rounds keep separate sums so all their degree loads can be in flight
+            unsigned long long d8[4] = {0, 0, 0, 0};
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                if (!((changed >> (8 * r)) & 0xFFu)) continue;   // warp-uniform
 #pragma unroll
                 for (int k = 0; k < 8; ++k) {
-                    const int j = j0 + k;
+                    const int j = 8 * r + k;
                     const unsigned dj = __shfl_sync(FULL_MASK, diff, j);
                     if (dj >> lane & 1u) {
                         const int u = ((base + j) << 5) + lane;
                         P.L[u] = ell;
-                        d8 += (unsigned long long)__ldg(&P.deg[u]);
+                        d8[r] += (unsigned long long)__ldg(&P.deg[u]);
                     }
                 }
-                fe += d8;
             }
+            fe += d8[0] + d8[1] + d8[2] + d8[3];
         }
-        unsigned want = 0;
-        int sso[4] = {0, 0, 0, 0};
 #pragma unroll
-        for (int c = 0; c < THETA; ++c) {
-            sso[c] = t * THETA + c;
-            if ((diff >> (SIGMA * c)) & FMASK) want |= 1u << c;
-        }
-        enqueue_sets(P, st, want, sso, P.Q[bn], P.SQ[bn], slot);
+        for (int c = 0; c < 4; ++c) rl[c] -= ra[c];
+        enqueue_ranges(P, st, want, sso, ra, rl, P.Q[bn], P.SQ[bn], slot);
       }
     }
     stage_flush(P, st, P.Q[bn], P.SQ[bn], slot);
@@ -660,30 +673,35 @@ __device__ __forceinline__ void housekeeping(const BfsParams &P, int ell, int bo
 }
 
 template <bool EAGER, int SIGMA, int LPV>
-__device__ __forceinline__ void push_dispatch(const BfsParams &P, Stage &st, bool tc, int ell, int bc, int bn, int sn,
-                                              int qlen, unsigned bsel) {
+__device__ __forceinline__ void push_dispatch(const BfsParams &P, Stage &st, int *grab, bool tc, int ell, int bc,
+                                              int bn, int sn, int qlen, unsigned bsel) {
     // eager levels run one pass at a time (their atomics and loads already
     // overlap within a pass, and a second pass's state would not fit the
     // 64-register budget of a 1024-thread CTA); lazy levels keep 1, 2 or 4
     if constexpr (EAGER) {
         if constexpr (Lay<SIGMA, LPV>::TC_OK)
-            if (tc) { push_level<true, true, 1, SIGMA, LPV>(P, st, ell, bc, bn, sn, qlen, bsel); return; }
-        push_level<true, false, 1, SIGMA, LPV>(P, st, ell, bc, bn, sn, qlen, bsel);
+            if (tc) { push_level<true, true, 1, SIGMA, LPV>(P, st, grab, ell, bc, bn, sn, qlen, bsel); return; }
+        push_level<true, false, 1, SIGMA, LPV>(P, st, grab, ell, bc, bn, sn, qlen, bsel);
     } else {
         if constexpr (Lay<SIGMA, LPV>::TC_OK) {
             if (tc) {
-                if (P.batch >= 4) push_level<false, true, 4, SIGMA, LPV>(P, st, ell, bc, bn, sn, qlen, bsel);
-                else if (P.batch >= 2) push_level<false, true, 2, SIGMA, LPV>(P, st, ell, bc, bn, sn, qlen, bsel);
-                else push_level<false, true, 1, SIGMA, LPV>(P, st, ell, bc, bn, sn, qlen, bsel);
+                if (P.batch >= 4) push_level<false, true, 4, SIGMA, LPV>(P, st, grab, ell, bc, bn, sn, qlen, bsel);
+                else if (P.batch >= 2) push_level<false, true, 2, SIGMA, LPV>(P, st, grab, ell, bc, bn, sn, qlen, bsel);
+                else push_level<false, true, 1, SIGMA, LPV>(P, st, grab, ell, bc, bn, sn, qlen, bsel);
                 return;
             }
         }
-        if (P.batch >= 4) push_level<false, false, 4, SIGMA, LPV>(P, st, ell, bc, bn, sn, qlen, bsel);
-        else if (P.batch >= 2) push_level<false, false, 2, SIGMA, LPV>(P, st, ell, bc, bn, sn, qlen, bsel);
-        else push_level<false, false, 1, SIGMA, LPV>(P, st, ell, bc, bn, sn, qlen, bsel);
+        if (P.batch >= 4) push_level<false, false, 4, SIGMA, LPV>(P, st, grab, ell, bc, bn, sn, qlen, bsel);
+        else if (P.batch >= 2) push_level<false, false, 2, SIGMA, LPV>(P, st, grab, ell, bc, bn, sn, qlen, bsel);
+        else push_level<false, false, 1, SIGMA, LPV>(P, st, grab, ell, bc, bn, sn, qlen, bsel);
     }
 }
 
+// One register budget for every CTA size: 64 a thread (1024 threads per
+// SM).  Measured on GB300, 16 resident warps at 128 registers were 20-50 %
+// slower and 48 warps at 40 registers (heavy spilling) up to 40 % slower on
+// the road-like grid: the kernel is latency-bound and 32 warps is the best
+// trade.
 template <int SIGMA, int LPV>
 __global__ void __launch_bounds__(BFS_MAX_THREADS, 1) k_bfs(BfsParams P) {
     using LY = Lay<SIGMA, LPV>;
@@ -708,6 +726,7 @@ __global__ void __launch_bounds__(BFS_MAX_THREADS, 1) k_bfs(BfsParams P) {
     st.sqn = 0;
     __shared__ int s_mode;
     __shared__ long long s_lvl[4];
+    __shared__ int s_grab[3];   // per-level work claims: push passes, stage-2 groups, bottom-up groups
 
     // ---- level 0 (Algorithm 2/3 init): L = inf except the source, frontier
     // and visited bits hold the source, Q = VSSs of the source's slice set.
@@ -763,6 +782,9 @@ __global__ void __launch_bounds__(BFS_MAX_THREADS, 1) k_bfs(BfsParams P) {
                 s_lvl[2] = c4[2];
                 s_lvl[3] = c4[3];
                 s_mode = m;
+                s_grab[0] = 0;
+                s_grab[1] = 0;
+                s_grab[2] = 0;
             }
         }
         __syncthreads();
@@ -804,20 +826,20 @@ __global__ void __launch_bounds__(BFS_MAX_THREADS, 1) k_bfs(BfsParams P) {
         if (qlen == 0) break;
 
         if (mode == BLEST_MODE_PUSH_EAGER_CC || mode == BLEST_MODE_PUSH_EAGER_TC) {
-            push_dispatch<true, SIGMA, LPV>(P, st, mode == BLEST_MODE_PUSH_EAGER_TC, ell, bc, bn, sn, qlen, bsel);
+            push_dispatch<true, SIGMA, LPV>(P, st, &s_grab[0], mode == BLEST_MODE_PUSH_EAGER_TC, ell, bc, bn, sn, qlen, bsel);
             housekeeping<SIGMA>(P, ell, bo, sql_old, sz, tid, nthreads);
             if (!grid_barrier(ctl, epoch, P.budget_ns)) return;
         } else {
             if (mode == BLEST_MODE_BOTTOM_UP)
-                bottom_up_level(P, bc, sn, s_found);
+                bottom_up_level(P, &s_grab[2], bc, sn, s_found);
             else
-                push_dispatch<false, SIGMA, LPV>(P, st, mode == BLEST_MODE_PUSH_LAZY_TC, ell, bc, bn, sn, qlen,
+                push_dispatch<false, SIGMA, LPV>(P, st, &s_grab[0], mode == BLEST_MODE_PUSH_LAZY_TC, ell, bc, bn, sn, qlen,
                                                  bsel);
             housekeeping<SIGMA>(P, ell, bo, sql_old, sz, tid, nthreads);
             if (!grid_barrier(ctl, epoch, P.budget_ns)) return;
             if (logger && ell - 1 < P.log_cap)
                 P.log[ell - 1].t_stage1_ns = (long long)global_ns() - P.log[ell - 1].t_ns;
-            finalize_level<SIGMA>(P, st, ell, bn, sn);
+            finalize_level<SIGMA>(P, st, &s_grab[1], ell, bn, sn);
             if (!grid_barrier(ctl, epoch, P.budget_ns)) return;
         }
     }
@@ -828,7 +850,8 @@ __global__ void __launch_bounds__(BFS_MAX_THREADS, 1) k_bfs(BfsParams P) {
 }
 
 // the kernel instance of a (sigma, tau) layout (nullptr for other pairs)
-const void *bfs_kernel_for(int sigma, int tau) {
+// the kernel instance of a (sigma, tau) layout (nullptr for other pairs)
+const void *bfs_kernel_for(int sigma, int tau, int /*block*/) {
     if (sigma == 8 && tau == 128) return (const void *)k_bfs<8, 32>;
     if (sigma == 8 && tau == 32) return (const void *)k_bfs<8, 8>;
     if (sigma == 16 && tau == 64) return (const void *)k_bfs<16, 32>;
@@ -842,14 +865,14 @@ const void *bfs_kernel_for(int sigma, int tau) {
 static size_t bfs_smem(int block) { return (size_t)(block / 32) * STG_BYTES; }
 
 static int bfs_grid_for_layout(int sigma, int tau, int block, int *num_sms) {
-    const void *kern = bfs_kernel_for(sigma, tau);
+    const void *kern = bfs_kernel_for(sigma, tau, block);
     if (!kern) return 0;
     int dev = 0;
     cudaGetDevice(&dev);
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)bfs_smem(BFS_MAX_THREADS)) != cudaSuccess)
+                             (int)bfs_smem(block)) != cudaSuccess)
         return 0;
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, bfs_smem(block));
@@ -909,7 +932,7 @@ blest_status bfs_run(blest_graph *h, int32_t source, int32_t *dev_out) {
     memset(&P, 0, sizeof P);
     P.n = (int)h->n;
     P.W = (int)((h->n + 31) / 32);
-    const void *kern = bfs_kernel_for(h->sigma, h->tau);
+    const void *kern = bfs_kernel_for(h->sigma, h->tau, h->block);
     if (!kern) return BLEST_ERR_INTERNAL;
     P.rowIds = h->g.rowIds;
     P.masks = h->g.masks;
@@ -1078,7 +1101,8 @@ extern "C" blest_status blest_bfs_noalloc(const blest_bvss_view *g, int32_t sour
     P.out = nullptr;
     if (cudaMemsetAsync(ctl, 0, sizeof(Ctl), s) != cudaSuccess) return BLEST_ERR_CUDA;
     void *args[] = {&P};
-    cudaError_t e = cudaLaunchCooperativeKernel(bfs_kernel_for(8, 128), dim3(grid), dim3(512), args, bfs_smem(512), s);
+    cudaError_t e =
+        cudaLaunchCooperativeKernel(bfs_kernel_for(8, 128, 512), dim3(grid), dim3(512), args, bfs_smem(512), s);
     if (e != cudaSuccess) {
         blest_internal_record_cuda_error(e, "cudaLaunchCooperativeKernel(k_bfs, no-alloc)", __FILE__, __LINE__);
         return BLEST_ERR_CUDA;
