@@ -319,28 +319,27 @@ __device__ void push_level(const BfsParams &P, Stage &st, int *grab, int ell, in
                     u[c] = r[b][c];
                     vw[c] = (c < THETA && (hits >> c & 1u)) ? P.Vc[u[c] >> 5] : 0xFFFFFFFFu;
                 }
-                // phase 2: claim the unvisited ones.  Lanes whose rows share a frontier
-                // word OR their bits together and one of them issues the atomic (rows
-                // of a VSS are often consecutive).  All of a lane's atomics and its
-                // degree and VSS-range loads are issued before any result is used, so
-                // they cost one round trip together.
-                unsigned old[4], ov[4];
-                int dg[4], a[4], len[4], sso[4], leader[4];
+                // phase 2: claim the unvisited ones, one atomic per candidate row (the
+                // lanes' atomics on a word are serialised by the memory system, so
+                // exactly one lane sees each bit and each slice-set field clear;
+                // combining them across the warp first costs more than it saves).
+                // All of a lane's atomics and its degree and VSS-range loads are
+                // issued before any result is used: one round trip together.
+                unsigned old[4];
+                int dg[4], a[4], len[4], sso[4];
                 unsigned cand = 0;
 #pragma unroll
                 for (int c = 0; c < THETA; ++c) {
                     const bool cd = !(vw[c] >> (u[c] & 31) & 1u);
-                    const int key = cd ? (u[c] >> 5) : -1;
-                    const unsigned peers = __match_any_sync(FULL_MASK, key);
-                    const unsigned bits = __reduce_or_sync(peers, cd ? (1u << (u[c] & 31)) : 0u);
-                    leader[c] = __ffs(peers) - 1;
-                    ov[c] = 0u;
-                    if (cd && lane == leader[c]) ov[c] = atomicOr(&Fn[key], bits);
-                    if (cd) cand |= 1u << c;
+                    old[c] = 0xFFFFFFFFu;
+                    if (cd) {
+                        old[c] = atomicOr(&Fn[u[c] >> 5], 1u << (u[c] & 31));
+                        cand |= 1u << c;
+                    }
                 }
 #pragma unroll
-                for (int c = 0; c < THETA; ++c) {
-                    sso[c] = u[c] >> LY::LOGS;
+                for (int c = 0; c < 4; ++c) {
+                    sso[c] = c < THETA ? (u[c] >> LY::LOGS) : 0;
                     dg[c] = 0;
                     a[c] = 0;
                     len[c] = 0;
@@ -350,56 +349,56 @@ __device__ void push_level(const BfsParams &P, Stage &st, int *grab, int ell, in
                         len[c] = __ldg(&P.realPtrs[sso[c] + 1]);
                     }
                 }
+                // phase 3: winners set their level and visited bits (one OR per word
+                // among the lane's own rows, which ascend); the first claim of a
+                // slice-set field enqueues its VSSs (once per set)
+                unsigned want = 0, wbits = 0;
+                int wword = -1;
 #pragma unroll
                 for (int c = 0; c < THETA; ++c) {
-                    const unsigned o = __shfl_sync(FULL_MASK, ov[c], leader[c]);
-                    old[c] = (cand >> c & 1u) ? o : 0xFFFFFFFFu;
-                }
-#pragma unroll
-                for (int c = THETA; c < 4; ++c) { a[c] = 0; len[c] = 0; sso[c] = 0; }
-                // phase 3: winners set their level; visited bits are OR-ed once per word;
-                // the first claim of a slice-set field enqueues its VSSs (once per set)
-                unsigned want = 0;
-#pragma unroll
-                for (int c = 0; c < THETA; ++c) {
-                    bool win = (cand >> c & 1u) && !(old[c] >> (u[c] & 31) & 1u);
-                    if constexpr (G > 1) {
-                        // VSSs of different slice sets in one pass can hold the same row at the
-                        // same slot position; both saw the bit clear in one aggregated atomic,
-                        // so the lowest such lane alone wins
-                        const unsigned dup = __match_any_sync(FULL_MASK, win ? u[c] : -1);
-                        if (win && lane != __ffs(dup) - 1) win = false;
-                    }
-                    const int key = win ? (u[c] >> 5) : -1;
-                    const unsigned peers = __match_any_sync(FULL_MASK, key);
-                    const unsigned bits = __reduce_or_sync(peers, win ? (1u << (u[c] & 31)) : 0u);
-                    if (win && lane == __ffs(peers) - 1) {
-                        red_or(&P.Vc[key], bits);
-                        red_or(&P.Vn[key], bits);
-                    }
-                    const int skey = win ? sso[c] : -1;
-                    const unsigned speers = __match_any_sync(FULL_MASK, skey);
+                    const bool win = (cand >> c & 1u) && !(old[c] >> (u[c] & 31) & 1u);
                     if (win) {
+                        const int wd = u[c] >> 5;
+                        if (wd != wword) {
+                            if (wword >= 0) {
+                                red_or(&P.Vc[wword], wbits);
+                                red_or(&P.Vn[wword], wbits);
+                            }
+                            wword = wd;
+                            wbits = 0;
+                        }
+                        wbits |= 1u << (u[c] & 31);
                         P.L[u[c]] = ell;
                         nv += 1;
                         fe += (unsigned long long)dg[c];
                         const int fo = u[c] & (31 & ~(SIGMA - 1));   // the set's field in the word
-                        if (lane == __ffs(speers) - 1 && ((old[c] >> fo) & LY::FMASK) == 0) want |= 1u << c;
+                        if (((old[c] >> fo) & LY::FMASK) == 0) want |= 1u << c;
                     }
                     len[c] -= a[c];
                 }
+                if (wword >= 0) {
+                    red_or(&P.Vc[wword], wbits);
+                    red_or(&P.Vn[wword], wbits);
+                }
                 enqueue_ranges(P, st, want, sso, a, len, P.Q[bn], P.SQ[bn], slot);
             } else {
-                // lazy marking: one fire-and-forget OR per distinct V_next word
+                // lazy marking: fire-and-forget ORs into V_next, one per distinct word
+                // among the lane's own rows (they ascend, so equal words are adjacent)
+                unsigned mbits = 0;
+                int mword = -1;
 #pragma unroll
                 for (int c = 0; c < THETA; ++c) {
-                    const bool hit = hits >> c & 1u;
-                    const int u = r[b][c];
-                    const int key = hit ? (u >> 5) : -1;
-                    const unsigned peers = __match_any_sync(FULL_MASK, key);
-                    const unsigned bits = __reduce_or_sync(peers, hit ? (1u << (u & 31)) : 0u);
-                    if (hit && lane == __ffs(peers) - 1) red_or(&P.Vn[key], bits);
+                    if (hits >> c & 1u) {
+                        const int u = r[b][c];
+                        if ((u >> 5) != mword) {
+                            if (mword >= 0) red_or(&P.Vn[mword], mbits);
+                            mword = u >> 5;
+                            mbits = 0;
+                        }
+                        mbits |= 1u << (u & 31);
+                    }
                 }
+                if (mword >= 0) red_or(&P.Vn[mword], mbits);
             }
         }
     }
@@ -592,26 +591,54 @@ __device__ void finalize_level(const BfsParams &P, Stage &st, int *grab, int ell
                 rl[c] = __ldg(&P.realPtrs[sso[c] + 1]);
             }
         }
-        const unsigned changed = __ballot_sync(FULL_MASK, diff != 0);
-        if (changed) {
-            // lane = vertex over the changed words, eight words per round; the
-            // rounds keep separate sums so all their degree loads can be in flight
-            unsigned long long d8[4] = {0, 0, 0, 0};
+        // out-degrees of the word's new vertices: lane = word, one 16-byte load
+        // per group of four vertices holding a new one, all in flight together
+        if (diff) {
+            const int4 *dq = reinterpret_cast<const int4 *>(P.deg) + (size_t)t * 8;
+            unsigned long long dsum = 0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const unsigned nib = (diff >> (4 * q)) & 0xFu;
+                if (nib) {
+                    const int v0 = t * 32 + 4 * q;
+                    int4 d;
+                    if (v0 + 4 <= P.n) {
+                        d = __ldg(dq + q);
+                    } else {   // the last, partial word: no load past vertex n - 1
+                        d.x = __ldg(&P.deg[v0]);
+                        d.y = v0 + 1 < P.n ? __ldg(&P.deg[v0 + 1]) : 0;
+                        d.z = v0 + 2 < P.n ? __ldg(&P.deg[v0 + 2]) : 0;
+                        d.w = v0 + 3 < P.n ? __ldg(&P.deg[v0 + 3]) : 0;
+                    }
+                    dsum += (unsigned long long)((nib & 1u ? d.x : 0) + (nib & 2u ? d.y : 0) +
+                                                 (nib & 4u ? d.z : 0) + (nib & 8u ? d.w : 0));
+                }
+            }
+            fe += dsum;
+        }
+        // level stores: a word with few new vertices is stored by its own lane;
+        // dense words go lane = vertex, eight words per round, so stores coalesce
+        const int pc = __popc(diff);
+        if (pc > 0 && pc <= 4) {
+            unsigned d = diff;
+            while (d) {
+                const int bit = __ffs(d) - 1;
+                d &= d - 1u;
+                P.L[t * 32 + bit] = ell;
+            }
+        }
+        const unsigned dense = __ballot_sync(FULL_MASK, pc > 4);
+        if (dense) {
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
-                if (!((changed >> (8 * r)) & 0xFFu)) continue;   // warp-uniform
+                if (!((dense >> (8 * r)) & 0xFFu)) continue;   // warp-uniform
 #pragma unroll
                 for (int k = 0; k < 8; ++k) {
                     const int j = 8 * r + k;
                     const unsigned dj = __shfl_sync(FULL_MASK, diff, j);
-                    if (dj >> lane & 1u) {
-                        const int u = ((base + j) << 5) + lane;
-                        P.L[u] = ell;
-                        d8[r] += (unsigned long long)__ldg(&P.deg[u]);
-                    }
+                    if ((dense >> j & 1u) && (dj >> lane & 1u)) P.L[((base + j) << 5) + lane] = ell;
                 }
             }
-            fe += d8[0] + d8[1] + d8[2] + d8[3];
         }
 #pragma unroll
         for (int c = 0; c < 4; ++c) rl[c] -= ra[c];
