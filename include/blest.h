@@ -141,7 +141,7 @@ void blest_default_opts(blest_build_opts *opts);
  * CSR or a sigma / tau pair other than (8, 32), (8, 128), (16, 64),
  * (32, 32); UNSUPPORTED for n >= 2^31, for engine_tc = 1 with a layout other
  * than sigma = 8, tau = 128 (the Fig. 3 fragment layout), or when the BVSS
- * would need 2^31 or more row-id slots. */
+ * would need 2^31 or more lane words (N_v * tau / theta). */
 blest_status blest_build(int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
                          const blest_build_opts *opts, blest_handle *out);
 

@@ -413,7 +413,7 @@ blest_status build_graph(blest_graph *h, const int64_t *row_ptr, const int32_t *
     long long Nv = 0;
     BUILD_TRY(cudaMemcpyAsync(&Nv, nv + Ns, sizeof(long long), cudaMemcpyDeviceToHost, st));
     BUILD_TRY(cudaStreamSynchronize(st));
-    if (Nv * tau >= ((long long)1 << 31)) return BLEST_ERR_UNSUPPORTED;
+    if (Nv * lanes >= ((long long)1 << 31)) return BLEST_ERR_UNSUPPORTED;   // lane words (64-bit slot indexing)
     h->Ns = Ns;
     h->Nv = Nv;
     if ((bs = dev_alloc_t(h, &h->g.realPtrs, (size_t)Ns + 1)) != BLEST_OK) return bs;

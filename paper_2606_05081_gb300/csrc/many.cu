@@ -158,33 +158,11 @@ __global__ void __launch_bounds__(MANY_BLOCK) k_many(ManyParams P) {
                 int qb = 0;
                 if (lane == 31 && incl) qb = atomicAdd(&s_qlen[cur ^ 1], incl);
                 qb = __shfl_sync(FULL_MASK, qb, 31) + incl - tot;
-                // short ranges by their own lane, long ones (hub slice sets) by the whole warp
-                int pos[4];
-                unsigned big = 0;
+                // each lane appends its own ranges: hub slice sets of graphs this
+                // small span few VSSs, and a warp-wide pass measured slower here
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    pos[c] = qb;
-                    if (want_len[c] <= 8) {
-                        for (int k = 0; k < want_len[c]; ++k) Qn[qb + k] = want_a[c] + k;
-                    } else {
-                        big |= 1u << c;
-                    }
-                    qb += want_len[c];
-                }
-                unsigned bl = __ballot_sync(FULL_MASK, big != 0);
-                while (bl) {
-                    const int j = __ffs(bl) - 1;
-                    bl &= bl - 1u;
-                    const unsigned bj = __shfl_sync(FULL_MASK, big, j);
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        const int aj = __shfl_sync(FULL_MASK, want_a[c], j);
-                        const int lj = __shfl_sync(FULL_MASK, want_len[c], j);
-                        const int pj = __shfl_sync(FULL_MASK, pos[c], j);
-                        if (bj >> c & 1u)
-                            for (int k = lane; k < lj; k += 32) Qn[pj + k] = aj + k;
-                    }
-                }
+                for (int c = 0; c < 4; ++c)
+                    for (int k = 0; k < want_len[c]; ++k) Qn[qb++] = want_a[c] + k;
             }
             __syncthreads();
             // the current frontier becomes the next level's (cleared) target

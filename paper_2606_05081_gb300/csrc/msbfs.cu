@@ -80,8 +80,45 @@ __device__ __forceinline__ bool ms_barrier(MsCtl *ctl, unsigned &epoch, unsigned
 
 __device__ __forceinline__ int get_vi(int u, int rho) { return (u & 7) * rho + (u >> 3); }
 
-// warp-aggregated append of one slice set per lane (VSS range -> Q)
-__device__ __forceinline__ void ms_enqueue(const MsParams &P, bool want, int ss, int *Q, int slot) {
+// Appends to the VSS queue and the dirty-set list are staged per warp in
+// shared memory and reserved in the global arrays once per MS_STG entries
+// (one atomic per warp and slice set on the same counter serialises in one
+// L2 slice when a level touches hundreds of thousands of sets).
+constexpr int MS_STG = 256;
+
+struct MsStage {
+    int *q, *d;   // staging areas of this warp: VSS ids, dirty slice-set ids
+    int qn, dn;   // staged counts (warp-uniform)
+};
+
+__device__ __forceinline__ void ms_flush_q(const MsParams &P, MsStage &st, int *Q, int slot) {
+    const int lane = lane_id();
+    __syncwarp();
+    if (st.qn) {
+        int base = 0;
+        if (lane == 0) base = atomicAdd(&P.ctl->qlen[slot], st.qn);
+        base = __shfl_sync(FULL_MASK, base, 0);
+        for (int k = lane; k < st.qn; k += 32) Q[base + k] = st.q[k];
+    }
+    __syncwarp();
+    st.qn = 0;
+}
+
+__device__ __forceinline__ void ms_flush_d(const MsParams &P, MsStage &st, int dl) {
+    const int lane = lane_id();
+    __syncwarp();
+    if (st.dn) {
+        int base = 0;
+        if (lane == 0) base = atomicAdd(&P.ctl->dlen[dl], st.dn);
+        base = __shfl_sync(FULL_MASK, base, 0);
+        for (int k = lane; k < st.dn; k += 32) P.dlist[dl][base + k] = st.d[k];
+    }
+    __syncwarp();
+    st.dn = 0;
+}
+
+// warp-aggregated append of one slice set per lane (its VSS range -> Q)
+__device__ __forceinline__ void ms_enqueue(const MsParams &P, MsStage &st, bool want, int ss, int *Q, int slot) {
     const int lane = lane_id();
     if (!__any_sync(FULL_MASK, want)) return;
     int a = 0, len = 0;
@@ -90,13 +127,24 @@ __device__ __forceinline__ void ms_enqueue(const MsParams &P, bool want, int ss,
         len = __ldg(&P.realPtrs[ss + 1]) - a;
     }
     const int incl = warp_incl_scan(len);
-    int base = 0;
-    if (lane == 31 && incl) base = atomicAdd(&P.ctl->qlen[slot], incl);
-    base = __shfl_sync(FULL_MASK, base, 31) + incl - len;
+    const int T = __shfl_sync(FULL_MASK, incl, 31);
+    if (T <= MS_STG && st.qn + T > MS_STG) ms_flush_q(P, st, Q, slot);
+    int *dst;
+    int base;
+    if (T > MS_STG) {      // larger than the staging area: reserve it directly
+        int g = 0;
+        if (lane == 31) g = atomicAdd(&P.ctl->qlen[slot], T);
+        dst = Q + __shfl_sync(FULL_MASK, g, 31);
+        base = incl - len;
+    } else {
+        dst = st.q;
+        base = st.qn + incl - len;
+        st.qn += T;
+    }
     // short ranges by their own lane, long ones (hub slice sets) by the whole warp
     const bool big = len > 8;
     if (!big)
-        for (int i = 0; i < len; ++i) Q[base + i] = a + i;
+        for (int i = 0; i < len; ++i) dst[base + i] = a + i;
     unsigned lanes = __ballot_sync(FULL_MASK, big);
     while (lanes) {
         const int j = __ffs(lanes) - 1;
@@ -104,21 +152,38 @@ __device__ __forceinline__ void ms_enqueue(const MsParams &P, bool want, int ss,
         const int aj = __shfl_sync(FULL_MASK, a, j);
         const int lj = __shfl_sync(FULL_MASK, len, j);
         const int bj = __shfl_sync(FULL_MASK, base, j);
-        for (int i = lane; i < lj; i += 32) Q[bj + i] = aj + i;
+        for (int i = lane; i < lj; i += 32) dst[bj + i] = aj + i;
     }
+    __syncwarp();
+}
+
+// warp-aggregated append of the dirty slice sets the lanes claimed
+__device__ __forceinline__ void ms_mark_dirty(const MsParams &P, MsStage &st, bool claimed, int so, int dl) {
+    const unsigned m = __ballot_sync(FULL_MASK, claimed);
+    if (!m) return;
+    const int cnt = __popc(m);
+    if (st.dn + cnt > MS_STG) ms_flush_d(P, st, dl);
+    if (claimed) st.d[st.dn + __popc(m & ((1u << lane_id()) - 1u))] = so;
+    st.dn += cnt;
+    __syncwarp();
 }
 
 template <int KW>
-__device__ void ms_stage1(const MsParams &P, int qlen, const int *Qc, int dl, int *s_rows, unsigned char *s_m) {
+__device__ void ms_stage1(const MsParams &P, MsStage &st, int *grab, int qlen, const int *Qc, int dl, int *s_rows,
+                          unsigned char *s_m) {
     constexpr int G = 32 / KW;
     const int lane = lane_id();
     const int g = lane / KW, w = lane % KW;
     const int wib = threadIdx.x >> 5;
     int *rows = s_rows + wib * 128;
     unsigned char *m8s = s_m + wib * 128;
-    const int gwarp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
-    for (int it = gwarp; it < qlen; it += nwarps) {
+    // queue entries interleaved over the blocks, claimed by the block's warps
+    for (;;) {
+        int kc = 0;
+        if (lane == 0) kc = atomicAdd(grab, 1);
+        kc = __shfl_sync(FULL_MASK, kc, 0);
+        const int it = (int)blockIdx.x + kc * (int)gridDim.x;
+        if (it >= qlen) break;
         const int vss = Qc[it];
         const int ss = __ldg(&P.v2r[vss]);
         const bool own = lane < P.lpv;
@@ -152,25 +217,31 @@ __device__ void ms_stage1(const MsParams &P, int qlen, const int *Qc, int dl, in
             const int u = rows[kk];
             if (hit) red_or(&P.Vn[(size_t)get_vi(u, P.rho) * KW + w], hit);
             const unsigned bal = __ballot_sync(FULL_MASK, hit != 0);
-            if (w == 0 && ((bal >> (g * KW)) & (KW == 32 ? 0xFFFFFFFFu : ((1u << KW) - 1u)))) {
-                const int so = u >> 3;
-                if (ld_volatile_i32(&P.dirty[so]) == 0 && atomicExch(&P.dirty[so], 1) == 0)
-                    P.dlist[dl][atomicAdd(&P.ctl->dlen[dl], 1)] = so;
-            }
+            bool claimed = false;
+            const int so = u >> 3;
+            if (w == 0 && ((bal >> (g * KW)) & (KW == 32 ? 0xFFFFFFFFu : ((1u << KW) - 1u))))
+                claimed = ld_volatile_i32(&P.dirty[so]) == 0 && atomicExch(&P.dirty[so], 1) == 0;
+            ms_mark_dirty(P, st, claimed, so, dl);
         }
     }
+    ms_flush_d(P, st, dl);
 }
 
 template <int KW>
-__device__ void ms_stage2(const MsParams &P, int ell, int dl, int qn, int dcount) {
+__device__ void ms_stage2(const MsParams &P, MsStage &st, int *grab, int ell, int dl, int qn, int dcount) {
     constexpr int G = 32 / KW;
     const int lane = lane_id();
     const int g = lane / KW, w = lane % KW;
-    const int gwarp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
     const int *dlist = P.dlist[dl];
-    for (int base = gwarp * G; base < dcount; base += nwarps * G) {
-        const int i = base + g;
+    const int nchunk = (dcount + G - 1) / G;
+    // chunks of G dirty sets interleaved over the blocks, claimed by the block's warps
+    for (;;) {
+        int kc = 0;
+        if (lane == 0) kc = atomicAdd(grab, 1);
+        kc = __shfl_sync(FULL_MASK, kc, 0);
+        const int chunk = (int)blockIdx.x + kc * (int)gridDim.x;
+        if (chunk >= nchunk) break;
+        const int i = chunk * G + g;
         const bool valid = i < dcount;
         const int ss = valid ? dlist[i] : 0;
         unsigned A = 0;
@@ -215,14 +286,23 @@ __device__ void ms_stage2(const MsParams &P, int ell, int dl, int qn, int dcount
         const unsigned bal = __ballot_sync(FULL_MASK, A != 0);
         const bool any = ((bal >> (g * KW)) & (KW == 32 ? 0xFFFFFFFFu : ((1u << KW) - 1u))) != 0;
         if (valid && w == 0) P.dirty[ss] = 0;
-        ms_enqueue(P, valid && w == 0 && any, ss, P.Q[qn], qn);
+        ms_enqueue(P, st, valid && w == 0 && any, ss, P.Q[qn], qn);
     }
+    ms_flush_q(P, st, P.Q[qn], qn);
 }
 
+// two 512-thread CTAs per SM (64 registers a thread)
 template <int KW>
-__global__ void __launch_bounds__(MS_BLOCK, 1) k_msbfs(MsParams P) {
+__global__ void __launch_bounds__(MS_BLOCK, 2) k_msbfs(MsParams P) {
     __shared__ int s_rows[(MS_BLOCK / 32) * 128];
     __shared__ unsigned char s_m[(MS_BLOCK / 32) * 128];
+    __shared__ int s_stg[(MS_BLOCK / 32) * 2 * MS_STG];
+    __shared__ int s_grab[2];
+    MsStage st;
+    st.q = s_stg + (threadIdx.x >> 5) * 2 * MS_STG;
+    st.d = st.q + MS_STG;
+    st.qn = 0;
+    st.dn = 0;
     const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const size_t nthreads = (size_t)gridDim.x * blockDim.x;
     MsCtl *ctl = P.ctl;
@@ -268,8 +348,9 @@ __global__ void __launch_bounds__(MS_BLOCK, 1) k_msbfs(MsParams P) {
             const bool ok = i < cnt;
             const int ss = ok ? P.dlist[1][i] : 0;
             if (ok) P.dirty[ss] = 0;
-            ms_enqueue(P, ok, ss, P.Q[0], 0);
+            ms_enqueue(P, st, ok, ss, P.Q[0], 0);
         }
+        ms_flush_q(P, st, P.Q[0], 0);
     }
     if (!ms_barrier(ctl, epoch, P.budget_ns)) return;
     if (tid == 0) ctl->dlen[1] = 0;
@@ -280,20 +361,24 @@ __global__ void __launch_bounds__(MS_BLOCK, 1) k_msbfs(MsParams P) {
     for (;; ++ell) {
         const int qc = (ell - 1) & 1, qn = ell & 1, dl = ell & 1;
         // one thread per block reads the shared counter (see k_bfs)
-        if (threadIdx.x == 0) s_cnt = ld_volatile_i32(&ctl->qlen[qc]);
+        if (threadIdx.x == 0) {
+            s_cnt = ld_volatile_i32(&ctl->qlen[qc]);
+            s_grab[0] = 0;
+            s_grab[1] = 0;
+        }
         __syncthreads();
         const int qlen = s_cnt;
         __syncthreads();
         if (qlen == 0) break;
         if (tid == 0) ctl->qlen[qn] = 0;
-        ms_stage1<KW>(P, qlen, P.Q[qc], dl, s_rows, s_m);
+        ms_stage1<KW>(P, st, &s_grab[0], qlen, P.Q[qc], dl, s_rows, s_m);
         if (!ms_barrier(ctl, epoch, P.budget_ns)) return;
         if (threadIdx.x == 0) s_cnt = ld_volatile_i32(&ctl->dlen[dl]);
         __syncthreads();
         const int dcount = s_cnt;
         __syncthreads();
         if (tid == 0) ctl->dlen[dl ^ 1] = 0;
-        ms_stage2<KW>(P, ell, dl, qn, dcount);
+        ms_stage2<KW>(P, st, &s_grab[1], ell, dl, qn, dcount);
         if (!ms_barrier(ctl, epoch, P.budget_ns)) return;
     }
     if (tid == 0) ctl->nlevels = ell - 1;
