@@ -113,6 +113,7 @@ typedef struct blest_info {
     double build_ms;         /* device time of the build */
     int64_t device_bytes;    /* device memory held by the handle */
     int32_t tau;             /* slices per VSS */
+    int32_t vss_batch;       /* VSS passes a warp keeps in flight (launch setting) */
 } blest_info;
 
 /* One record per BFS level of the last single-source BFS. */
@@ -130,6 +131,7 @@ typedef struct blest_level_log {
                                 learned policy) */
     int64_t t_stage1_ns;     /* device time of stage 1 alone (lazy and bottom-up levels; equals t_ns
                                 for eager levels) */
+    int64_t vss_batch;       /* VSS passes a warp kept in flight (top-down levels) */
 } blest_level_log;
 
 /* Fill *opts with the defaults documented above. */
@@ -160,7 +162,11 @@ blest_status blest_msbfs(blest_handle h, const int32_t *sources, int32_t k, int3
  * far: n int64 distance sums (Eq. 6); cc: n doubles, cc[u] = (reach[u]-1) /
  * far[u] (Eq. 7 with component-size normalisation; 0 when far[u] = 0), may be
  * NULL; reach: n int64 component sizes, may be NULL.  Undirected graphs only
- * (UNSUPPORTED otherwise). */
+ * (UNSUPPORTED otherwise).  Each batch is one replay of a CUDA graph (source
+ * ids from a device cursor, the persistent multi-source kernel, the cursor
+ * advance) captured on the handle's stream at the first call, so that stream
+ * must allow capture (the handle's own stream does; cudaStreamLegacy does
+ * not). */
 blest_status blest_closeness(blest_handle h, int64_t *far, double *cc, int64_t *reach);
 
 /* Partial closeness: distance sums from the sources with original ids
@@ -240,20 +246,25 @@ void blest_destroy(blest_handle h);
 const char *blest_status_string(blest_status s);
 
 /* ---- Learned level-mode policy (replaces the hand-set rule of §5.3 / §7.1)
- * A 3-layer MLP (6 -> 32 -> 32 -> 5, tanh, fp32) predicts the log device
- * time of each BLEST_MODE_* from six per-level features; BLEST_POLICY_LEARNED
- * runs the mode with the smallest prediction.  Weights: BLEST_MLP_NW floats,
- * [0,6) feature means, [6,12) feature 1/std, then W1[32][6], b1[32],
- * W2[32][32], b2[32], W3[5][32], b3[5].  All arrays below may be host or
- * device memory and are row-major (one sample per row). */
-#define BLEST_MLP_NW 1457
+ * A 3-layer MLP (6 -> 32 -> 32 -> 9, tanh, fp32) predicts, from six
+ * per-level features, the log device time of each of BLEST_NUM_CHOICES
+ * level choices; BLEST_POLICY_LEARNED runs the choice with the smallest
+ * prediction.  A choice is a mode and the VSS passes a warp keeps in flight:
+ * choices 0-4 are the modes BLEST_MODE_* (lazy ones with one pass), 5 and 6
+ * lazy CUDA-core with 2 and 4 passes, 7 and 8 lazy b1-MMA with 2 and 4.
+ * Weights: BLEST_MLP_NW floats, [0,6) feature means, [6,12) feature 1/std,
+ * then W1[32][6], b1[32], W2[32][32], b2[32], W3[9][32], b3[9].  All arrays
+ * below may be host or device memory and are row-major (one sample per
+ * row). */
+#define BLEST_NUM_CHOICES 9
+#define BLEST_MLP_NW 1589
 
 /* Raw features of level-log records, exactly as the BFS kernel computes
  * them: out[n*6] = log1p of (frontier, frontier_edges, unvisited, slots,
  * level, avg_deg). */
 blest_status blest_mlp_features(const blest_level_log *recs, int64_t n, float avg_deg, float *out);
 
-/* Masked mean squared error of the predictions against targets (n*5 log
+/* Masked mean squared error of the predictions against targets (n*9 log
  * times, mask 1 = observed) and its gradient (BLEST_MLP_NW floats; the
  * normalisation entries get 0). */
 blest_status blest_mlp_loss_grad(const float *features, const float *targets, const float *mask, int64_t n,
@@ -267,7 +278,7 @@ blest_status blest_mlp_loss_grad(const float *features, const float *targets, co
 blest_status blest_mlp_train(const float *features, const float *targets, const float *mask, int64_t n,
                              int32_t epochs, float lr, float weight_decay, float *weights, float *loss_out);
 
-/* Predictions (n*5, may be NULL) and chosen modes (n, may be NULL) with the
+/* Predictions (n*9, may be NULL) and chosen choices (n, may be NULL) with the
  * in-kernel inference routine. */
 blest_status blest_mlp_predict(const float *weights, const float *features, int64_t n, float *pred,
                                int32_t *choice);

@@ -4,10 +4,12 @@ INFRASTRUCTURE ONLY.
 The paper chooses the level mode with a hand-set rule (§5.3 Eq. 5 with
 eta = 10, calibrated for Hopper, §7.1); the learned policy replaces it with a
 3-layer perceptron that predicts, from six per-level features, the log
-device time of each of the five level modes, and picks the smallest.
+device time of each of nine level choices (the five level modes, lazy ones
+with one VSS pass in flight, plus lazy CUDA-core and b1-MMA levels with two
+and four passes), and picks the smallest.
 
 Network (same layout as the device weights): x = (raw - mean) * istd;
-h1 = tanh(W1 x + b1) (32); h2 = tanh(W2 h1 + b2) (32); y = W3 h2 + b3 (5).
+h1 = tanh(W1 x + b1) (32); h2 = tanh(W2 h1 + b2) (32); y = W3 h2 + b3 (9).
 Loss: mean over the observed (sample, mode) pairs of (y - log t)^2.
 Optimiser: Adam (Kingma & Ba, 2015) with bias correction.
 """
@@ -15,7 +17,7 @@ from __future__ import annotations
 
 import numpy as np
 
-IN, H, OUT = 6, 32, 5
+IN, H, OUT = 6, 32, 9
 OFF_MEAN, OFF_ISTD = 0, 6
 OFF_W1 = 12
 OFF_B1 = OFF_W1 + H * IN

@@ -29,7 +29,22 @@ REORDER_NONE, REORDER_RCM, REORDER_JACCARD, REORDER_AUTO = range(4)
 MODE_PUSH_EAGER_CC, MODE_PUSH_EAGER_TC, MODE_PUSH_LAZY_CC, MODE_PUSH_LAZY_TC, MODE_BOTTOM_UP = range(5)
 MODE_NAMES = ["push_eager_cc", "push_eager_tc", "push_lazy_cc", "push_lazy_tc", "bottom_up"]
 POLICY_HEURISTIC, POLICY_LEARNED, POLICY_FIXED, POLICY_SCHEDULE = range(4)
-MLP_NW = 12 + 32 * 6 + 32 + 32 * 32 + 32 + 5 * 32 + 5
+NUM_CHOICES = 9   # learned-policy choices: modes 0-4 (lazy: 1 pass), 5/6 lazy CC 2/4 passes, 7/8 lazy TC 2/4
+MLP_NW = 12 + 32 * 6 + 32 + 32 * 32 + 32 + NUM_CHOICES * 32 + NUM_CHOICES
+
+
+def choice_mode_batch(c: int):
+    """(mode, VSS passes in flight) of a learned-policy choice."""
+    if c < 5:
+        return c, 1
+    return (2 if c < 7 else 3), (2 if (c - 5) % 2 == 0 else 4)
+
+
+def choice_of(mode: int, batch: int) -> int:
+    """The learned-policy choice of a mode run with `batch` passes in flight."""
+    if mode in (MODE_PUSH_LAZY_CC, MODE_PUSH_LAZY_TC) and batch in (2, 4):
+        return (5 if mode == MODE_PUSH_LAZY_CC else 7) + (0 if batch == 2 else 1)
+    return mode
 
 
 class BuildOpts(ctypes.Structure):
@@ -46,14 +61,16 @@ class Info(ctypes.Structure):
                 ("update_divergence", ctypes.c_double), ("lazy", ctypes.c_int32),
                 ("switching", ctypes.c_int32), ("reorder", ctypes.c_int32), ("sigma", ctypes.c_int32),
                 ("grid_blocks", ctypes.c_int32), ("block_threads", ctypes.c_int32),
-                ("build_ms", ctypes.c_double), ("device_bytes", ctypes.c_int64), ("tau", ctypes.c_int32)]
+                ("build_ms", ctypes.c_double), ("device_bytes", ctypes.c_int64), ("tau", ctypes.c_int32),
+                ("vss_batch", ctypes.c_int32)]
 
 
 class LevelLog(ctypes.Structure):
     _fields_ = [("level", ctypes.c_int32), ("mode", ctypes.c_int32), ("frontier", ctypes.c_int64),
                 ("frontier_edges", ctypes.c_int64), ("unvisited", ctypes.c_int64), ("queue", ctypes.c_int64),
                 ("t_ns", ctypes.c_int64), ("scanned_vertices", ctypes.c_int64),
-                ("scanned_arcs", ctypes.c_int64), ("slots", ctypes.c_int64), ("t_stage1_ns", ctypes.c_int64)]
+                ("scanned_arcs", ctypes.c_int64), ("slots", ctypes.c_int64), ("t_stage1_ns", ctypes.c_int64),
+                ("vss_batch", ctypes.c_int64)]
 
 
 class BvssView(ctypes.Structure):
@@ -339,6 +356,7 @@ def mlp_features(records, avg_deg: float) -> np.ndarray:
 
 
 def mlp_loss_grad(features, targets, mask, weights):
+    _mlp_shapes(weights, features, targets, mask)
     X, T, M, W = _f32(features), _f32(targets), _f32(mask), _f32(weights)
     loss = ctypes.c_float(0)
     g = np.empty(MLP_NW, np.float32)
@@ -348,6 +366,7 @@ def mlp_loss_grad(features, targets, mask, weights):
 
 
 def mlp_train(features, targets, mask, weights, epochs: int = 2000, lr: float = 1e-2, weight_decay: float = 0.0):
+    _mlp_shapes(weights, features, targets, mask)
     X, T, M = _f32(features), _f32(targets), _f32(mask)
     W = _f32(weights).copy()
     hist = np.empty(epochs, np.float32)
@@ -356,9 +375,22 @@ def mlp_train(features, targets, mask, weights, epochs: int = 2000, lr: float = 
     return W, hist
 
 
+def _mlp_shapes(weights, features, targets=None, mask=None):
+    """The C entry points cannot see buffer sizes: check them here."""
+    if np.asarray(weights).size != MLP_NW:
+        raise ValueError(f"weights: {MLP_NW} values expected")
+    if np.asarray(features).ndim != 2 or np.asarray(features).shape[1] != 6:
+        raise ValueError("features: shape (n, 6) expected")
+    n = np.asarray(features).shape[0]
+    for nm, a in (("targets", targets), ("mask", mask)):
+        if a is not None and np.asarray(a).shape != (n, NUM_CHOICES):
+            raise ValueError(f"{nm}: shape ({n}, {NUM_CHOICES}) expected")
+
+
 def mlp_predict(weights, features):
+    _mlp_shapes(weights, features)
     W, X = _f32(weights), _f32(features)
-    pred = np.empty((len(X), 5), np.float32)
+    pred = np.empty((len(X), NUM_CHOICES), np.float32)
     ch = np.empty(len(X), np.int32)
     _check(_lib.blest_mlp_predict(W.ctypes.data, X.ctypes.data, len(X), pred.ctypes.data, ch.ctypes.data),
            "blest_mlp_predict")

@@ -243,14 +243,54 @@ __device__ __forceinline__ void enqueue_ranges(const BfsParams &P, Stage &st, un
     __syncwarp();
 }
 
-__device__ __forceinline__ void flush_counts(const BfsParams &P, int slot, unsigned long long nv,
-                                             unsigned long long fe) {
+// Per-CTA totals of a level's appends and counters (shared memory, zeroed at
+// the level start): the level's last flush reserves queue space and adds
+// the counters once per CTA instead of once per warp, so the control block
+// sees a few hundred atomics per level rather than thousands.
+struct BlkAcc {
+    int q, s;                       // staged queue entries / slice-set ids of the CTA
+    int qbase, sbase;               // the CTA's reserved offsets
+    unsigned long long nv, fe;      // newly visited vertices and their out-arcs
+    unsigned long long sv, sa;      // bottom-up: probed vertices and extra arcs read
+};
+
+// Called by every thread of the CTA at the end of a level's last phase.
+__device__ __forceinline__ void block_flush(const BfsParams &P, Stage &st, BlkAcc *acc, int2 *Q, int *SQ, int slot,
+                                            unsigned long long nv, unsigned long long fe) {
+    const int lane = lane_id();
     nv = warp_sum(nv);
     fe = warp_sum(fe);
-    if (lane_id() == 0 && nv) {
-        red_add_u64(&P.ctl->newv[slot], nv);
-        red_add_u64(&P.ctl->fedges[slot], fe);
+    int wq = 0, ws = 0;
+    if (lane == 0) {
+        if (st.qn) wq = atomicAdd(&acc->q, st.qn);
+        if (st.sqn) ws = atomicAdd(&acc->s, st.sqn);
+        if (nv) {
+            atomicAdd(&acc->nv, nv);
+            atomicAdd(&acc->fe, fe);
+        }
     }
+    wq = __shfl_sync(FULL_MASK, wq, 0);
+    ws = __shfl_sync(FULL_MASK, ws, 0);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        acc->qbase = acc->q ? atomicAdd(&P.ctl->qlen[slot], acc->q) : 0;
+        acc->sbase = acc->s ? atomicAdd(&P.ctl->sqlen[slot], acc->s) : 0;
+        if (acc->nv) {
+            red_add_u64(&P.ctl->newv[slot], acc->nv);
+            red_add_u64(&P.ctl->fedges[slot], acc->fe);
+        }
+        if (acc->sv) {
+            red_add_u64(&P.ctl->scan_v[slot], acc->sv);
+            red_add_u64(&P.ctl->scan_a[slot], acc->sa);
+        }
+    }
+    __syncthreads();
+    const int qb = acc->qbase + wq, sb = acc->sbase + ws;
+    for (int k = lane; k < st.qn; k += 32) Q[qb + k] = st.q[k];
+    for (int k = lane; k < st.sqn; k += 32) SQ[sb + k] = st.sq[k];
+    __syncwarp();
+    st.qn = 0;
+    st.sqn = 0;
 }
 
 // ---------------------------------------------------------------- push
@@ -260,8 +300,8 @@ __device__ __forceinline__ void flush_counts(const BfsParams &P, int slot, unsig
 // then their frontier fields, before using any of them, so the
 // dependent-load chain is paid once per B*G VSSs.
 template <bool EAGER, bool TC, int B, int SIGMA, int LPV>
-__device__ void push_level(const BfsParams &P, Stage &st, int *grab, int ell, int bc, int bn, int slot, int qlen,
-                           unsigned bsel) {
+__device__ void push_level(const BfsParams &P, Stage &st, int *grab, BlkAcc *acc, int ell, int bc, int bn, int slot,
+                           int qlen, unsigned bsel) {
     using LY = Lay<SIGMA, LPV>;
     constexpr int THETA = LY::THETA, G = LY::G;
     const int lane = lane_id();
@@ -403,8 +443,7 @@ __device__ void push_level(const BfsParams &P, Stage &st, int *grab, int ell, in
         }
     }
     if (EAGER) {
-        stage_flush(P, st, P.Q[bn], P.SQ[bn], slot);
-        flush_counts(P, slot, nv, fe);
+        block_flush(P, st, acc, P.Q[bn], P.SQ[bn], slot, nv, fe);
     }
 }
 
@@ -428,7 +467,7 @@ __device__ __forceinline__ int nth_set_bit(unsigned x, int k) {
     return pos;
 }
 
-__device__ void bottom_up_level(const BfsParams &P, int *grab, int bc, int slot, unsigned *s_found) {
+__device__ void bottom_up_level(const BfsParams &P, int *grab, BlkAcc *acc, int bc, int slot, unsigned *s_found) {
     const int lane = lane_id();
     unsigned *found = s_found + (threadIdx.x >> 5) * 32;
     const unsigned *Fc = P.F[bc];
@@ -527,11 +566,12 @@ __device__ void bottom_up_level(const BfsParams &P, int *grab, int bc, int slot,
         if (f) P.Vn[w] = vis | f;   // this warp owns word w in this phase
         __syncwarp();
     }
+    // counted per CTA; the stage-2 flush of this level adds them to the control block
     sv = warp_sum(sv);
     sa = warp_sum(sa);
     if (lane == 0 && sv) {
-        red_add_u64(&P.ctl->scan_v[slot], sv);
-        red_add_u64(&P.ctl->scan_a[slot], sa);
+        atomicAdd(&acc->sv, sv);
+        atomicAdd(&acc->sa, sa);
     }
 }
 
@@ -541,7 +581,7 @@ __device__ void bottom_up_level(const BfsParams &P, int *grab, int bc, int slot,
 // for the level stores and degree loads, so both are coalesced.  A word
 // holds theta = 32/SIGMA slice-set fields; a changed field enqueues its set.
 template <int SIGMA>
-__device__ void finalize_level(const BfsParams &P, Stage &st, int *grab, int ell, int bn, int slot) {
+__device__ void finalize_level(const BfsParams &P, Stage &st, int *grab, BlkAcc *acc, int ell, int bn, int slot) {
     constexpr int THETA = 32 / SIGMA;
     constexpr unsigned FMASK = SIGMA == 32 ? 0xFFFFFFFFu : ((1u << SIGMA) - 1u);
     const int lane = lane_id();
@@ -645,23 +685,28 @@ __device__ void finalize_level(const BfsParams &P, Stage &st, int *grab, int ell
         enqueue_ranges(P, st, want, sso, ra, rl, P.Q[bn], P.SQ[bn], slot);
       }
     }
-    stage_flush(P, st, P.Q[bn], P.SQ[bn], slot);
-    flush_counts(P, slot, nv, fe);
+    block_flush(P, st, acc, P.Q[bn], P.SQ[bn], slot, nv, fe);
 }
 
 // -------------------------------------------------------- mode decision
-// Called by a full warp; all lanes return the same mode.  Every block
-// evaluates it on the same inputs, so every block picks the same mode.
+// Called by a full warp; all lanes return the same choice (a mode, or for the
+// learned policy one of its BLEST_NUM_CHOICES mode / VSS-batch choices).
+// Every block evaluates it on the same inputs, so every block picks the same.
 template <bool TC_OK>
 __device__ __forceinline__ int decide_mode(const BfsParams &P, int ell, long long frontier, long long fedges,
                                            long long unvisited, long long slots, int qlen) {
     int mode;
+    if (P.policy == BLEST_POLICY_LEARNED && P.mlp) {
+        int c = mlp_choose_warp(P.mlp, frontier, fedges, unvisited, slots, ell, P.avg_deg);
+        if (c < 0 || c >= MLP_OUT) c = BLEST_MODE_PUSH_EAGER_CC;
+        // layouts without the Fig. 3 fragment run the CUDA-core twin of a tensor-core choice
+        if (!TC_OK) c = (c == 1) ? 0 : (c == 3) ? 2 : (c == 7) ? 5 : (c == 8) ? 6 : c;
+        return c;
+    }
     if (P.policy == BLEST_POLICY_FIXED) {
         mode = P.fixed_mode;
     } else if (P.policy == BLEST_POLICY_SCHEDULE && P.sched_len > 0) {
         mode = P.schedule[(ell - 1) % P.sched_len];
-    } else if (P.policy == BLEST_POLICY_LEARNED && P.mlp) {
-        mode = mlp_choose_warp(P.mlp, frontier, fedges, unvisited, slots, ell, P.avg_deg);
     } else {
         // §5.2/§7.1: lazy updates when U_div exceeds the threshold; Eq. 5
         // switches to bottom-up when #unvisited < eta * |Q_curr|.
@@ -700,27 +745,27 @@ __device__ __forceinline__ void housekeeping(const BfsParams &P, int ell, int bo
 }
 
 template <bool EAGER, int SIGMA, int LPV>
-__device__ __forceinline__ void push_dispatch(const BfsParams &P, Stage &st, int *grab, bool tc, int ell, int bc,
-                                              int bn, int sn, int qlen, unsigned bsel) {
+__device__ __forceinline__ void push_dispatch(const BfsParams &P, Stage &st, int *grab, BlkAcc *acc, bool tc, int ell,
+                                              int bc, int bn, int sn, int qlen, unsigned bsel, int batch = 1) {
     // eager levels run one pass at a time (their atomics and loads already
     // overlap within a pass, and a second pass's state would not fit the
     // 64-register budget of a 1024-thread CTA); lazy levels keep 1, 2 or 4
     if constexpr (EAGER) {
         if constexpr (Lay<SIGMA, LPV>::TC_OK)
-            if (tc) { push_level<true, true, 1, SIGMA, LPV>(P, st, grab, ell, bc, bn, sn, qlen, bsel); return; }
-        push_level<true, false, 1, SIGMA, LPV>(P, st, grab, ell, bc, bn, sn, qlen, bsel);
+            if (tc) { push_level<true, true, 1, SIGMA, LPV>(P, st, grab, acc, ell, bc, bn, sn, qlen, bsel); return; }
+        push_level<true, false, 1, SIGMA, LPV>(P, st, grab, acc, ell, bc, bn, sn, qlen, bsel);
     } else {
         if constexpr (Lay<SIGMA, LPV>::TC_OK) {
             if (tc) {
-                if (P.batch >= 4) push_level<false, true, 4, SIGMA, LPV>(P, st, grab, ell, bc, bn, sn, qlen, bsel);
-                else if (P.batch >= 2) push_level<false, true, 2, SIGMA, LPV>(P, st, grab, ell, bc, bn, sn, qlen, bsel);
-                else push_level<false, true, 1, SIGMA, LPV>(P, st, grab, ell, bc, bn, sn, qlen, bsel);
+                if (batch >= 4) push_level<false, true, 4, SIGMA, LPV>(P, st, grab, acc, ell, bc, bn, sn, qlen, bsel);
+                else if (batch >= 2) push_level<false, true, 2, SIGMA, LPV>(P, st, grab, acc, ell, bc, bn, sn, qlen, bsel);
+                else push_level<false, true, 1, SIGMA, LPV>(P, st, grab, acc, ell, bc, bn, sn, qlen, bsel);
                 return;
             }
         }
-        if (P.batch >= 4) push_level<false, false, 4, SIGMA, LPV>(P, st, grab, ell, bc, bn, sn, qlen, bsel);
-        else if (P.batch >= 2) push_level<false, false, 2, SIGMA, LPV>(P, st, grab, ell, bc, bn, sn, qlen, bsel);
-        else push_level<false, false, 1, SIGMA, LPV>(P, st, grab, ell, bc, bn, sn, qlen, bsel);
+        if (batch >= 4) push_level<false, false, 4, SIGMA, LPV>(P, st, grab, acc, ell, bc, bn, sn, qlen, bsel);
+        else if (batch >= 2) push_level<false, false, 2, SIGMA, LPV>(P, st, grab, acc, ell, bc, bn, sn, qlen, bsel);
+        else push_level<false, false, 1, SIGMA, LPV>(P, st, grab, acc, ell, bc, bn, sn, qlen, bsel);
     }
 }
 
@@ -754,6 +799,7 @@ __global__ void __launch_bounds__(BFS_MAX_THREADS, 1) k_bfs(BfsParams P) {
     __shared__ int s_mode;
     __shared__ long long s_lvl[4];
     __shared__ int s_grab[3];   // per-level work claims: push passes, stage-2 groups, bottom-up groups
+    __shared__ BlkAcc s_acc;    // per-level CTA totals for the last flush
 
     // ---- level 0 (Algorithm 2/3 init): L = inf except the source, frontier
     // and visited bits hold the source, Q = VSSs of the source's slice set.
@@ -812,6 +858,12 @@ __global__ void __launch_bounds__(BFS_MAX_THREADS, 1) k_bfs(BfsParams P) {
                 s_grab[0] = 0;
                 s_grab[1] = 0;
                 s_grab[2] = 0;
+                s_acc.q = 0;
+                s_acc.s = 0;
+                s_acc.nv = 0;
+                s_acc.fe = 0;
+                s_acc.sv = 0;
+                s_acc.sa = 0;
             }
         }
         __syncthreads();
@@ -819,7 +871,10 @@ __global__ void __launch_bounds__(BFS_MAX_THREADS, 1) k_bfs(BfsParams P) {
         const long long frontier = s_lvl[1];
         const long long fedges = s_lvl[2];
         const int sql_old = (int)s_lvl[3];
-        const int mode = s_mode;
+        const int choice = s_mode;
+        const int mode = mlp_choice_mode(choice);
+        // VSS passes in flight: the learned choice's, else the launch's setting
+        const int batch = (P.policy == BLEST_POLICY_LEARNED && P.mlp) ? mlp_choice_batch(choice) : P.batch;
         __syncthreads();   // s_lvl / s_mode are rewritten at the next level start
         visited += frontier;
         const long long unvisited = (long long)P.n - visited;
@@ -847,26 +902,28 @@ __global__ void __launch_bounds__(BFS_MAX_THREADS, 1) k_bfs(BfsParams P) {
                 rec.scanned_arcs = 0;
                 rec.slots = (long long)qlen * LY::TAU;
                 rec.t_stage1_ns = 0;
+                rec.vss_batch = (mode == BLEST_MODE_BOTTOM_UP) ? 0
+                              : (mode == BLEST_MODE_PUSH_EAGER_CC || mode == BLEST_MODE_PUSH_EAGER_TC) ? 1 : batch;
                 P.log[ell - 1] = rec;
             }
         }
         if (qlen == 0) break;
 
         if (mode == BLEST_MODE_PUSH_EAGER_CC || mode == BLEST_MODE_PUSH_EAGER_TC) {
-            push_dispatch<true, SIGMA, LPV>(P, st, &s_grab[0], mode == BLEST_MODE_PUSH_EAGER_TC, ell, bc, bn, sn, qlen, bsel);
+            push_dispatch<true, SIGMA, LPV>(P, st, &s_grab[0], &s_acc, mode == BLEST_MODE_PUSH_EAGER_TC, ell, bc, bn, sn, qlen, bsel);
             housekeeping<SIGMA>(P, ell, bo, sql_old, sz, tid, nthreads);
             if (!grid_barrier(ctl, epoch, P.budget_ns)) return;
         } else {
             if (mode == BLEST_MODE_BOTTOM_UP)
-                bottom_up_level(P, &s_grab[2], bc, sn, s_found);
+                bottom_up_level(P, &s_grab[2], &s_acc, bc, sn, s_found);
             else
-                push_dispatch<false, SIGMA, LPV>(P, st, &s_grab[0], mode == BLEST_MODE_PUSH_LAZY_TC, ell, bc, bn, sn, qlen,
-                                                 bsel);
+                push_dispatch<false, SIGMA, LPV>(P, st, &s_grab[0], &s_acc, mode == BLEST_MODE_PUSH_LAZY_TC, ell, bc, bn, sn, qlen,
+                                                 bsel, batch);
             housekeeping<SIGMA>(P, ell, bo, sql_old, sz, tid, nthreads);
             if (!grid_barrier(ctl, epoch, P.budget_ns)) return;
             if (logger && ell - 1 < P.log_cap)
                 P.log[ell - 1].t_stage1_ns = (long long)global_ns() - P.log[ell - 1].t_ns;
-            finalize_level<SIGMA>(P, st, &s_grab[1], ell, bn, sn);
+            finalize_level<SIGMA>(P, st, &s_grab[1], &s_acc, ell, bn, sn);
             if (!grid_barrier(ctl, epoch, P.budget_ns)) return;
         }
     }

@@ -309,6 +309,7 @@ extern "C" blest_status blest_get_info(blest_handle h, blest_info *info) {
     info->reorder = h->reorder;
     info->sigma = h->sigma;
     info->tau = h->tau;
+    info->vss_batch = h->vss_batch;
     info->grid_blocks = h->grid;
     info->block_threads = h->block;
     info->build_ms = h->build_ms;

@@ -1,12 +1,17 @@
-// Learned per-level kernel choice: a 3-layer MLP (6 -> 32 -> 32 -> 5, tanh
-// hidden units, fp32) that predicts the log device time of each level mode;
-// the level runs the mode with the smallest prediction.  The same weights
-// are trained on the device by mlp.cu.
+// Learned per-level kernel choice: a 3-layer MLP (6 -> 32 -> 32 -> 9, tanh
+// hidden units, fp32) that predicts the log device time of each level
+// choice -- a level mode and, for lazy top-down levels, the VSS passes a
+// warp keeps in flight; the level runs the choice with the smallest
+// prediction.  The same weights are trained on the device by mlp.cu.
+//
+// Choices: 0-4 are the level modes (BLEST_MODE_*), lazy ones with one pass
+// in flight; 5, 6 = lazy CUDA-core with 2, 4 passes; 7, 8 = lazy b1-MMA
+// with 2, 4 passes.
 //
 // Weight vector layout (fp32, MLP_NW values):
 //   [0, 6)        feature means          [6, 12)      feature 1/std
 //   W1 [32][6]    b1 [32]                W2 [32][32]  b2 [32]
-//   W3 [5][32]    b3 [5]
+//   W3 [9][32]    b3 [9]
 // Features, in order: log1p(frontier vertices), log1p(frontier out-arcs),
 // log1p(unvisited vertices), log1p(active BVSS slots = tau * |Q|),
 // log1p(level index), log1p(average degree).
@@ -15,7 +20,7 @@
 
 #define MLP_IN 6
 #define MLP_H 32
-#define MLP_OUT 5
+#define MLP_OUT 9
 #define MLP_OFF_MEAN 0
 #define MLP_OFF_ISTD 6
 #define MLP_OFF_W1 12
@@ -101,3 +106,8 @@ __device__ __forceinline__ int mlp_choose_warp(const float *__restrict__ w, long
     mlp_raw_features(x, frontier, fedges, unvisited, slots, level, avg_deg);
     return mlp_argmin_warp(mlp_forward_warp(w, x));
 }
+
+// mode and VSS passes in flight of a choice (launch_batch for the rule's and
+// fixed modes, which use the launch's setting)
+__host__ __device__ inline int mlp_choice_mode(int c) { return c < 5 ? c : (c < 7 ? 2 : 3); }
+__host__ __device__ inline int mlp_choice_batch(int c) { return c < 5 ? 1 : ((c - 5) % 2 == 0 ? 2 : 4); }

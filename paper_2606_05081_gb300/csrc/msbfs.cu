@@ -48,6 +48,14 @@ struct MsbfsWork {
     int *d_src = nullptr;
     int grid = 0;
     long long *far = nullptr, *reach = nullptr;   // closeness accumulators (reordered ids)
+    // closeness: one batch (source ids from a device cursor, the persistent
+    // kernel, cursor advance) captured once in a CUDA graph and replayed
+    int *k_dev = nullptr;          // sources in the current batch
+    long long *cursor = nullptr;   // [0] next source, [1] end of the range
+    int *sticky = nullptr;         // first device error of any replayed batch
+    cudaGraph_t cc_graph = nullptr;
+    cudaGraphExec_t cc_exec = nullptr;
+    cudaStream_t cc_stream = nullptr;
 };
 
 namespace {
@@ -69,6 +77,7 @@ struct MsParams {
     const int *srcs;              // k source ids, original numbering
     const int *new_of_old;        // may be null
     const int *old_of_new;        // may be null
+    const int *k_dev;             // non-null: the batch size is read here (graph replays)
     int *levels;                  // k*n, source-major, original ids; may be null
     long long *far, *reach;       // may be null
     unsigned long long budget_ns;
@@ -115,6 +124,23 @@ __device__ __forceinline__ void ms_flush_d(const MsParams &P, MsStage &st, int d
     }
     __syncwarp();
     st.dn = 0;
+}
+
+// The last flush of a stage, called by every thread of the CTA: warps add
+// their staged counts in shared memory and one thread reserves the CTA's
+// space in the global list (one atomic per CTA instead of per warp).
+__device__ __forceinline__ void ms_block_flush(int *list, int *ctr, int *staged, int &n, int *s_tot) {
+    const int lane = lane_id();
+    int off = 0;
+    if (lane == 0 && n) off = atomicAdd(&s_tot[0], n);
+    off = __shfl_sync(FULL_MASK, off, 0);
+    __syncthreads();
+    if (threadIdx.x == 0) s_tot[1] = s_tot[0] ? atomicAdd(ctr, s_tot[0]) : 0;
+    __syncthreads();
+    const int base = s_tot[1] + off;
+    for (int k = lane; k < n; k += 32) list[base + k] = staged[k];
+    __syncwarp();
+    n = 0;
 }
 
 // warp-aggregated append of one slice set per lane (its VSS range -> Q)
@@ -169,8 +195,8 @@ __device__ __forceinline__ void ms_mark_dirty(const MsParams &P, MsStage &st, bo
 }
 
 template <int KW>
-__device__ void ms_stage1(const MsParams &P, MsStage &st, int *grab, int qlen, const int *Qc, int dl, int *s_rows,
-                          unsigned char *s_m) {
+__device__ void ms_stage1(const MsParams &P, MsStage &st, int *grab, int *s_tot, int qlen, const int *Qc, int dl,
+                          int *s_rows, unsigned char *s_m) {
     constexpr int G = 32 / KW;
     const int lane = lane_id();
     const int g = lane / KW, w = lane % KW;
@@ -224,11 +250,12 @@ __device__ void ms_stage1(const MsParams &P, MsStage &st, int *grab, int qlen, c
             ms_mark_dirty(P, st, claimed, so, dl);
         }
     }
-    ms_flush_d(P, st, dl);
+    ms_block_flush(P.dlist[dl], &P.ctl->dlen[dl], st.d, st.dn, s_tot);
 }
 
 template <int KW>
-__device__ void ms_stage2(const MsParams &P, MsStage &st, int *grab, int ell, int dl, int qn, int dcount) {
+__device__ void ms_stage2(const MsParams &P, MsStage &st, int *grab, int *s_tot, int ell, int dl, int qn, int dcount,
+                          int k) {
     constexpr int G = 32 / KW;
     const int lane = lane_id();
     const int g = lane / KW, w = lane % KW;
@@ -265,7 +292,7 @@ __device__ void ms_stage2(const MsParams &P, MsStage &st, int *grab, int ell, in
                             const int b = __ffs(d) - 1;
                             d &= d - 1;
                             const int c = w * 32 + b;
-                            if (c < P.k) P.levels[(size_t)c * P.n + uo] = ell;
+                            if (c < k) P.levels[(size_t)c * P.n + uo] = ell;
                         }
                     }
                 }
@@ -288,7 +315,7 @@ __device__ void ms_stage2(const MsParams &P, MsStage &st, int *grab, int ell, in
         if (valid && w == 0) P.dirty[ss] = 0;
         ms_enqueue(P, st, valid && w == 0 && any, ss, P.Q[qn], qn);
     }
-    ms_flush_q(P, st, P.Q[qn], qn);
+    ms_block_flush(P.Q[qn], &P.ctl->qlen[qn], st.q, st.qn, s_tot);
 }
 
 // two 512-thread CTAs per SM (64 registers a thread)
@@ -298,6 +325,7 @@ __global__ void __launch_bounds__(MS_BLOCK, 2) k_msbfs(MsParams P) {
     __shared__ unsigned char s_m[(MS_BLOCK / 32) * 128];
     __shared__ int s_stg[(MS_BLOCK / 32) * 2 * MS_STG];
     __shared__ int s_grab[2];
+    __shared__ int s_tot[2][2];   // per stage: the CTA's staged total and its reserved base
     MsStage st;
     st.q = s_stg + (threadIdx.x >> 5) * 2 * MS_STG;
     st.d = st.q + MS_STG;
@@ -307,6 +335,7 @@ __global__ void __launch_bounds__(MS_BLOCK, 2) k_msbfs(MsParams P) {
     const size_t nthreads = (size_t)gridDim.x * blockDim.x;
     MsCtl *ctl = P.ctl;
     unsigned epoch = 0;
+    const int k = P.k_dev ? *P.k_dev : P.k;
 
     // ---- init: zero the bit arrays and flags, -1 levels for the k lanes
     const size_t words = (size_t)P.rho * 8 * KW;
@@ -318,10 +347,10 @@ __global__ void __launch_bounds__(MS_BLOCK, 2) k_msbfs(MsParams P) {
     for (size_t i = tid; i < (size_t)P.rho * KW; i += nthreads) P.active[i] = 0u;
     for (size_t i = tid; i < (size_t)P.rho; i += nthreads) P.dirty[i] = 0;
     if (P.levels)
-        for (size_t i = tid; i < (size_t)P.k * P.n; i += nthreads) P.levels[i] = -1;
+        for (size_t i = tid; i < (size_t)k * P.n; i += nthreads) P.levels[i] = -1;
     if (!ms_barrier(ctl, epoch, P.budget_ns)) return;
     // ---- sources: lane c starts at srcs[c]
-    if (tid < (size_t)P.k) {
+    if (tid < (size_t)k) {
         const int c = (int)tid;
         const int so = __ldg(&P.srcs[c]);
         const int u = P.new_of_old ? __ldg(&P.new_of_old[so]) : so;
@@ -365,20 +394,22 @@ __global__ void __launch_bounds__(MS_BLOCK, 2) k_msbfs(MsParams P) {
             s_cnt = ld_volatile_i32(&ctl->qlen[qc]);
             s_grab[0] = 0;
             s_grab[1] = 0;
+            s_tot[0][0] = 0;
+            s_tot[1][0] = 0;
         }
         __syncthreads();
         const int qlen = s_cnt;
         __syncthreads();
         if (qlen == 0) break;
         if (tid == 0) ctl->qlen[qn] = 0;
-        ms_stage1<KW>(P, st, &s_grab[0], qlen, P.Q[qc], dl, s_rows, s_m);
+        ms_stage1<KW>(P, st, &s_grab[0], s_tot[0], qlen, P.Q[qc], dl, s_rows, s_m);
         if (!ms_barrier(ctl, epoch, P.budget_ns)) return;
         if (threadIdx.x == 0) s_cnt = ld_volatile_i32(&ctl->dlen[dl]);
         __syncthreads();
         const int dcount = s_cnt;
         __syncthreads();
         if (tid == 0) ctl->dlen[dl ^ 1] = 0;
-        ms_stage2<KW>(P, st, &s_grab[1], ell, dl, qn, dcount);
+        ms_stage2<KW>(P, st, &s_grab[1], s_tot[1], ell, dl, qn, dcount, k);
         if (!ms_barrier(ctl, epoch, P.budget_ns)) return;
     }
     if (tid == 0) ctl->nlevels = ell - 1;
@@ -408,9 +439,31 @@ int ms_grid() {
 
 }  // namespace
 
+// the next batch of a closeness range: source ids cursor[0] .. up to 1024
+__global__ void k_ms_batch_src(int *d_src, int *k_dev, const long long *cursor) {
+    const long long b = cursor[0], e = cursor[1];
+    const int k = (int)((e - b) < 1024 ? (e - b) : 1024);
+    if (threadIdx.x == 0) *k_dev = k;
+    for (int c = threadIdx.x; c < k; c += blockDim.x) d_src[c] = (int)(b + c);
+}
+
+// after a batch: advance the cursor, keep the first device error
+__global__ void k_ms_batch_next(long long *cursor, const MsCtl *ctl, int *sticky) {
+    cursor[0] += 1024;
+    if (ctl->err && *sticky == 0) *sticky = ctl->err;
+}
+
+static void ms_release_graph(MsbfsWork *m) {
+    if (m->cc_exec) cudaGraphExecDestroy(m->cc_exec);
+    if (m->cc_graph) cudaGraphDestroy(m->cc_graph);
+    m->cc_exec = nullptr;
+    m->cc_graph = nullptr;
+}
+
 void msbfs_release(blest_graph *h) {
     if (h->ms) {
         if (h->ms->h_ctl) cudaFreeHost(h->ms->h_ctl);
+        ms_release_graph(h->ms);
         delete h->ms;
         h->ms = nullptr;
     }
@@ -421,6 +474,7 @@ static blest_status ms_prepare(blest_graph *h, int kappa) {
     if (h->ms && h->ms->kappa < kappa) {
         // grow: the old arrays stay owned by the handle (freed at destroy)
         if (h->ms->h_ctl) cudaFreeHost(h->ms->h_ctl);
+        ms_release_graph(h->ms);
         delete h->ms;
         h->ms = nullptr;
     }
@@ -448,8 +502,10 @@ static blest_status ms_prepare(blest_graph *h, int kappa) {
     return BLEST_OK;
 }
 
-// One multi-source launch over k <= kappa sources already on the device.
-static blest_status ms_launch(blest_graph *h, int k, int *levels_dev, long long *far, long long *reach) {
+// One multi-source launch over k <= kappa sources already on the device
+// (k_dev non-null: the batch size is read from the device at launch).
+static blest_status ms_launch(blest_graph *h, int k, int *levels_dev, long long *far, long long *reach,
+                              const int *k_dev = nullptr) {
     MsbfsWork *m = h->ms;
     MsParams P;
     memset(&P, 0, sizeof P);
@@ -474,6 +530,7 @@ static blest_status ms_launch(blest_graph *h, int k, int *levels_dev, long long 
     P.srcs = m->d_src;
     P.new_of_old = h->g.new_of_old;
     P.old_of_new = h->g.old_of_new;
+    P.k_dev = k_dev;
     P.levels = levels_dev;
     P.far = far;
     P.reach = reach;
@@ -532,22 +589,52 @@ extern "C" blest_status blest_msbfs(blest_handle h, const int32_t *sources, int3
 
 // Distance sums from the sources [first, first + count) (original ids),
 // accumulated into the handle's device accumulators.
+// Closeness over sources [first, first + count): 1024-source batches, each
+// one replay of a CUDA graph holding the source-id kernel, the control-block
+// reset, the persistent multi-source kernel and the cursor advance; one
+// host synchronisation for the whole range.
 static blest_status closeness_batches(blest_graph *h, int64_t first, int64_t count) {
     blest_status st = ms_prepare(h, 1024);
     if (st != BLEST_OK) return st;
-    std::vector<int32_t> src(1024);
-    for (int64_t b = first; b < first + count; b += 1024) {
-        const int k = (int)((first + count - b) < 1024 ? (first + count - b) : 1024);
-        for (int c = 0; c < k; ++c) src[(size_t)c] = (int32_t)(b + c);
-        if (cudaMemcpyAsync(h->ms->d_src, src.data(), (size_t)k * 4, cudaMemcpyHostToDevice, h->stream) !=
-            cudaSuccess)
-            return BLEST_ERR_CUDA;
-        st = ms_launch(h, k, nullptr, h->ms->far, h->ms->reach);
-        if (st != BLEST_OK) return st;
-        st = ms_finish(h, true);  // the host buffer `src` is reused next batch
-        if (st != BLEST_OK) return st;
+    MsbfsWork *m = h->ms;
+    if (count <= 0) return BLEST_OK;
+    if (!m->k_dev) {
+        if ((st = dev_alloc_t(h, &m->k_dev, 1)) != BLEST_OK) return st;
+        if ((st = dev_alloc_t(h, &m->cursor, 2)) != BLEST_OK) return st;
+        if ((st = dev_alloc_t(h, &m->sticky, 1)) != BLEST_OK) return st;
     }
-    return BLEST_OK;
+    cudaStream_t cs = h->stream;
+    if (!m->cc_exec || m->cc_stream != cs) {
+        ms_release_graph(m);
+        if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return BLEST_ERR_CUDA;
+        k_ms_batch_src<<<1, 1024, 0, cs>>>(m->d_src, m->k_dev, m->cursor);
+        st = ms_launch(h, 1024, nullptr, m->far, m->reach, m->k_dev);
+        k_ms_batch_next<<<1, 1, 0, cs>>>(m->cursor, m->ctl, m->sticky);
+        cudaGraph_t g = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(cs, &g);
+        if (st != BLEST_OK || ec != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            blest_internal_record_cuda_error(ec, "capture of the closeness batch", __FILE__, __LINE__);
+            return st != BLEST_OK ? st : BLEST_ERR_CUDA;
+        }
+        m->cc_graph = g;
+        if (cudaGraphInstantiate(&m->cc_exec, g, 0) != cudaSuccess) {
+            ms_release_graph(m);
+            return BLEST_ERR_CUDA;
+        }
+        m->cc_stream = cs;
+    }
+    const long long range[2] = {(long long)first, (long long)(first + count)};
+    if (cudaMemcpyAsync(m->cursor, range, sizeof range, cudaMemcpyHostToDevice, cs) != cudaSuccess)
+        return BLEST_ERR_CUDA;
+    if (cudaMemsetAsync(m->sticky, 0, sizeof(int), cs) != cudaSuccess) return BLEST_ERR_CUDA;
+    for (int64_t b = first; b < first + count; b += 1024)
+        if (cudaGraphLaunch(m->cc_exec, cs) != cudaSuccess) return BLEST_ERR_CUDA;
+    int err = 0;
+    if (cudaMemcpyAsync(&err, m->sticky, sizeof(int), cudaMemcpyDeviceToHost, cs) != cudaSuccess)
+        return BLEST_ERR_CUDA;
+    if (cudaStreamSynchronize(cs) != cudaSuccess) return BLEST_ERR_CUDA;
+    return err ? (blest_status)err : BLEST_OK;
 }
 
 static blest_status closeness_common(blest_graph *h, int64_t first, int64_t count, int64_t *far, double *cc,

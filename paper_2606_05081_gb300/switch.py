@@ -26,20 +26,22 @@ import time
 
 import numpy as np
 
-from . import (MLP_NW, POLICY_FIXED, POLICY_HEURISTIC, POLICY_LEARNED, Graph, mlp_features, mlp_predict,
-               mlp_train)
+from . import (MLP_NW, NUM_CHOICES, POLICY_FIXED, POLICY_HEURISTIC, POLICY_LEARNED, Graph, choice_mode_batch,
+               choice_of, mlp_features, mlp_predict, mlp_train)
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 DEFAULT_WEIGHTS = os.path.join(HERE, "switch_mlp.f32")
-NUM_MODES = 5
-
-
 def level_times(h: Graph, source: int, out, reps: int = 1):
-    """Per-level records of one BFS and its (levels x modes) device-time
-    matrix in ns (min over reps)."""
+    """Per-level records of one BFS and its (levels x choices) device-time
+    matrix in ns (min over reps): choice c runs its mode at every level with
+    its number of VSS passes in flight."""
     recs, T = None, None
-    for m in range(NUM_MODES):
-        h.set_policy(POLICY_FIXED, m)
+    info = h.info()
+    block, batch0 = info["block_threads"], info["vss_batch"]
+    for c in range(NUM_CHOICES):
+        mode, batch = choice_mode_batch(c)
+        h.set_launch(block, batch)
+        h.set_policy(POLICY_FIXED, mode)
         best = None
         for _ in range(reps):
             h.bfs(int(source), out)
@@ -49,16 +51,18 @@ def level_times(h: Graph, source: int, out, reps: int = 1):
             if recs is None:
                 recs = log
         if T is None:
-            T = np.zeros((len(best), NUM_MODES))
+            T = np.zeros((len(best), NUM_CHOICES))
         if len(best) != T.shape[0]:
             raise RuntimeError("level count differs between modes")
-        T[:, m] = best
+        T[:, c] = best
+    h.set_launch(block, batch0)
     h.set_policy(POLICY_HEURISTIC)
     return recs, T
 
 
 def dataset(handles, sources_per, reps: int = 2, avg_degs=None):
-    """Features (n, 6), log-time targets (n, 5), mask, and the raw matrices."""
+    """Features (n, 6), log-time targets (n, NUM_CHOICES), mask, and the raw
+    matrices."""
     import torch
     X, Y, mats = [], [], []
     for i, (h, srcs) in enumerate(zip(handles, sources_per)):
@@ -81,7 +85,7 @@ def init_weights(X, seed: int = 0) -> np.ndarray:
     w[0:6] = X.mean(0)
     w[6:12] = 1.0 / np.maximum(X.std(0), 1e-3)
     off = 12
-    for fo, fi in ((32, 6), (32, 32), (5, 32)):
+    for fo, fi in ((32, 6), (32, 32), (NUM_CHOICES, 32)):
         a = np.sqrt(6.0 / (fi + fo))
         w[off:off + fo * fi] = rs.uniform(-a, a, fo * fi)
         off += fo * fi + fo
@@ -105,15 +109,16 @@ def train(X, Y, M=None, epochs: int = 1500, lr: float = 5e-3, weight_decay: floa
     return mlp_train(X, rel, mask, w0, epochs, lr, weight_decay)
 
 
-def heuristic_modes(info: dict, recs, eta: float = 10.0, tc: bool = False):
-    """The paper's rule on logged levels (§5.3, §7.1)."""
+def heuristic_modes(info: dict, recs, eta: float = 10.0, tc: bool = False, batch: int = 2):
+    """The paper's rule on logged levels (§5.3, §7.1), as choices (its lazy
+    levels run with the launch's `batch` VSS passes in flight)."""
     lazy, sw = info["lazy"], info["switching"]
     out = []
     for r in recs:
         m = (3 if tc else 2) if lazy else (1 if tc else 0)
         if sw and r["unvisited"] < eta * r["queue"]:
             m = 4
-        out.append(m)
+        out.append(choice_of(m, batch))
     return np.array(out)
 
 
@@ -134,8 +139,8 @@ def evaluate(h: Graph, sources, weights, reps: int = 2):
         recs, T = level_times(h, int(s), out, reps)
         _, ch = mlp_predict(weights, mlp_features(recs, ad))
         r = np.arange(len(ch))
-        tot["heuristic_tc"] += T[r, heuristic_modes(info, recs, tc=True)].sum()
-        tot["heuristic_cc"] += T[r, heuristic_modes(info, recs, tc=False)].sum()
+        tot["heuristic_tc"] += T[r, heuristic_modes(info, recs, tc=True, batch=info["vss_batch"])].sum()
+        tot["heuristic_cc"] += T[r, heuristic_modes(info, recs, tc=False, batch=info["vss_batch"])].sum()
         tot["learned"] += T[r, ch].sum()
         tot["optimal"] += T.min(axis=1).sum()
     opt = tot["optimal"]

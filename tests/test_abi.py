@@ -4,6 +4,7 @@ import os
 import re
 import subprocess
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -60,3 +61,20 @@ def test_no_product_module_imports_oracle():
                 src = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in src and "from oracle" not in src, f
                 assert "bfs_oracle" not in src, f
+
+
+def test_mlp_buffer_shapes_checked_before_the_c_call():
+    """The C entry points cannot see buffer sizes, so the binding checks them
+    (a wrong width would let the library write past a host array)."""
+    b = pytest.importorskip("paper_2606_05081_gb300")
+    assert b.MLP_NW == 1589 and b.NUM_CHOICES == 9
+    X = np.zeros((3, 6), np.float32)
+    with pytest.raises(ValueError):
+        b.mlp_predict(np.zeros(1457, np.float32), X)
+    with pytest.raises(ValueError):
+        b.mlp_train(X, np.zeros((3, 5), np.float32), np.ones((3, 5), np.float32), np.zeros(b.MLP_NW, np.float32))
+    with pytest.raises(ValueError):
+        b.mlp_loss_grad(np.zeros((3, 5), np.float32), np.zeros((3, 9)), np.ones((3, 9)), np.zeros(b.MLP_NW))
+    for c in range(b.NUM_CHOICES):
+        m, k = b.choice_mode_batch(c)
+        assert b.choice_of(m, k) == c

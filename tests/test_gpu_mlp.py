@@ -25,8 +25,8 @@ def blest():
 def _data(n=500, seed=1):
     rs = np.random.RandomState(seed)
     X = rs.uniform(0, 16, (n, 6)).astype(np.float32)
-    Y = (rs.normal(10, 1.5, (n, 5)) + 0.2 * X[:, :1]).astype(np.float32)
-    M = (rs.uniform(size=(n, 5)) > 0.1).astype(np.float32)
+    Y = (rs.normal(10, 1.5, (n, omlp.OUT)) + 0.2 * X[:, :1]).astype(np.float32)
+    M = (rs.uniform(size=(n, omlp.OUT)) > 0.1).astype(np.float32)
     return X, Y, M
 
 
@@ -65,7 +65,7 @@ def test_training_is_deterministic_and_tracks_oracle(blest):
 def test_predictions_match_oracle(blest):
     X, _, _ = _data(400, seed=7)
     w = omlp.init_weights(X.astype(np.float64).mean(0), X.astype(np.float64).std(0), seed=8)
-    w[omlp.OFF_B3:] = [0.3, -0.2, 0.1, 0.0, 0.05]
+    w[omlp.OFF_B3:] = [0.3, -0.2, 0.1, 0.0, 0.05, 0.2, -0.1, 0.15, 0.25]
     w = w.astype(np.float32)
     pred, ch = blest.mlp_predict(w, X)
     ref, _ = omlp.forward(w.astype(np.float64), X.astype(np.float64))
@@ -92,7 +92,7 @@ def test_in_kernel_decisions_and_exact_levels(blest):
                 assert np.array_equal(h.bfs(int(s)), oracle.bfs(g, int(s)))
                 log = h.level_log()
                 _, ch = blest.mlp_predict(w, blest.mlp_features(log, ad))
-                assert [r["mode"] for r in log] == ch.tolist()
+                assert [blest.choice_of(r["mode"], r["vss_batch"]) for r in log] == ch.tolist()
         h.set_policy(blest.POLICY_HEURISTIC)
 
 

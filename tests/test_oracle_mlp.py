@@ -16,7 +16,8 @@ def _data(n=40, seed=1):
 
 
 def test_layout_size():
-    assert mlp.NW == 12 + 32 * 6 + 32 + 32 * 32 + 32 + 5 * 32 + 5 == 1457
+    assert mlp.OUT == 9
+    assert mlp.NW == 12 + 32 * 6 + 32 + 32 * 32 + 32 + 9 * 32 + 9 == 1589
 
 
 def test_gradient_matches_central_differences():
@@ -41,9 +42,9 @@ def test_zero_network_predicts_bias_and_mse():
     raw, tgt, mask = _data(10)
     w = np.zeros(mlp.NW)
     w[mlp.OFF_ISTD:mlp.OFF_ISTD + 6] = 1.0
-    w[mlp.OFF_B3:] = [1, 2, 3, 4, 5]
+    w[mlp.OFF_B3:] = np.arange(1, mlp.OUT + 1)
     y, _ = mlp.forward(w, raw)
-    assert np.array_equal(y, np.tile([1, 2, 3, 4, 5], (10, 1)).astype(float))
+    assert np.array_equal(y, np.tile(np.arange(1, mlp.OUT + 1), (10, 1)).astype(float))
     loss, g = mlp.loss_and_grad(w, raw, tgt, mask)
     r = (y - tgt) * mask
     assert abs(loss - (r ** 2).sum() / mask.sum()) < 1e-12
@@ -65,7 +66,7 @@ def test_first_adam_step_is_signed_lr():
 
 def test_training_reduces_loss():
     raw, tgt, mask = _data(200, seed=7)
-    tgt = np.stack([raw[:, 0] * 0.5 + k for k in range(5)], 1)
+    tgt = np.stack([raw[:, 0] * 0.5 + k for k in range(mlp.OUT)], 1)
     w = mlp.init_weights(raw.mean(0), raw.std(0), seed=1)
     m = np.zeros(mlp.NW)
     v = np.zeros(mlp.NW)
