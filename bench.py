@@ -449,12 +449,17 @@ def main():
     # roofline of the persistent BFS kernel under the headline arm
     hbm, peak_kind = peaks()
     alg_b, dev_s = 0.0, 0.0
+    per_graph_roof = {}
     for r in runs:
         logs = results["tuned"][2][r.name]
         ti = r.h_tuned.info()
-        alg_b += sum(algorithmic_bytes(lg, r.g.n, rc, ti["sigma"], ti["tau"]) +
-                     (8.0 * r.g.n if r.info["reorder"] else 0.0) for lg, rc in zip(logs, r.reached))
-        dev_s += float(results["tuned"][0][r.name].mean(axis=0).sum()) * 1e-3
+        gb = sum(algorithmic_bytes(lg, r.g.n, rc, ti["sigma"], ti["tau"]) +
+                 (8.0 * r.g.n if r.info["reorder"] else 0.0) for lg, rc in zip(logs, r.reached))
+        gs = float(results["tuned"][0][r.name].mean(axis=0).sum()) * 1e-3
+        alg_b += gb
+        dev_s += gs
+        per_graph_roof[r.name] = {"achieved_gbs": gb / gs / 1e9, "frac": gb / gs / 1e9 / hbm,
+                                  "algorithmic_bytes_per_launch": gb / len(r.srcs)}
     achieved = alg_b / dev_s / 1e9
 
     # end to end through the C ABI with host buffers, headline arm
@@ -502,7 +507,7 @@ def main():
                                                   for r in runs]), "peak_kind": peak_kind,
                      "kernel": "k_bfs (persistent, all levels)",
                      "algorithmic_bytes_per_launch": alg_b / sum(len(r.srcs) for r in runs),
-                     "kernel_sha": kernel_sha()},
+                     "kernel_sha": kernel_sha(), "per_graph": per_graph_roof},
         "e2e": {"value": e2e, "unit": "GTEPS", "h2d_bytes_per_step": 4 * sum(len(r.srcs) for r in runs),
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": args.steps * sum(len(r.srcs) for r in runs) * len(arms),

@@ -252,6 +252,9 @@ const char *blest_status_string(blest_status s);
  * prediction.  A choice is a mode and the VSS passes a warp keeps in flight:
  * choices 0-4 are the modes BLEST_MODE_* (lazy ones with one pass), 5 and 6
  * lazy CUDA-core with 2 and 4 passes, 7 and 8 lazy b1-MMA with 2 and 4.
+ * Bottom-up is never chosen for a level with more than 16 unvisited
+ * vertices per scheduled slot (raw features: log1p(unvisited) >
+ * log1p(slots) + log 16), whatever the prediction.
  * Weights: BLEST_MLP_NW floats, [0,6) feature means, [6,12) feature 1/std,
  * then W1[32][6], b1[32], W2[32][32], b2[32], W3[9][32], b3[9].  All arrays
  * below may be host or device memory and are row-major (one sample per

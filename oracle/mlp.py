@@ -108,9 +108,17 @@ def adam_step(w, g, m, v, t, lr=1e-2, b1=0.9, b2=0.999, eps=1e-8, wd=0.0):
     return w, m, v
 
 
+BU_GUARD_LOG = np.log(16.0)
+
+
 def choose(w, raw):
-    """Mode with the smallest predicted log time (lowest index on ties)."""
+    """Choice with the smallest predicted log time (lowest index on ties);
+    bottom-up (choice 4) is excluded on levels with more than 16 unvisited
+    vertices per scheduled slot (raw features 2 and 3)."""
     y, _ = forward(w, raw)
+    raw = np.atleast_2d(np.asarray(raw, np.float64))
+    y = np.array(y, np.float64, copy=True).reshape(raw.shape[0], OUT)
+    y[raw[:, 2] > raw[:, 3] + BU_GUARD_LOG, 4] = np.inf
     return np.argmin(y, axis=-1)
 
 

@@ -524,20 +524,30 @@ __device__ void bottom_up_level(const BfsParams &P, int *grab, BlkAcc *acc, int 
                 hd[k] = act[k] ? __ldg(&P.head[u[k]]) : make_int4(-1, -1, -1, -1);
                 if (act[k]) sv += 1;
             }
-            unsigned fw[2][4];
+            // the highest-degree in-neighbour alone first (it is the likeliest
+            // frontier member); the other three only where it missed, which
+            // keeps the random frontier-word reads through L2 to about one a
+            // vertex
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const int v0 = hd[k].x;
+                const unsigned f0 = v0 >= 0 ? Fc[v0 >> 5] : 0u;
+                hit[k] = (v0 >= 0) && ((f0 >> (v0 & 31)) & 1u);
+            }
+            unsigned fw[2][3];
 #pragma unroll
             for (int k = 0; k < 2; ++k)
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
+                for (int q = 1; q < 4; ++q) {
                     const int vq = pick(hd[k], q);
-                    fw[k][q] = vq >= 0 ? Fc[vq >> 5] : 0u;
+                    fw[k][q - 1] = (!hit[k] && vq >= 0) ? Fc[vq >> 5] : 0u;
                 }
 #pragma unroll
             for (int k = 0; k < 2; ++k)
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
+                for (int q = 1; q < 4; ++q) {
                     const int vq = pick(hd[k], q);
-                    hit[k] |= (vq >= 0) && ((fw[k][q] >> (vq & 31)) & 1u);
+                    hit[k] |= (vq >= 0) && ((fw[k][q - 1] >> (vq & 31)) & 1u);
                 }
             // rows longer than four: the rest of the row, four ids per round
 #pragma unroll

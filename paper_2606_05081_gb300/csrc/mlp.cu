@@ -169,7 +169,7 @@ __global__ void k_mlp_predict(const float *__restrict__ w, const float *__restri
     const float y = mlp_forward_warp(w, x);
     const int lane = threadIdx.x & 31;
     if (pred && lane < MLP_OUT) pred[(size_t)s * MLP_OUT + lane] = y;
-    const int c = mlp_argmin_warp(y);
+    const int c = mlp_argmin_warp(y, mlp_bu_blocked(x));
     if (choice && lane == 0) choice[s] = c;
 }
 

@@ -66,7 +66,7 @@ __device__ __forceinline__ void mlp_stage_weights(const float *__restrict__ w, f
 // Warp-cooperative forward pass on raw features x (all 32 lanes call it;
 // lane h owns hidden unit h of both layers), weights staged by
 // mlp_stage_weights.  Lane o < MLP_OUT returns the prediction for mode o
-// (other lanes return 0).  Sums run in input order with fused multiply-adds.
+// (other lanes return 0).
 __device__ __forceinline__ float mlp_forward_warp(const float *__restrict__ w, const float *xr) {
     const int lane = threadIdx.x & 31;
     float x[MLP_IN];
@@ -76,25 +76,42 @@ __device__ __forceinline__ float mlp_forward_warp(const float *__restrict__ w, c
 #pragma unroll
     for (int i = 0; i < MLP_IN; ++i) a1 = fmaf(w[MLP_OFF_W1 + i * MLP_H + lane], x[i], a1);
     const float h1 = tanhf(a1);
-    float a2 = w[MLP_OFF_B2 + lane];
+    // four interleaved partial sums (inputs k = j mod 4) shorten the chain of
+    // dependent multiply-adds the level start waits on; summed in a fixed order
+    float p2[4] = {w[MLP_OFF_B2 + lane], 0.f, 0.f, 0.f};
 #pragma unroll
-    for (int k = 0; k < MLP_H; ++k) a2 = fmaf(w[MLP_OFF_W2 + k * MLP_H + lane], __shfl_sync(0xFFFFFFFFu, h1, k), a2);
-    const float h2 = tanhf(a2);
+    for (int k = 0; k < MLP_H; ++k)
+        p2[k & 3] = fmaf(w[MLP_OFF_W2 + k * MLP_H + lane], __shfl_sync(0xFFFFFFFFu, h1, k), p2[k & 3]);
+    const float h2 = tanhf((p2[0] + p2[1]) + (p2[2] + p2[3]));
     const int o = lane < MLP_OUT ? lane : 0;
-    float y = w[MLP_OFF_B3 + o];
+    float p3[4] = {w[MLP_OFF_B3 + o], 0.f, 0.f, 0.f};
 #pragma unroll
-    for (int k = 0; k < MLP_H; ++k) y = fmaf(w[MLP_OFF_W3 + k * MLP_OUT + o], __shfl_sync(0xFFFFFFFFu, h2, k), y);
+    for (int k = 0; k < MLP_H; ++k)
+        p3[k & 3] = fmaf(w[MLP_OFF_W3 + k * MLP_OUT + o], __shfl_sync(0xFFFFFFFFu, h2, k), p3[k & 3]);
+    const float y = (p3[0] + p3[1]) + (p3[2] + p3[3]);
     return lane < MLP_OUT ? y : 0.f;
 }
 
-// argmin over the MLP_OUT predictions (lowest index on ties); all lanes get it
-__device__ __forceinline__ int mlp_argmin_warp(float y) {
-    float best = __shfl_sync(0xFFFFFFFFu, y, 0);
-    int arg = 0;
+// Bottom-up guard: a bottom-up level reads every unvisited vertex, a
+// top-down level only the scheduled slots, so a level with more than 16
+// unvisited vertices per scheduled slot never runs bottom-up whatever the
+// network predicts (this keeps graphs unlike the training set away from
+// the one choice whose cost grows with the unvisited set).  Tested on the
+// raw features: log1p(unvisited) > log1p(slots) + log(16).
+#define MLP_BU_GUARD_LOG 2.7725887f
+
+__host__ __device__ inline bool mlp_bu_blocked(const float *xraw) { return xraw[2] > xraw[3] + MLP_BU_GUARD_LOG; }
+
+// argmin over the MLP_OUT predictions (lowest index on ties), skipping
+// bottom-up (choice 4) when blocked; all lanes get it
+__device__ __forceinline__ int mlp_argmin_warp(float y, bool no_bu) {
+    int arg = -1;
+    float best = 0.f;
 #pragma unroll
-    for (int o = 1; o < MLP_OUT; ++o) {
+    for (int o = 0; o < MLP_OUT; ++o) {
         const float v = __shfl_sync(0xFFFFFFFFu, y, o);
-        if (v < best) { best = v; arg = o; }
+        if (no_bu && o == 4) continue;
+        if (arg < 0 || v < best) { best = v; arg = o; }
     }
     return arg;
 }
@@ -104,7 +121,7 @@ __device__ __forceinline__ int mlp_choose_warp(const float *__restrict__ w, long
                                                long long unvisited, long long slots, int level, float avg_deg) {
     float x[MLP_IN];
     mlp_raw_features(x, frontier, fedges, unvisited, slots, level, avg_deg);
-    return mlp_argmin_warp(mlp_forward_warp(w, x));
+    return mlp_argmin_warp(mlp_forward_warp(w, x), mlp_bu_blocked(x));
 }
 
 // mode and VSS passes in flight of a choice (launch_batch for the rule's and

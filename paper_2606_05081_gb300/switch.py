@@ -170,13 +170,15 @@ TRAIN_LAYOUTS = ((8, 128), (8, 32))
 
 def training_graphs():
     """The graph families of the single-source (RMAT, road-like grid) and
-    batched (RMAT, Barabasi-Albert) workloads over the size range they are
-    used at; random geometric graphs are left out (a held-out family)."""
+    batched (RMAT, Barabasi-Albert with m = 4 and 8) workloads over the size
+    range they are used at; random geometric graphs are left out (a held-out
+    family), as are RMAT 25 and Barabasi-Albert graphs of 2^24 vertices."""
     import graphgen as gg
     out = [(f"rmat{s}", (lambda s=s: gg.rmat(s, 16, seed=100 + s)), {}) for s in (14, 16, 18, 20, 22, 24)]
     out += [(f"grid{r}", (lambda r=r: gg.grid(r, r, 0.05, 0.001, seed=200 + r)), {"reorder": 1})
             for r in (256, 1024, 2048)]
     out += [(f"ba{n}", (lambda n=n: gg.ba(n, 4, seed=300 + n % 997)), {}) for n in (1 << 16, 1 << 20, 1 << 22)]
+    out += [(f"ba{n}m8", (lambda n=n: gg.ba(n, 8, seed=400 + n % 991)), {}) for n in (1 << 20, 1 << 22)]
     return out
 
 

@@ -70,9 +70,17 @@ def test_predictions_match_oracle(blest):
     pred, ch = blest.mlp_predict(w, X)
     ref, _ = omlp.forward(w.astype(np.float64), X.astype(np.float64))
     assert np.all(np.abs(pred - ref) <= 1e-4 * (1 + np.abs(ref)))
-    srt = np.sort(ref, axis=1)
-    clear = srt[:, 1] - srt[:, 0] > 1e-3
-    assert np.array_equal(ch[clear], np.argmin(ref, axis=1)[clear])
+    # the choice is the argmin with bottom-up excluded where the guard holds
+    blocked = X[:, 2].astype(np.float64) > X[:, 3].astype(np.float64) + omlp.BU_GUARD_LOG
+    near = np.abs(X[:, 2].astype(np.float64) - X[:, 3] - omlp.BU_GUARD_LOG) < 1e-4
+    refg = ref.copy()
+    refg[blocked, 4] = np.inf
+    srt = np.sort(refg, axis=1)
+    clear = (srt[:, 1] - srt[:, 0] > 1e-3) & ~near
+    assert blocked.any() and (~blocked).any()
+    assert np.array_equal(ch[clear], np.argmin(refg, axis=1)[clear])
+    assert np.array_equal(ch[clear], omlp.choose(w.astype(np.float64), X.astype(np.float64))[clear])
+    assert not np.any(ch[blocked & ~near] == 4)
 
 
 def test_in_kernel_decisions_and_exact_levels(blest):
