@@ -84,7 +84,8 @@ struct Ctl {
 // same number of times.  Arrivals are counted on a monotone counter; the
 // k-th barrier waits for k*gridDim.x arrivals.  A wait that exceeds the
 // budget records BLEST_ERR_TIMEOUT and returns; once err is set every block
-// leaves at its next barrier, so no block spins forever.
+// leaves at its next barrier (whose spin loop checks err every 64 polls), so
+// no block spins forever.
 // Returns true when the grid may proceed.
 __device__ __forceinline__ bool grid_barrier(Ctl *ctl, unsigned &epoch, uint64_t budget_ns) {
     __shared__ int s_ok;
@@ -110,7 +111,9 @@ __device__ __forceinline__ bool grid_barrier(Ctl *ctl, unsigned &epoch, uint64_t
             }
             if (spins > 256) __nanosleep(32);
         }
-        if (ld_volatile_i32(&ctl->err) != 0) ok = 0;
+        // no error check once the barrier has completed: a block that gave up
+        // had arrived first, so the others finish this barrier and see the
+        // error in the spin loop of the next one
         s_ok = ok;
     }
     __syncthreads();
