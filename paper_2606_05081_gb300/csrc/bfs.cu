@@ -814,7 +814,20 @@ __global__ void __launch_bounds__(BFS_MAX_THREADS, 1) k_bfs(BfsParams P) {
     // ---- level 0 (Algorithm 2/3 init): L = inf except the source, frontier
     // and visited bits hold the source, Q = VSSs of the source's slice set.
     const int src = P.new_of_old ? __ldg(&P.new_of_old[P.src]) : P.src;
-    for (int i = tid; i < P.n; i += nthreads) P.L[i] = (i == src) ? 0 : -1;
+    if ((reinterpret_cast<uintptr_t>(P.L) & 15u) == 0) {   // 16-byte stores where aligned
+        const long long n4 = P.n & ~3;
+        const int4 m1 = make_int4(-1, -1, -1, -1);
+        for (long long i = (long long)tid * 4; i < n4; i += (long long)nthreads * 4) {
+            int4 v = m1;
+            if (src >= i && src < i + 4) {
+                if (src == i) v.x = 0; else if (src == i + 1) v.y = 0; else if (src == i + 2) v.z = 0; else v.w = 0;
+            }
+            reinterpret_cast<int4 *>(P.L + i)[0] = v;
+        }
+        for (long long i = n4 + tid; i < P.n; i += nthreads) P.L[i] = (i == src) ? 0 : -1;
+    } else {
+        for (int i = tid; i < P.n; i += nthreads) P.L[i] = (i == src) ? 0 : -1;
+    }
     for (int w = tid; w < P.W; w += nthreads) {
         const unsigned b = (w == (src >> 5)) ? (1u << (src & 31)) : 0u;
         P.Vc[w] = b;
@@ -938,9 +951,28 @@ __global__ void __launch_bounds__(BFS_MAX_THREADS, 1) k_bfs(BfsParams P) {
         }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) ctl->nlevels = ell - 1;
-    // undo the reordering: out[v] = L[new_of_old[v]]
-    if (P.new_of_old)
-        for (int v = tid; v < P.n; v += nthreads) P.out[v] = P.L[__ldg(&P.new_of_old[v])];
+    // undo the reordering: out[v] = L[new_of_old[v]].  Eight vertices a
+    // thread per step: two 16-byte loads of the permutation, then eight
+    // independent gathers, so each thread pays the gather latency once per
+    // eight vertices rather than once per vertex.
+    if (P.new_of_old) {
+        const bool vec = (reinterpret_cast<uintptr_t>(P.out) & 15u) == 0;
+        const long long n8 = P.n & ~7;
+        for (long long v0 = (long long)tid * 8; v0 < n8; v0 += (long long)nthreads * 8) {
+            const int4 pa = __ldg(reinterpret_cast<const int4 *>(P.new_of_old + v0));
+            const int4 pb = __ldg(reinterpret_cast<const int4 *>(P.new_of_old + v0) + 1);
+            const int4 ga = make_int4(P.L[pa.x], P.L[pa.y], P.L[pa.z], P.L[pa.w]);
+            const int4 gb = make_int4(P.L[pb.x], P.L[pb.y], P.L[pb.z], P.L[pb.w]);
+            if (vec) {
+                reinterpret_cast<int4 *>(P.out + v0)[0] = ga;
+                reinterpret_cast<int4 *>(P.out + v0)[1] = gb;
+            } else {
+                P.out[v0] = ga.x; P.out[v0 + 1] = ga.y; P.out[v0 + 2] = ga.z; P.out[v0 + 3] = ga.w;
+                P.out[v0 + 4] = gb.x; P.out[v0 + 5] = gb.y; P.out[v0 + 6] = gb.z; P.out[v0 + 7] = gb.w;
+            }
+        }
+        for (long long v = n8 + tid; v < P.n; v += nthreads) P.out[v] = P.L[__ldg(&P.new_of_old[v])];
+    }
 }
 
 // the kernel instance of a (sigma, tau) layout (nullptr for other pairs)
