@@ -194,6 +194,26 @@ __device__ __forceinline__ void ms_mark_dirty(const MsParams &P, MsStage &st, bo
     __syncwarp();
 }
 
+// bit g = OR of the KW-bit field g of x (the 32/KW lane groups of a ballot)
+template <int KW>
+__device__ __forceinline__ unsigned group_bits(unsigned x) {
+    if constexpr (KW == 32) {
+        return x != 0u ? 1u : 0u;
+    } else if constexpr (KW == 8) {
+        x = (x | (x >> 4)) & 0x0F0F0F0Fu;
+        x = (x | (x >> 2)) & 0x03030303u;
+        x = (x | (x >> 1)) & 0x01010101u;           // bit 8g = any of byte g
+        return (x * 0x01020408u) >> 24 & 0xFu;      // gather bits 0, 8, 16, 24 into 0..3
+    } else {                                          // KW == 2: 16 pairs
+        x = (x | (x >> 1)) & 0x55555555u;            // bit 2g = any of pair g
+        x = (x | (x >> 1)) & 0x33333333u;
+        x = (x | (x >> 2)) & 0x0F0F0F0Fu;
+        x = (x | (x >> 4)) & 0x00FF00FFu;
+        x = (x | (x >> 8)) & 0x0000FFFFu;
+        return x;
+    }
+}
+
 template <int KW>
 __device__ void ms_stage1(const MsParams &P, MsStage &st, int *grab, int *s_tot, int qlen, const int *Qc, int dl,
                           int *s_rows, unsigned char *s_m) {
@@ -233,6 +253,10 @@ __device__ void ms_stage1(const MsParams &P, MsStage &st, int *grab, int *s_tot,
 #pragma unroll
         for (int j = 0; j < 8; ++j) f[j] = aw ? P.F[(size_t)get_vi(ss * 8 + j, P.rho) * KW + w] : 0u;
         __syncwarp();
+        // slots with a hit (bit s of hm[s / 32]); their slice sets are marked
+        // dirty after the loop, 32 slots at a time, so the loop never waits on
+        // the dirty flags
+        unsigned hm0 = 0, hm1 = 0, hm2 = 0, hm3 = 0;
 #pragma unroll 2
         for (int t = 0; t < (nslots + G - 1) / G; ++t) {
             const int kk = t * G + g;
@@ -243,10 +267,27 @@ __device__ void ms_stage1(const MsParams &P, MsStage &st, int *grab, int *s_tot,
             const int u = rows[kk];
             if (hit) red_or(&P.Vn[(size_t)get_vi(u, P.rho) * KW + w], hit);
             const unsigned bal = __ballot_sync(FULL_MASK, hit != 0);
+            // one bit per group (any of its KW lanes hit), packed: slots t*G .. t*G+G-1
+            const unsigned gb = group_bits<KW>(bal);
+            if (gb) {
+                const int s0 = t * G;                       // G divides 32: one word holds them
+                const unsigned bits = gb << (s0 & 31);
+                if (s0 < 32) hm0 |= bits;
+                else if (s0 < 64) hm1 |= bits;
+                else if (s0 < 96) hm2 |= bits;
+                else hm3 |= bits;
+            }
+        }
+#pragma unroll
+        for (int r4 = 0; r4 < 4; ++r4) {
+            const unsigned hm = r4 == 0 ? hm0 : (r4 == 1 ? hm1 : (r4 == 2 ? hm2 : hm3));
+            if (!hm) continue;   // warp-uniform
             bool claimed = false;
-            const int so = u >> 3;
-            if (w == 0 && ((bal >> (g * KW)) & (KW == 32 ? 0xFFFFFFFFu : ((1u << KW) - 1u))))
+            int so = 0;
+            if (hm >> lane & 1u) {
+                so = rows[32 * r4 + lane] >> 3;
                 claimed = ld_volatile_i32(&P.dirty[so]) == 0 && atomicExch(&P.dirty[so], 1) == 0;
+            }
             ms_mark_dirty(P, st, claimed, so, dl);
         }
     }
@@ -272,14 +313,30 @@ __device__ void ms_stage2(const MsParams &P, MsStage &st, int *grab, int *s_tot,
         const bool valid = i < dcount;
         const int ss = valid ? dlist[i] : 0;
         unsigned A = 0;
+        // four vertices at a time: their V_next / V_curr words load together
 #pragma unroll 1
-        for (int j = 0; j < 8; ++j) {
+        for (int j0 = 0; j0 < 8; j0 += 4) {
+          unsigned nx4[4], cu4[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+              const int u = ss * 8 + j0 + q;
+              nx4[q] = 0u;
+              cu4[q] = 0u;
+              if (valid && u < P.n) {
+                  const size_t e = (size_t)get_vi(u, P.rho) * KW + w;
+                  nx4[q] = P.Vn[e];
+                  cu4[q] = P.Vc[e];
+              }
+          }
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int j = j0 + q;
             const int u = ss * 8 + j;
             unsigned diff = 0;
             if (valid && u < P.n) {
                 const size_t e = (size_t)get_vi(u, P.rho) * KW + w;
-                const unsigned next = P.Vn[e];
-                const unsigned cur = P.Vc[e];
+                const unsigned next = nx4[q];
+                const unsigned cur = cu4[q];
                 diff = next ^ cur;
                 P.F[e] = diff;
                 if (diff) {
@@ -306,6 +363,7 @@ __device__ void ms_stage2(const MsParams &P, MsStage &st, int *grab, int *s_tot,
                     P.reach[u] += cnt;
                 }
             }
+          }
         }
         if (valid) {
             P.active[(size_t)ss * KW + w] = A;
