@@ -148,7 +148,8 @@ def algorithmic_bytes(log, n: int, reached: int, sigma: int = 8, tau: int = 128)
         each probed vertex and 4 B per further in-neighbour id read;
       every newly visited vertex: its level (4 B) and its degree (4 B);
       init: 4 B per vertex of levels and 5 bitvectors (20 B per 32 vertices).
-    The caller adds 8 B per vertex for the un-permute of a reordered graph."""
+    The caller adds 12 B per vertex for the un-permute of a reordered graph
+    (permutation entry, the gathered level, the stored level)."""
     W = (n + 31) // 32
     per_vss = 4.0 * tau + 4.0 * tau / (32 // sigma) + 8.0 + sigma / 8.0
     b = 4.0 * n + 20.0 * W + 8.0 * reached
@@ -454,7 +455,7 @@ def main():
         logs = results["tuned"][2][r.name]
         ti = r.h_tuned.info()
         gb = sum(algorithmic_bytes(lg, r.g.n, rc, ti["sigma"], ti["tau"]) +
-                 (8.0 * r.g.n if r.info["reorder"] else 0.0) for lg, rc in zip(logs, r.reached))
+                 (12.0 * r.g.n if r.info["reorder"] else 0.0) for lg, rc in zip(logs, r.reached))
         gs = float(results["tuned"][0][r.name].mean(axis=0).sum()) * 1e-3
         alg_b += gb
         dev_s += gs

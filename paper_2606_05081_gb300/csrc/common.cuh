@@ -36,8 +36,6 @@ __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long
     return v;
 }
 __device__ __forceinline__ int ld_volatile_i32(const int *p) { return *(volatile const int *)p; }
-__device__ __forceinline__ unsigned ld_volatile_u32(const unsigned *p) { return *(volatile const unsigned *)p; }
-__device__ __forceinline__ long long ld_volatile_i64(const long long *p) { return *(volatile const long long *)p; }
 
 // Fire-and-forget atomic OR (the return value is never consumed, so the
 // memory system may complete it asynchronously: §5.2).
@@ -118,9 +116,4 @@ __device__ __forceinline__ bool grid_barrier(Ctl *ctl, unsigned &epoch, uint64_t
     }
     __syncthreads();
     return s_ok != 0;
-}
-
-// Byte view helpers for sigma = 8 frontier words.
-__device__ __forceinline__ unsigned ld_byte(const unsigned *words, int idx) {
-    return (unsigned)reinterpret_cast<const unsigned char *>(words)[idx];
 }
