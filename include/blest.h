@@ -114,6 +114,9 @@ typedef struct blest_info {
     int64_t device_bytes;    /* device memory held by the handle */
     int32_t tau;             /* slices per VSS */
     int32_t vss_batch;       /* VSS passes a warp keeps in flight (launch setting) */
+    int32_t policy;          /* blest_policy in force */
+    int32_t engine_tc;       /* 1: the rule and fixed policies run the b1-MMA hit test of Fig. 3 */
+    int32_t model_loaded;    /* 1 once MLP weights are loaded; without them LEARNED falls back to the rule */
 } blest_info;
 
 /* One record per BFS level of the last single-source BFS. */

@@ -62,7 +62,8 @@ class Info(ctypes.Structure):
                 ("switching", ctypes.c_int32), ("reorder", ctypes.c_int32), ("sigma", ctypes.c_int32),
                 ("grid_blocks", ctypes.c_int32), ("block_threads", ctypes.c_int32),
                 ("build_ms", ctypes.c_double), ("device_bytes", ctypes.c_int64), ("tau", ctypes.c_int32),
-                ("vss_batch", ctypes.c_int32)]
+                ("vss_batch", ctypes.c_int32), ("policy", ctypes.c_int32), ("engine_tc", ctypes.c_int32),
+                ("model_loaded", ctypes.c_int32)]
 
 
 class LevelLog(ctypes.Structure):

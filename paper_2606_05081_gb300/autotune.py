@@ -6,7 +6,9 @@ the caller keeps disjoint from the ones it measures:
 * ``autotune(h, ...)`` tunes the launch of one handle: CTA size (256, 512,
   1024 threads), VSS passes a warp keeps in flight in top-down levels
   (1, 2, 4) and, on the sigma = 8, tau = 128 layout only, the top-down
-  hit-test engine (b1 MMA of Fig. 3 or CUDA cores);
+  hit-test engine (b1 MMA of Fig. 3 or CUDA cores) -- unless the handle
+  runs the learned policy with weights loaded, which picks the engine per
+  level itself, so the engine setting would not change what runs;
 * ``autotune_layout(build, ...)`` builds the graph once per BVSS layout --
   slice width sigma in {8, 16, 32} with its warp-wide VSS (tau = 32 *
   32 / sigma), plus the narrow tau = 32 VSS at sigma = 8 -- tunes each
@@ -15,6 +17,8 @@ the caller keeps disjoint from the ones it measures:
 from __future__ import annotations
 
 import itertools
+
+from . import POLICY_LEARNED
 
 BLOCKS = (256, 512, 1024)
 BATCHES = (1, 2, 4)
@@ -28,7 +32,8 @@ def autotune(h, sources, reps: int = 2, stream=None):
     s = stream if stream is not None else torch.cuda.Stream(dev)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     info = h.info()
-    engines = (False, True) if (info["sigma"], info["tau"]) == (8, 128) else (False,)
+    learned = info["policy"] == POLICY_LEARNED and info["model_loaded"]
+    engines = (False, True) if (info["sigma"], info["tau"]) == (8, 128) and not learned else (bool(info["engine_tc"]),)
     results = []
     with torch.cuda.stream(s):
         h.set_stream(s.cuda_stream, True)

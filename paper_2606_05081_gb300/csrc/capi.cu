@@ -314,6 +314,9 @@ extern "C" blest_status blest_get_info(blest_handle h, blest_info *info) {
     info->block_threads = h->block;
     info->build_ms = h->build_ms;
     info->device_bytes = h->device_bytes;
+    info->policy = h->policy;
+    info->engine_tc = h->engine_tc;
+    info->model_loaded = h->d_mlp != nullptr;
     return BLEST_OK;
 }
 

@@ -78,3 +78,31 @@ def test_mlp_buffer_shapes_checked_before_the_c_call():
     for c in range(b.NUM_CHOICES):
         m, k = b.choice_mode_batch(c)
         assert b.choice_of(m, k) == c
+
+
+def test_ctypes_structs_match_the_header_layout(tmp_path):
+    """Every struct of the boundary has the same size and field offsets in
+    the C header (compiled by gcc) as in the ctypes binding."""
+    import ctypes
+
+    import paper_2606_05081_gb300 as blest
+    pairs = {"blest_build_opts": blest.BuildOpts, "blest_info": blest.Info,
+             "blest_level_log": blest.LevelLog, "blest_bvss_view": blest.BvssView}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "blest.h"', 'int main(void) {']
+    for cname, cls in pairs.items():
+        lines.append(f'printf("{cname} sizeof %zu\\n", sizeof({cname}));')
+        for f, _ in cls._fields_:
+            lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines.append('return 0; }')
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for ln in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines():
+        s, f, v = ln.split()
+        got[(s, f)] = int(v)
+    for cname, cls in pairs.items():
+        assert got[(cname, "sizeof")] == ctypes.sizeof(cls), cname
+        for f, _ in cls._fields_:
+            assert got[(cname, f)] == getattr(cls, f).offset, (cname, f)

@@ -127,3 +127,17 @@ def test_held_out_families_sampled_sources(blest, family):
         g = gg.rgg(1 << 24, 10.0, seed=27)
     with blest.build_graph(g) as h:
         _check_sources(blest, h, g, gg.sources(g, 64, 5)[:2])
+
+
+def test_closeness_lattice2048_first_row_closed_form(blest):
+    """Unperturbed 2048 x 2048 lattice, sources = row 0 (ids 0..2047, two
+    batches of 1024): the distance sum to (r, c) is sum over c' of
+    r + |c - c'| = 2048 r + c(c+1)/2 + (2047-c)(2048-c)/2, for every vertex."""
+    R = C = 2048
+    g = gg.lattice(R, C)
+    with blest.build_graph(g) as h:
+        far, reach = h.closeness_range(0, C)
+    r, c = np.divmod(np.arange(R * C, dtype=np.int64), C)
+    expect = C * r + c * (c + 1) // 2 + (C - 1 - c) * (C - c) // 2
+    assert np.array_equal(far, expect)
+    assert np.all(reach == C)
