@@ -196,6 +196,20 @@ def measured_traffic(runs_layouts):
     return float(np.mean(vals))
 
 
+def nvtx_range(name=None):
+    """Open (name) or close (None) an NVTX range around a timed region, so a
+    profiler can select exactly its launches (ncu --nvtx --nvtx-include
+    "timed_tuned/"); a no-op where NVTX is unavailable."""
+    try:
+        import torch
+        if name is None:
+            torch.cuda.nvtx.range_pop()
+        else:
+            torch.cuda.nvtx.range_push(name)
+    except Exception:
+        pass
+
+
 def harmonic(x):
     x = np.asarray(x, np.float64)
     return float(len(x) / np.sum(1.0 / x))
@@ -409,6 +423,7 @@ def main():
             t0e, t1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             psm = {r.name: np.zeros((args.steps, len(r.srcs))) for r in runs}
             t0e.record(stream)
+            nvtx_range("timed_" + arm)
             for k in range(args.steps):
                 for r in runs:
                     r.step(set_arm(r, arm), True)
@@ -416,6 +431,7 @@ def main():
                 for r in runs:
                     for i in range(len(r.srcs)):
                         psm[r.name][k, i] = r.ev[i][0].elapsed_time(r.ev[i][1])
+            nvtx_range()
             t1e.record(stream)
             torch.cuda.synchronize()
             for r in runs:

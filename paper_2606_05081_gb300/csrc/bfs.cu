@@ -157,18 +157,16 @@ struct Stage {
 __device__ __forceinline__ void stage_flush(const BfsParams &P, Stage &st, int2 *Q, int *SQ, int slot) {
     const int lane = lane_id();
     __syncwarp();
-    if (st.qn) {
-        int base = 0;
-        if (lane == 0) base = atomicAdd(&P.ctl->qlen[slot], st.qn);
-        base = __shfl_sync(FULL_MASK, base, 0);
-        for (int k = lane; k < st.qn; k += 32) Q[base + k] = st.q[k];
+    // both reservations are issued before either is used: one round trip
+    int qb = 0, sb = 0;
+    if (lane == 0) {
+        if (st.qn) qb = atomicAdd(&P.ctl->qlen[slot], st.qn);
+        if (st.sqn) sb = atomicAdd(&P.ctl->sqlen[slot], st.sqn);
     }
-    if (st.sqn) {
-        int base = 0;
-        if (lane == 0) base = atomicAdd(&P.ctl->sqlen[slot], st.sqn);
-        base = __shfl_sync(FULL_MASK, base, 0);
-        for (int k = lane; k < st.sqn; k += 32) SQ[base + k] = st.sq[k];
-    }
+    qb = __shfl_sync(FULL_MASK, qb, 0);
+    sb = __shfl_sync(FULL_MASK, sb, 0);
+    for (int k = lane; k < st.qn; k += 32) Q[qb + k] = st.q[k];
+    for (int k = lane; k < st.sqn; k += 32) SQ[sb + k] = st.sq[k];
     __syncwarp();
     st.qn = 0;
     st.sqn = 0;
@@ -586,10 +584,12 @@ __device__ void bottom_up_level(const BfsParams &P, int *grab, BlkAcc *acc, int 
 }
 
 // --------------------------------------------------- stage 2 (finalize)
-// Algorithm 3 stage 2.  Lane = word for the V_curr / V_next sweep and the
-// F writes; then, word by word over the words that changed, lane = vertex
-// for the level stores and degree loads, so both are coalesced.  A word
-// holds theta = 32/SIGMA slice-set fields; a changed field enqueues its set.
+// Algorithm 3 stage 2.  Lane = word for the V_curr / V_next sweep, the F
+// writes and the enqueue; a word with at most four new vertices stores their
+// levels and loads their out-degrees from its own lane, a denser word is
+// stored lane = vertex, eight words per round, so those stores coalesce.  A
+// word holds theta = 32/SIGMA slice-set fields; a changed field enqueues its
+// set.
 template <int SIGMA>
 __device__ void finalize_level(const BfsParams &P, Stage &st, int *grab, BlkAcc *acc, int ell, int bn, int slot) {
     constexpr int THETA = 32 / SIGMA;
@@ -614,6 +614,7 @@ __device__ void finalize_level(const BfsParams &P, Stage &st, int *grab, BlkAcc 
           const int tt = (i + g2 * half) * 32 + lane;
           nx[g2] = tt < P.W ? P.Vn[tt] : 0u;
           cu[g2] = tt < P.W ? P.Vc[tt] : 0u;
+
       }
 #pragma unroll 1
       for (int g2 = 0; g2 < 2; ++g2) {
@@ -628,8 +629,8 @@ __device__ void finalize_level(const BfsParams &P, Stage &st, int *grab, BlkAcc 
                 nv += (unsigned long long)__popc(diff);
             }
         }
-        // the VSS ranges of the changed slice-set fields load while the level
-        // stores and degree loads below are in flight
+        // the VSS ranges of the changed slice-set fields load together with the
+        // degrees below
         unsigned want = 0;
         int sso[4] = {0, 0, 0, 0}, ra[4] = {0, 0, 0, 0}, rl[4] = {0, 0, 0, 0};
 #pragma unroll
@@ -641,9 +642,26 @@ __device__ void finalize_level(const BfsParams &P, Stage &st, int *grab, BlkAcc 
                 rl[c] = __ldg(&P.realPtrs[sso[c] + 1]);
             }
         }
-        // out-degrees of the word's new vertices: lane = word, one 16-byte load
-        // per group of four vertices holding a new one, all in flight together
-        if (diff) {
+        // a sparse word (at most four new vertices): level stores and degree
+        // loads from its own lane, the degrees summed only after the enqueue
+        // below, so their latency overlaps it
+        const int pc = __popc(diff);
+        int dv[4] = {0, 0, 0, 0};
+        if (pc > 0 && pc <= 4) {
+            unsigned d = diff;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (d) {
+                    const int v = t * 32 + __ffs(d) - 1;
+                    d &= d - 1u;
+                    dv[q] = __ldg(&P.deg[v]);
+                    P.L[v] = ell;
+                }
+            }
+        }
+        // a dense word: one 16-byte degree load per group of four vertices
+        // holding a new one, all in flight together
+        if (pc > 4) {
             const int4 *dq = reinterpret_cast<const int4 *>(P.deg) + (size_t)t * 8;
             unsigned long long dsum = 0;
 #pragma unroll
@@ -651,31 +669,20 @@ __device__ void finalize_level(const BfsParams &P, Stage &st, int *grab, BlkAcc 
                 const unsigned nib = (diff >> (4 * q)) & 0xFu;
                 if (nib) {
                     const int v0 = t * 32 + 4 * q;
-                    int4 d;
+                    int4 dd;
                     if (v0 + 4 <= P.n) {
-                        d = __ldg(dq + q);
+                        dd = __ldg(dq + q);
                     } else {   // the last, partial word: no load past vertex n - 1
-                        d.x = __ldg(&P.deg[v0]);
-                        d.y = v0 + 1 < P.n ? __ldg(&P.deg[v0 + 1]) : 0;
-                        d.z = v0 + 2 < P.n ? __ldg(&P.deg[v0 + 2]) : 0;
-                        d.w = v0 + 3 < P.n ? __ldg(&P.deg[v0 + 3]) : 0;
+                        dd.x = __ldg(&P.deg[v0]);
+                        dd.y = v0 + 1 < P.n ? __ldg(&P.deg[v0 + 1]) : 0;
+                        dd.z = v0 + 2 < P.n ? __ldg(&P.deg[v0 + 2]) : 0;
+                        dd.w = v0 + 3 < P.n ? __ldg(&P.deg[v0 + 3]) : 0;
                     }
-                    dsum += (unsigned long long)((nib & 1u ? d.x : 0) + (nib & 2u ? d.y : 0) +
-                                                 (nib & 4u ? d.z : 0) + (nib & 8u ? d.w : 0));
+                    dsum += (unsigned long long)((nib & 1u ? dd.x : 0) + (nib & 2u ? dd.y : 0) +
+                                                 (nib & 4u ? dd.z : 0) + (nib & 8u ? dd.w : 0));
                 }
             }
             fe += dsum;
-        }
-        // level stores: a word with few new vertices is stored by its own lane;
-        // dense words go lane = vertex, eight words per round, so stores coalesce
-        const int pc = __popc(diff);
-        if (pc > 0 && pc <= 4) {
-            unsigned d = diff;
-            while (d) {
-                const int bit = __ffs(d) - 1;
-                d &= d - 1u;
-                P.L[t * 32 + bit] = ell;
-            }
         }
         const unsigned dense = __ballot_sync(FULL_MASK, pc > 4);
         if (dense) {
@@ -693,6 +700,7 @@ __device__ void finalize_level(const BfsParams &P, Stage &st, int *grab, BlkAcc 
 #pragma unroll
         for (int c = 0; c < 4; ++c) rl[c] -= ra[c];
         enqueue_ranges(P, st, want, sso, ra, rl, P.Q[bn], P.SQ[bn], slot);
+        fe += (unsigned long long)(dv[0] + dv[1]) + (unsigned long long)(dv[2] + dv[3]);
       }
     }
     block_flush(P, st, acc, P.Q[bn], P.SQ[bn], slot, nv, fe);
