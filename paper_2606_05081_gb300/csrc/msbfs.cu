@@ -214,15 +214,25 @@ __device__ __forceinline__ unsigned group_bits(unsigned x) {
     }
 }
 
+// Per-warp table of subset ORs of a slice set's frontier words: entry e < 16
+// is the OR of the words of its vertices j < 4 with bit j of e set, entry
+// 16 + e the same for vertices 4 + j.  Stored entry-major ([e][lane]), so a
+// warp reading one entry per lane hits 32 distinct banks whatever entries
+// the lanes pick.  A slot's hit word is then two loads and one OR instead of
+// eight mask-selected ORs.
+constexpr int MS_TAB = 32;
+constexpr size_t MS_TAB_BYTES = (size_t)(MS_BLOCK / 32) * MS_TAB * 32 * sizeof(unsigned);
+
 template <int KW>
 __device__ void ms_stage1(const MsParams &P, MsStage &st, int *grab, int *s_tot, int qlen, const int *Qc, int dl,
-                          int *s_rows, unsigned char *s_m) {
+                          int *s_rows, unsigned char *s_m, unsigned *s_tab) {
     constexpr int G = 32 / KW;
     const int lane = lane_id();
     const int g = lane / KW, w = lane % KW;
     const int wib = threadIdx.x >> 5;
     int *rows = s_rows + wib * 128;
     unsigned char *m8s = s_m + wib * 128;
+    unsigned *tab = s_tab + (size_t)wib * MS_TAB * 32 + lane;   // this lane's column
     // queue entries interleaved over the blocks, claimed by the block's warps
     for (;;) {
         int kc = 0;
@@ -252,6 +262,16 @@ __device__ void ms_stage1(const MsParams &P, MsStage &st, int *grab, int *s_tot,
         unsigned f[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) f[j] = aw ? P.F[(size_t)get_vi(ss * 8 + j, P.rho) * KW + w] : 0u;
+        // each lane writes and reads only its own column: no warp sync needed
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            unsigned v[16];
+            v[0] = 0u;
+#pragma unroll
+            for (int e = 1; e < 16; ++e) v[e] = v[e & (e - 1)] | f[4 * h + ((e & 1) ? 0 : (e & 2) ? 1 : (e & 4) ? 2 : 3)];
+#pragma unroll
+            for (int e = 0; e < 16; ++e) tab[(16 * h + e) * 32] = v[e];
+        }
         __syncwarp();
         // slots with a hit (bit s of hm[s / 32]); their slice sets are marked
         // dirty after the loop, 32 slots at a time, so the loop never waits on
@@ -261,9 +281,7 @@ __device__ void ms_stage1(const MsParams &P, MsStage &st, int *grab, int *s_tot,
         for (int t = 0; t < (nslots + G - 1) / G; ++t) {
             const int kk = t * G + g;
             const unsigned m8 = m8s[kk];
-            unsigned hit = 0;
-#pragma unroll
-            for (int j = 0; j < 8; ++j) hit |= (m8 >> j & 1u) ? f[j] : 0u;
+            const unsigned hit = tab[(m8 & 15u) * 32] | tab[(16u + (m8 >> 4)) * 32];
             const int u = rows[kk];
             if (hit) red_or(&P.Vn[(size_t)get_vi(u, P.rho) * KW + w], hit);
             const unsigned bal = __ballot_sync(FULL_MASK, hit != 0);
@@ -382,6 +400,7 @@ __global__ void __launch_bounds__(MS_BLOCK, 2) k_msbfs(MsParams P) {
     __shared__ int s_rows[(MS_BLOCK / 32) * 128];
     __shared__ unsigned char s_m[(MS_BLOCK / 32) * 128];
     __shared__ int s_stg[(MS_BLOCK / 32) * 2 * MS_STG];
+    extern __shared__ unsigned s_tab[];   // MS_TAB_BYTES: the warps' subset-OR tables
     __shared__ int s_grab[2];
     __shared__ int s_tot[2][2];   // per stage: the CTA's staged total and its reserved base
     MsStage st;
@@ -460,7 +479,7 @@ __global__ void __launch_bounds__(MS_BLOCK, 2) k_msbfs(MsParams P) {
         __syncthreads();
         if (qlen == 0) break;
         if (tid == 0) ctl->qlen[qn] = 0;
-        ms_stage1<KW>(P, st, &s_grab[0], s_tot[0], qlen, P.Q[qc], dl, s_rows, s_m);
+        ms_stage1<KW>(P, st, &s_grab[0], s_tot[0], qlen, P.Q[qc], dl, s_rows, s_m, s_tab);
         if (!ms_barrier(ctl, epoch, P.budget_ns)) return;
         if (threadIdx.x == 0) s_cnt = ld_volatile_i32(&ctl->dlen[dl]);
         __syncthreads();
@@ -491,7 +510,10 @@ int ms_grid() {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_msbfs<KW>, MS_BLOCK, 0);
+    if (cudaFuncSetAttribute(k_msbfs<KW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MS_TAB_BYTES) !=
+        cudaSuccess)
+        return 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_msbfs<KW>, MS_BLOCK, MS_TAB_BYTES);
     return per * sms;
 }
 
@@ -596,7 +618,7 @@ static blest_status ms_launch(blest_graph *h, int k, int *levels_dev, long long 
     if (cudaMemsetAsync(m->ctl, 0, sizeof(MsCtl), h->stream) != cudaSuccess) return BLEST_ERR_CUDA;
     void *args[] = {&P};
     const void *fn = m->KW == 2 ? (const void *)k_msbfs<2> : (m->KW == 8 ? (const void *)k_msbfs<8> : (const void *)k_msbfs<32>);
-    cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(m->grid), dim3(MS_BLOCK), args, 0, h->stream);
+    cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(m->grid), dim3(MS_BLOCK), args, MS_TAB_BYTES, h->stream);
     if (e != cudaSuccess) {
         blest_internal_record_cuda_error(e, "cudaLaunchCooperativeKernel(k_msbfs)", __FILE__, __LINE__);
         return BLEST_ERR_CUDA;
