@@ -250,14 +250,12 @@ __device__ void ms_stage1(const MsParams &P, MsStage &st, int *grab, int *s_tot,
         const unsigned words = __ballot_sync(FULL_MASK, m != 0);
         const int nslots = words ? 4 * (32 - __clz(words)) : 0;
         __syncwarp();
-        rows[lane * 4 + 0] = r.x;
-        rows[lane * 4 + 1] = r.y;
-        rows[lane * 4 + 2] = r.z;
-        rows[lane * 4 + 3] = r.w;
-        m8s[lane * 4 + 0] = (unsigned char)(m & 0xFFu);
-        m8s[lane * 4 + 1] = (unsigned char)((m >> 8) & 0xFFu);
-        m8s[lane * 4 + 2] = (unsigned char)((m >> 16) & 0xFFu);
-        m8s[lane * 4 + 3] = (unsigned char)(m >> 24);
+        // slot 4l + i: the bit-array element index of its row (the slice set
+        // of the row, for the dirty claims, is that index mod rho) and its
+        // 8-bit slice mask (byte i of the lane word, little-endian)
+        reinterpret_cast<int4 *>(rows)[lane] =
+            make_int4(get_vi(r.x, P.rho), get_vi(r.y, P.rho), get_vi(r.z, P.rho), get_vi(r.w, P.rho));
+        reinterpret_cast<unsigned *>(m8s)[lane] = m;
         const unsigned aw = P.active[(size_t)ss * KW + w];
         unsigned f[8];
 #pragma unroll
@@ -277,24 +275,24 @@ __device__ void ms_stage1(const MsParams &P, MsStage &st, int *grab, int *s_tot,
         // dirty after the loop, 32 slots at a time, so the loop never waits on
         // the dirty flags
         unsigned hm0 = 0, hm1 = 0, hm2 = 0, hm3 = 0;
+        const int nt = (nslots + G - 1) / G;
+        for (int c0 = 0; c0 < nslots; c0 += 32) {   // chunks of 32 slots (warp-uniform)
+            unsigned hm = 0;
+            const int t1 = min(nt, (c0 + 32) / G);
 #pragma unroll 2
-        for (int t = 0; t < (nslots + G - 1) / G; ++t) {
-            const int kk = t * G + g;
-            const unsigned m8 = m8s[kk];
-            const unsigned hit = tab[(m8 & 15u) * 32] | tab[(16u + (m8 >> 4)) * 32];
-            const int u = rows[kk];
-            if (hit) red_or(&P.Vn[(size_t)get_vi(u, P.rho) * KW + w], hit);
-            const unsigned bal = __ballot_sync(FULL_MASK, hit != 0);
-            // one bit per group (any of its KW lanes hit), packed: slots t*G .. t*G+G-1
-            const unsigned gb = group_bits<KW>(bal);
-            if (gb) {
-                const int s0 = t * G;                       // G divides 32: one word holds them
-                const unsigned bits = gb << (s0 & 31);
-                if (s0 < 32) hm0 |= bits;
-                else if (s0 < 64) hm1 |= bits;
-                else if (s0 < 96) hm2 |= bits;
-                else hm3 |= bits;
+            for (int t = c0 / G; t < t1; ++t) {
+                const int kk = t * G + g;
+                const unsigned m8 = m8s[kk];
+                const unsigned hit = tab[(m8 & 15u) * 32] | tab[(16u + (m8 >> 4)) * 32];
+                if (hit) red_or(&P.Vn[(size_t)rows[kk] * KW + w], hit);
+                // one bit per group (any of its KW lanes hit): slots t*G .. t*G+G-1,
+                // G divides 32, so they sit in this chunk's word
+                hm |= group_bits<KW>(__ballot_sync(FULL_MASK, hit != 0)) << ((t * G) & 31);
             }
+            if (c0 == 0) hm0 = hm;
+            else if (c0 == 32) hm1 = hm;
+            else if (c0 == 64) hm2 = hm;
+            else hm3 = hm;
         }
 #pragma unroll
         for (int r4 = 0; r4 < 4; ++r4) {
@@ -303,7 +301,7 @@ __device__ void ms_stage1(const MsParams &P, MsStage &st, int *grab, int *s_tot,
             bool claimed = false;
             int so = 0;
             if (hm >> lane & 1u) {
-                so = rows[32 * r4 + lane] >> 3;
+                so = rows[32 * r4 + lane] % P.rho;
                 claimed = ld_volatile_i32(&P.dirty[so]) == 0 && atomicExch(&P.dirty[so], 1) == 0;
             }
             ms_mark_dirty(P, st, claimed, so, dl);
@@ -397,8 +395,8 @@ __device__ void ms_stage2(const MsParams &P, MsStage &st, int *grab, int *s_tot,
 // two 512-thread CTAs per SM (64 registers a thread)
 template <int KW>
 __global__ void __launch_bounds__(MS_BLOCK, 2) k_msbfs(MsParams P) {
-    __shared__ int s_rows[(MS_BLOCK / 32) * 128];
-    __shared__ unsigned char s_m[(MS_BLOCK / 32) * 128];
+    __shared__ __align__(16) int s_rows[(MS_BLOCK / 32) * 128];
+    __shared__ __align__(16) unsigned char s_m[(MS_BLOCK / 32) * 128];
     __shared__ int s_stg[(MS_BLOCK / 32) * 2 * MS_STG];
     extern __shared__ unsigned s_tab[];   // MS_TAB_BYTES: the warps' subset-OR tables
     __shared__ int s_grab[2];
