@@ -514,8 +514,9 @@ __device__ void bottom_up_level(const BfsParams &P, int *grab, BlkAcc *acc, int 
                 const int ej = __shfl_sync(FULL_MASK, excl, j);
                 u[k] = act[k] ? ((base + j) << 5) + nth_set_bit(uj, idx - ej) : 0;
             }
-            // round 1: the first four in-neighbours (rows sorted by descending
-            // degree) come from one coalesced 16-byte head load per vertex
+            // first probe: the first four in-neighbours (rows sorted by
+            // descending degree) come from one coalesced 16-byte head load per
+            // vertex
             int4 hd[2];
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
@@ -547,7 +548,7 @@ __device__ void bottom_up_level(const BfsParams &P, int *grab, BlkAcc *acc, int 
                     const int vq = pick(hd[k], q);
                     hit[k] |= (vq >= 0) && ((fw[k][q - 1] >> (vq & 31)) & 1u);
                 }
-            // rows longer than four: the rest of the row, four ids per round
+            // rows longer than four: the rest of the row, four ids per step
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
                 if (act[k] && !hit[k] && hd[k].w >= 0) {
@@ -983,7 +984,6 @@ __global__ void __launch_bounds__(BFS_MAX_THREADS, 1) k_bfs(BfsParams P) {
     }
 }
 
-// the kernel instance of a (sigma, tau) layout (nullptr for other pairs)
 // the kernel instance of a (sigma, tau) layout (nullptr for other pairs)
 const void *bfs_kernel_for(int sigma, int tau, int /*block*/) {
     if (sigma == 8 && tau == 128) return (const void *)k_bfs<8, 32>;
