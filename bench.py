@@ -332,6 +332,9 @@ def main():
     ap.add_argument("--sources", type=int, default=NUM_SOURCES)
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (tuned arm = default launch)")
     ap.add_argument("--levels", action="store_true", help="per-level log of the first source to stderr")
+    ap.add_argument("--ablation", action="store_true",
+                    help="also time the rungs between the plain and the tuned arm: the paper's rule with the "
+                         "CUDA-core hit test on the default layout, then on the autotuned layout and launch")
     ap.add_argument("--tau", type=int, default=0, help="VSS width of the multi-source and closeness builds "
                     "(0 = 128)")
     ap.add_argument("--layout", default=None, help="sigma,tau of the tuned arm when the autotuner is off")
@@ -393,6 +396,11 @@ def main():
                 print(r.name, "level", json.dumps(rec), file=sys.stderr)
 
     arms = {"plain": (blest.POLICY_HEURISTIC, "default", True), "tuned": (tuned_policy, "tuned", None)}
+    if args.ablation:
+        arms = {"plain": arms["plain"],
+                "rule_cc": (blest.POLICY_HEURISTIC, "default", False),
+                "rule_cc_tuned": (blest.POLICY_HEURISTIC, "tuned", False),
+                "tuned": arms["tuned"]}
 
     def set_arm(r, arm):
         """The arm's handle, configured: plain = default layout and launch,
@@ -527,10 +535,19 @@ def main():
                      "kernel_sha": kernel_sha(), "per_graph": per_graph_roof},
         "e2e": {"value": e2e, "unit": "GTEPS", "h2d_bytes_per_step": 4 * sum(len(r.srcs) for r in runs),
                 "d2h_bytes_per_step": d2h},
-        "gpu_launches": args.steps * sum(len(r.srcs) for r in runs) * len(arms),
+        "gpu_launches": args.steps * sum(len(r.srcs) for r in runs),   # one k_bfs per BFS of the tuned arm
         "clocks": clk.summary(),
         "autotune": {k: {kk: vv for kk, vv in v.items() if kk != "tried"} for k, v in tune_info.items()},
     }
+    if args.ablation:
+        what = {"plain": "the paper's rule, b1 MMA hit test, sigma 8 / tau 128, 512-thread CTAs",
+                "rule_cc": "the paper's rule, CUDA-core hit test, sigma 8 / tau 128, 512-thread CTAs",
+                "rule_cc_tuned": "the paper's rule, CUDA-core hit test, autotuned layout and launch",
+                "tuned": "learned per-level policy, autotuned layout and launch"}
+        line["ablation"] = {}
+        for arm in arms:
+            v, per = gteps_of(results[arm][0])
+            line["ablation"][arm] = {"value": v, "per_graph": per, "what": what[arm]}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rates = []
         for r in runs:
