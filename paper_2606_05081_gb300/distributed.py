@@ -10,6 +10,8 @@ component-size normalisation) is then computed in fp64 on every rank.
 """
 from __future__ import annotations
 
+import os
+
 import numpy as np
 
 
@@ -47,3 +49,46 @@ def closeness_allreduce(partial, n: int, rank: int, world: int, dist=None, group
     nz = f > 0
     cc[nz] = (r[nz] - 1).astype(np.float64) / f[nz].astype(np.float64)
     return f, r, cc
+
+
+def closeness_checkpointed(partial, n: int, path: str, first: int = 0, count: int | None = None,
+                           chunk: int = 16 * 1024):
+    """All-source (or a source range's) distance sums, resumable.
+
+    Runs the sources [first, first + count) in chunks of `chunk` sources
+    through partial(first, count) -> (far, reach) (``Graph.closeness_range``
+    or any callable returning int64 n-vectors), adds each chunk into running
+    int64 sums and, after every chunk, saves the sums and the next source id
+    to `path` (written to a temporary file, then renamed, so a crash leaves
+    either the previous or the new checkpoint).  A call that finds `path`
+    resumes after its last completed chunk; a checkpoint of another n or
+    range raises ValueError.  Since far and reach are sums over sources, the
+    resumed result equals an uninterrupted run bit for bit.  Returns (far,
+    reach) as int64 numpy arrays; the checkpoint is left in place."""
+    if count is None:
+        count = n - first
+    if first < 0 or count < 0 or first + count > n:
+        raise ValueError("source range outside [0, n)")
+    if chunk <= 0:
+        raise ValueError("chunk must be positive")
+    end = first + count
+    far = np.zeros(n, np.int64)
+    reach = np.zeros(n, np.int64)
+    nxt = first
+    if os.path.exists(path):
+        with np.load(path) as ck:
+            if int(ck["n"]) != n or int(ck["first"]) != first or int(ck["end"]) != end:
+                raise ValueError(f"checkpoint {path} belongs to another graph or source range")
+            far[:] = ck["far"]
+            reach[:] = ck["reach"]
+            nxt = int(ck["next"])
+    while nxt < end:
+        c = min(chunk, end - nxt)
+        f, r = partial(nxt, c)
+        far += np.asarray(f.cpu() if hasattr(f, "cpu") else f, dtype=np.int64)
+        reach += np.asarray(r.cpu() if hasattr(r, "cpu") else r, dtype=np.int64)
+        nxt += c
+        tmp = path + ".tmp.npz"
+        np.savez(tmp, n=n, first=first, end=end, next=nxt, far=far, reach=reach)
+        os.replace(tmp, path)
+    return far, reach

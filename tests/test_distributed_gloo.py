@@ -1,7 +1,9 @@
 """The source-range split of closeness across processes, on CPU: two gloo
 ranks each sum the distances from their own sources (the oracle's serial
 BFS stands in for the GPU batches) and one all-reduce completes far, reach
-and cc, which must equal the single-process oracle exactly."""
+and cc, which must equal the single-process oracle exactly.  The resumable
+run is tested the same way: a failure injected on the host part-way through,
+then a rerun that must resume after the last saved chunk and end bit-exact."""
 import os
 import socket
 
@@ -80,3 +82,59 @@ def test_closeness_two_gloo_ranks_equal_single_process():
     for rank, far, reach, cc in res:
         assert np.array_equal(far, far_r) and np.array_equal(reach, reach_r), rank
         assert np.array_equal(cc, cc_r), rank
+
+
+class _Crash(RuntimeError):
+    pass
+
+
+def _counting(partial, fail_after=None):
+    """partial wrapped to record its calls and raise after `fail_after` of them."""
+    calls = []
+
+    def run(first, count):
+        if fail_after is not None and len(calls) == fail_after:
+            raise _Crash("injected failure")
+        calls.append((first, count))
+        return partial(first, count)
+    return run, calls
+
+
+def test_checkpointed_closeness_resumes_after_a_failure(tmp_path):
+    from paper_2606_05081_gb300.distributed import closeness_checkpointed
+    g = gg.disjoint_union(gg.rmat(9, seed=5), gg.path(300), gg.from_edges(3, [], [], True))
+    far_r, reach_r, _ = oracle.closeness(g)
+    path = str(tmp_path / "cc.npz")
+    run, calls = _counting(_partial_oracle(g), fail_after=2)
+    with pytest.raises(_Crash):
+        closeness_checkpointed(run, g.n, path, chunk=100)
+    assert calls == [(0, 100), (100, 100)]
+    with np.load(path) as ck:
+        assert int(ck["next"]) == 200
+    # the rerun starts after the last completed chunk and ends bit-exact
+    run2, calls2 = _counting(_partial_oracle(g))
+    far, reach = closeness_checkpointed(run2, g.n, path, chunk=100)
+    assert calls2[0] == (200, 100) and sum(c for _, c in calls2) == g.n - 200
+    assert np.array_equal(far, far_r) and np.array_equal(reach, reach_r)
+    # a finished checkpoint runs nothing more
+    run3, calls3 = _counting(_partial_oracle(g))
+    far3, reach3 = closeness_checkpointed(run3, g.n, path, chunk=100)
+    assert calls3 == [] and np.array_equal(far3, far_r) and np.array_equal(reach3, reach_r)
+
+
+def test_checkpointed_ranges_sum_to_the_whole_and_reject_foreign_checkpoints(tmp_path):
+    from paper_2606_05081_gb300.distributed import closeness_checkpointed, source_ranges
+    g = gg.rmat(10, seed=8)
+    far_r, reach_r, _ = oracle.closeness(g)
+    far = np.zeros(g.n, np.int64)
+    reach = np.zeros(g.n, np.int64)
+    for rank, (first, count) in enumerate(source_ranges(g.n, 3)):
+        f, r = closeness_checkpointed(_partial_oracle(g), g.n, str(tmp_path / f"r{rank}.npz"), first, count,
+                                      chunk=300)
+        far += f
+        reach += r
+    assert np.array_equal(far, far_r) and np.array_equal(reach, reach_r)
+    with pytest.raises(ValueError):   # rank 0's checkpoint, another range
+        closeness_checkpointed(_partial_oracle(g), g.n, str(tmp_path / "r0.npz"), 1, 10)
+    with pytest.raises(ValueError):
+        closeness_checkpointed(_partial_oracle(g), g.n, str(tmp_path / "x.npz"), 0, g.n + 1)
