@@ -97,6 +97,28 @@ def test_closeness_ranges_add_up(blest):
         assert r1[v] == int((d >= 0).sum())
 
 
+def test_closeness_checkpointed_resumes_on_the_gpu(blest, tmp_path):
+    """Chunks of 1500 sources (not a multiple of the 1024-lane batch), an
+    injected host failure after the first chunk, then a resumed run: equal to
+    the oracle's all-source sums."""
+    from paper_2606_05081_gb300.distributed import closeness_checkpointed
+    g = gg.disjoint_union(gg.rmat(12, seed=13), gg.path(500))
+    far_r, reach_r, _ = oracle.closeness(g)
+    path = str(tmp_path / "cc.npz")
+    with blest.build_graph(g) as h:
+        calls = []
+
+        def failing(first, count):
+            if calls:
+                raise RuntimeError("injected failure")
+            calls.append(first)
+            return h.closeness_range(first, count)
+        with pytest.raises(RuntimeError):
+            closeness_checkpointed(failing, g.n, path, chunk=1500)
+        far, reach = closeness_checkpointed(h.closeness_range, g.n, path, chunk=1500)
+    assert np.array_equal(far, far_r) and np.array_equal(reach, reach_r)
+
+
 def test_msbfs_rejects_bad_args(blest):
     g = gg.path(10)
     with blest.build_graph(g) as h:
