@@ -26,7 +26,7 @@ import time
 
 import numpy as np
 
-from . import (MLP_NW, NUM_CHOICES, POLICY_FIXED, POLICY_HEURISTIC, POLICY_LEARNED, Graph, choice_mode_batch,
+from . import (MLP_NW, NUM_CHOICES, POLICY_FIXED, POLICY_HEURISTIC, Graph, choice_mode_batch,
                choice_of, mlp_features, mlp_predict, mlp_train)
 
 HERE = os.path.dirname(os.path.abspath(__file__))
