@@ -16,6 +16,9 @@ Contents (each function cites the passage of the paper it restates):
   paper_frag_b          the fragB register layout of Fig. 3
   gteps_edges           the edge count used for TEPS (a reading; the paper
                         defines none)
+  classify (module)     the scale-free-like test of the §4.2 footnote
+  reorder (module)      RCM (§4.2) and JaccardWithWindows (Algorithm 1)
+  mlp (module)          the level-mode MLP, its loss, gradient and Adam
 Every function here is pinned by tests in ``tests/test_oracle_*.py`` against
 closed forms, library routines, brute force or values printed in the paper.
 """
