@@ -20,6 +20,11 @@ jaccard_with_windows: Algorithm 1 (§4.1), one window at a time, each step in
     nbrs(j) = out-neighbours of j (the nonzeros of column j of A); for the
     incremental update, the columns of row i are the in-neighbours of i,
     which equal the neighbours on an undirected graph.
+
+symmetrized: a directed graph is reordered through its symmetrised pattern
+    G + G^T (a reading: RCM is defined for symmetric patterns, and Algorithm
+    1's incremental update assumes the in- and out-neighbours coincide); the
+    orderings above then run on that graph unchanged.
 """
 from __future__ import annotations
 
@@ -175,3 +180,26 @@ def permute(g, new_of_old):
     out = gg.from_edges(g.n, p[src].astype(np.int32), p[g.col].astype(np.int32), symmetrize=False)
     out.directed = g.directed
     return out
+
+
+class _Csr:
+    """A plain CSR graph (n, row_ptr, col) for the oracle's own use."""
+
+    def __init__(self, n, row_ptr, col):
+        self.n, self.row_ptr, self.col, self.directed = n, row_ptr, col, False
+
+
+def symmetrized(g):
+    """G + G^T: every arc in both directions, duplicates and self loops
+    dropped, rows sorted."""
+    n = g.n
+    src = np.repeat(np.arange(n, dtype=np.int64), np.diff(g.row_ptr))
+    dst = g.col.astype(np.int64)
+    u = np.concatenate([src, dst])
+    v = np.concatenate([dst, src])
+    keep = u != v
+    key = np.unique(u[keep] * n + v[keep])
+    rows, cols = key // n, key % n
+    rp = np.zeros(n + 1, np.int64)
+    np.add.at(rp, rows + 1, 1)
+    return _Csr(n, np.cumsum(rp), cols.astype(np.int32))

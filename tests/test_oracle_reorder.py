@@ -113,3 +113,19 @@ def test_jaccard_compresses_vs_random_order():
     s_rand = oracle.bvss(gr, 8)["num_slices"]
     s_jacc = oracle.bvss(reorder.permute(gr, pj), 8)["num_slices"]
     assert s_jacc < 0.95 * s_rand
+
+
+def test_symmetrized_pattern():
+    import graphgen as gg
+    g = gg.from_edges(5, [0, 0, 1, 3, 4, 2], [1, 1, 2, 3, 2, 4], symmetrize=False)
+    s = reorder.symmetrized(g)
+    nb = [sorted(s.col[s.row_ptr[v]:s.row_ptr[v + 1]].tolist()) for v in range(5)]
+    assert nb == [[1], [0, 2], [1, 4], [], [2]]      # 3->3 dropped, 0->1 once, 2<->4 once
+    # an undirected graph is its own symmetrised pattern
+    u = gg.rmat(9, seed=4)
+    su = reorder.symmetrized(u)
+    assert np.array_equal(su.row_ptr, u.row_ptr) and np.array_equal(su.col, u.col)
+    # on a directed graph, RCM of the pattern is a permutation
+    d = gg.er(300, 900, seed=2, directed=True)
+    p = reorder.rcm(reorder.symmetrized(d))
+    assert np.array_equal(np.sort(p), np.arange(300))
