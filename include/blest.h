@@ -52,7 +52,9 @@ typedef enum {
     BLEST_ERR_INTERNAL = 6     /* a device-side consistency check failed */
 } blest_status;
 
-/* Vertex reordering applied by blest_build (§4). */
+/* Vertex reordering applied by blest_build (§4).  On a directed graph the
+ * ordering is computed on its symmetrised pattern G + G^T (RCM is defined for
+ * symmetric patterns); the permutation changes speed, never levels. */
 enum {
     BLEST_REORDER_NONE = 0,
     BLEST_REORDER_RCM = 1,      /* reverse Cuthill-McKee (§4.2) */
@@ -301,14 +303,22 @@ blest_status blest_mlp_predict(const float *weights, const float *features, int6
  * is a static array of the library's device image that every GPU loading
  * the library holds until the process exits.
  *  - Limits: n <= 1,048,576 vertices and num_vss <= 131,072; larger graphs
- *    return BLEST_ERR_UNSUPPORTED.
+ *    return BLEST_ERR_UNSUPPORTED.  The BVSS must have the sigma = 8,
+ *    tau = 128 layout (the view's sigma and tau fields say so; any other
+ *    layout returns BLEST_ERR_UNSUPPORTED).
+ *  - Vertex ids are those of the BVSS: for a handle built with reordering,
+ *    blest_get_bvss returns the reordered graph, so `source`, `out_degree`
+ *    and the levels written are in the reordered numbering (map them with
+ *    blest_get_perm: reordered id = new_of_old[original id]).
  *  - The first call on each device looks up the array's device address with
  *    that device current; make that first call before any stream capture.
+ *    That set-up is guarded by a lock, so first calls may come from several
+ *    host threads.
  *  - All calls share the scratch array: calls that overlap on the GPU (other
  *    streams or host threads) race.  Each call clears what must start at zero.
- *  - levels must be device memory (n int32); the call is synchronous on
- *    `stream` (a cudaStream_t, NULL = the legacy default stream) and returns
- *    the device status. */
+ *  - levels must be device memory (n int32).  The call is synchronous: it
+ *    launches on `stream` (a cudaStream_t, NULL = the legacy default stream),
+ *    waits for that stream and returns the device status. */
 typedef struct blest_bvss_view {
     int64_t n;                       /* vertices */
     int64_t num_slice_sets;          /* N_s = ceil(n / 8): sigma = 8, tau = 128 layout only */
@@ -319,9 +329,44 @@ typedef struct blest_bvss_view {
     const int32_t *virtual_to_real;  /* device, N_v */
     const int32_t *out_degree;       /* device, n out-degrees (per-level counters) */
     int32_t engine_tc;               /* 1: b1 MMA hit test, 0: CUDA cores */
+    int32_t sigma;                   /* slice width of the BVSS: must be 8 */
+    int32_t tau;                     /* slices per VSS: must be 128 */
 } blest_bvss_view;
 
 blest_status blest_bfs_noalloc(const blest_bvss_view *g, int32_t source, int32_t *levels, void *stream);
+
+/* ---- Scale-free-like test (§4.2 footnote) --------------------------------
+ * The test BLEST_REORDER_AUTO applies to choose JaccardWithWindows (scale-
+ * free-like) or RCM.  A degree distribution is heavy-tailed when (a) the top
+ * 1 % of vertices hold at least 5 % and the top 10 % at least 40 % of the
+ * total degree, or (b) a least-squares line through the log-log degree
+ * histogram over the degrees k >= 5 has slope -gamma with R^2 >= 0.70 and
+ * gamma in [1, 5]; a graph is scale-free-like when its out- or in-degree
+ * distribution is.  Readings: "top p %" = floor(p n / 100) vertices, at
+ * least one; the fit takes every k >= 5 with at least one vertex,
+ * unweighted, and fails with fewer than two such k (gamma = R^2 = NaN). */
+typedef struct blest_degree_report {
+    double top1;          /* share of the total degree held by the top 1 % */
+    double top10;         /* share held by the top 10 % */
+    double gamma;         /* minus the slope of the log-log histogram fit (NaN: no fit) */
+    double r2;            /* R^2 of that fit (NaN: no fit) */
+    int32_t points;       /* degrees k >= 5 present (fit points) */
+    int32_t concentrated; /* test (a) */
+    int32_t powerlaw;     /* test (b) */
+    int32_t heavy;        /* (a) or (b) */
+} blest_degree_report;
+
+typedef struct blest_scale_free_report {
+    blest_degree_report out_deg;
+    blest_degree_report in_deg;   /* equals out_deg when in_deg was NULL */
+    int32_t scale_free;           /* out_deg.heavy or in_deg.heavy */
+} blest_scale_free_report;
+
+/* Run the test on caller degree arrays (n int32 each, host or device;
+ * in_deg NULL for an undirected graph).  The histogram is built on the GPU.
+ * INVALID for n < 1, n >= 2^31 or a negative degree. */
+blest_status blest_scale_free_test(const int32_t *out_deg, const int32_t *in_deg, int64_t n,
+                                   blest_scale_free_report *out);
 
 /* Test hook for the timed-out grid barrier: launches a cooperative kernel in
  * which one block waits on a barrier no other block joins.  Returns

@@ -79,7 +79,19 @@ class BvssView(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("num_slice_sets", ctypes.c_int64), ("num_vss", ctypes.c_int64),
                 ("row_ids", ctypes.c_void_p), ("masks", ctypes.c_void_p), ("real_ptrs", ctypes.c_void_p),
                 ("virtual_to_real", ctypes.c_void_p), ("out_degree", ctypes.c_void_p),
-                ("engine_tc", ctypes.c_int32)]
+                ("engine_tc", ctypes.c_int32), ("sigma", ctypes.c_int32), ("tau", ctypes.c_int32)]
+
+
+class DegreeReport(ctypes.Structure):
+    """blest_degree_report: one degree distribution under the §4.2 footnote test."""
+    _fields_ = [("top1", ctypes.c_double), ("top10", ctypes.c_double), ("gamma", ctypes.c_double),
+                ("r2", ctypes.c_double), ("points", ctypes.c_int32), ("concentrated", ctypes.c_int32),
+                ("powerlaw", ctypes.c_int32), ("heavy", ctypes.c_int32)]
+
+
+class ScaleFreeReport(ctypes.Structure):
+    """blest_scale_free_report."""
+    _fields_ = [("out_deg", DegreeReport), ("in_deg", DegreeReport), ("scale_free", ctypes.c_int32)]
 
 
 _P = ctypes.c_void_p
@@ -109,6 +121,7 @@ _sigs = {
     "blest_status_string": (ctypes.c_char_p, [_S]),
     "blest_selftest_barrier_timeout": (_S, [ctypes.c_int32]),
     "blest_bfs_noalloc": (_S, [ctypes.POINTER(BvssView), ctypes.c_int32, _P, _P]),
+    "blest_scale_free_test": (_S, [_P, _P, ctypes.c_int64, ctypes.POINTER(ScaleFreeReport)]),
     "blest_mlp_features": (_S, [_P, ctypes.c_int64, ctypes.c_float, _P]),
     "blest_mlp_loss_grad": (_S, [_P, _P, _P, ctypes.c_int64, _P, _P, _P]),
     "blest_mlp_train": (_S, [_P, _P, _P, ctypes.c_int64, ctypes.c_int32, ctypes.c_float, ctypes.c_float, _P, _P]),
@@ -327,6 +340,26 @@ def build_many(batch, **opts) -> Graph:
 
 def selftest_barrier_timeout(timeout_ms: int = 20) -> int:
     return int(_lib.blest_selftest_barrier_timeout(int(timeout_ms)))
+
+
+def scale_free_test(out_deg, in_deg=None) -> dict:
+    """The §4.2 footnote's scale-free-like test on degree arrays (numpy or
+    torch, host or device; in_deg None for an undirected graph)."""
+    def arr(x):
+        if x is None:
+            return None
+        if hasattr(x, "data_ptr"):
+            import torch
+            return x.to(dtype=torch.int32).contiguous()
+        return np.ascontiguousarray(np.asarray(x), dtype=np.int32)
+    o, i = arr(out_deg), arr(in_deg)
+    rep = ScaleFreeReport()
+    _check(_lib.blest_scale_free_test(_ptr(o), _ptr(i) if i is not None else None, len(o), ctypes.byref(rep)),
+           "blest_scale_free_test")
+
+    def d(r):
+        return {f: getattr(r, f) for f, _ in DegreeReport._fields_}
+    return {"out": d(rep.out_deg), "in": d(rep.in_deg), "scale_free": bool(rep.scale_free)}
 
 
 def bfs_noalloc(view: BvssView, source: int, levels, stream=None):

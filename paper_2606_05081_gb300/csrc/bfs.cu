@@ -21,6 +21,7 @@
 // top-down eager level needs a single grid barrier and no O(n) clearing.
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 
 #include "handle.h"
 #include "mlp.h"
@@ -1154,10 +1155,13 @@ constexpr int NOALLOC_MAX_DEVICES = 64;
 unsigned char *g_noalloc_addr[NOALLOC_MAX_DEVICES];   // device address per device ordinal
 int g_noalloc_grid[NOALLOC_MAX_DEVICES];
 
+std::mutex g_noalloc_mu;   // guards the per-device set-up above
+
 // Once per device, with that device current: the host-side symbol is only a
 // stand-in, so look up the array's device address.
 blest_status noalloc_setup(int dev, unsigned char **base, int *grid) {
     if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return BLEST_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
     if (!g_noalloc_addr[dev]) {
         void *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
@@ -1183,6 +1187,8 @@ extern "C" blest_status blest_bfs_noalloc(const blest_bvss_view *g, int32_t sour
     if (!g || !levels || !g->row_ids || !g->masks || !g->real_ptrs || !g->virtual_to_real || !g->out_degree)
         return BLEST_ERR_INVALID;
     if (g->n < 1 || g->num_vss < 0 || g->num_slice_sets != (g->n + 7) / 8) return BLEST_ERR_INVALID;
+    // the kernel instance below reads rowIds at a stride of 128 per VSS
+    if (g->sigma != 8 || g->tau != 128) return BLEST_ERR_UNSUPPORTED;
     if (g->n > NOALLOC_MAX_N || g->num_vss > NOALLOC_MAX_NV) return BLEST_ERR_UNSUPPORTED;
     if (source < 0 || (int64_t)source >= g->n) return BLEST_ERR_INVALID;
     if (!is_device_ptr(levels)) return BLEST_ERR_INVALID;

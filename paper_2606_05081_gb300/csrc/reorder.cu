@@ -18,7 +18,9 @@
 //   index; the ratio inter / (|R| + deg - inter) is compared as exact 64-bit
 //   cross-products.
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
+#include <cstring>
 #include <vector>
 
 #include "prim.cuh"
@@ -62,6 +64,28 @@ __global__ void k_arc_keys(const long long *__restrict__ rp, const int *__restri
             const int i = col[p];
             keys[p] = ((int64_t)i == j) ? ~0ull : (((unsigned long long)j << B) | (unsigned long long)i);
         }
+}
+
+// both orientations of every arc (a directed graph's symmetrised pattern,
+// G + G^T, on which the orderings run): keys 2p and 2p + 1
+__global__ void k_arc_keys_sym(const long long *__restrict__ rp, const int *__restrict__ col, int64_t n, int B,
+                               unsigned long long *keys) {
+    const int lane = lane_id();
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t j = gw; j < n; j += nw)
+        for (long long p = rp[j] + lane; p < rp[j + 1]; p += 32) {
+            const int i = col[p];
+            const bool loop = (int64_t)i == j;
+            keys[2 * p] = loop ? ~0ull : (((unsigned long long)j << B) | (unsigned long long)i);
+            keys[2 * p + 1] = loop ? ~0ull : (((unsigned long long)i << B) | (unsigned long long)j);
+        }
+}
+
+// in-degrees of a duplicate-free CSR
+__global__ void k_in_degree(const int *__restrict__ col, int64_t m, int *indeg) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < m; p += stride) atomicAdd(&indeg[col[p]], 1);
 }
 
 __global__ void k_uniq_flags(const unsigned long long *__restrict__ k, int64_t m, int *flag) {
@@ -392,9 +416,12 @@ __global__ void k_window_keys(const int *__restrict__ deg, int64_t n, int W, uns
 }  // namespace
 
 // Clean CSR of the input (rows sorted, duplicates and self loops removed).
+// The duplicate- and loop-free CSR of (rp, col), rows sorted; sym: of its
+// symmetrised pattern (every arc in both directions).
 static blest_status clean_csr(cudaStream_t st, Tmp &T, const long long *rp, const int *col, int64_t n,
-                              int64_t nnz, long long **rp_out, int **col_out, int **deg_out) {
+                              int64_t nnz_in, long long **rp_out, int **col_out, int **deg_out, bool sym = false) {
     const int B = ceil_log2_i64(n) > 0 ? ceil_log2_i64(n) : 1;
+    const int64_t nnz = sym ? 2 * nnz_in : nnz_in;
     unsigned long long *k = T.get<unsigned long long>((size_t)nnz + 1);
     unsigned long long *ka = T.get<unsigned long long>((size_t)nnz + 1);
     long long *hist = T.get<long long>(radix_hist_elems(nnz));
@@ -407,7 +434,8 @@ static blest_status clean_csr(cudaStream_t st, Tmp &T, const long long *rp, cons
     long long *rp2 = T.get<long long>((size_t)n + 2);
     if (T.bad) return BLEST_ERR_OOM;
     cudaMemsetAsync(deg, 0, ((size_t)n + 1) * 4, st);
-    k_arc_keys<<<gridn(n * 32), TB, 0, st>>>(rp, col, n, B, k);
+    if (sym) k_arc_keys_sym<<<gridn(n * 32), TB, 0, st>>>(rp, col, n, B, k);
+    else k_arc_keys<<<gridn(n * 32), TB, 0, st>>>(rp, col, n, B, k);
     if (radix_sort_u64(k, nullptr, ka, nullptr, nnz, 2 * B + 1, hist, stmp, st) != cudaSuccess) return BLEST_ERR_CUDA;
     k_uniq_flags<<<gridn(nnz), TB, 0, st>>>(k, nnz, flag);
     if (scan_exclusive_i32_to_i64(flag, pos, nnz, stmp, st) != cudaSuccess) return BLEST_ERR_CUDA;
@@ -550,26 +578,145 @@ static blest_status jaccard_order(blest_graph *h, Tmp &T, const long long *rp, c
     return BLEST_OK;
 }
 
-// Scale-free-like test of the §4.2 footnote (degree concentration part):
-// the top 1% of vertices hold >= 5% and the top 10% hold >= 40% of the degree.
-static bool scale_free_like(const std::vector<int> &deg) {
-    std::vector<int> d(deg);
-    std::sort(d.begin(), d.end(), std::greater<int>());
-    long double tot = 0;
-    for (int x : d) tot += x;
-    if (tot <= 0) return false;
-    long double t1 = 0, t10 = 0;
-    const size_t n1 = std::max<size_t>(1, d.size() / 100), n10 = std::max<size_t>(1, d.size() / 10);
-    for (size_t i = 0; i < d.size(); ++i) {
-        if (i < n1) t1 += d[i];
-        if (i < n10) t10 += d[i];
+// ------------------------------------------------ scale-free-like test
+// The §4.2 footnote: a degree distribution is heavy-tailed when (a) the top
+// 1 % of vertices hold >= 5 % and the top 10 % >= 40 % of the total degree,
+// or (b) a least-squares line through the log-log degree histogram over
+// k >= 5 has slope -gamma with R^2 >= 0.70 and gamma in [1, 5].  The
+// histogram is built on the device; both tests read only the histogram
+// (the top-p % sums walk it from the highest degree down), so the host part
+// is O(max degree).  Top p % = floor(p n / 100) vertices, at least one; the
+// fit takes every k >= 5 with h(k) > 0, unweighted, and needs two points.
+
+__global__ void k_neg_check(const int *__restrict__ deg, int64_t n, int *bad) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
+        if (deg[v] < 0) atomicExch(bad, 1);
+}
+
+__global__ void k_deg_max(const int *__restrict__ deg, int64_t n, int *mx) {
+    int m = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) m = max(m, deg[v]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(FULL_MASK, m, o));
+    if (lane_id() == 0 && m) atomicMax(mx, m);
+}
+
+// hist[k] = #vertices of degree k; degrees below SMALL_BINS count in shared
+// memory first (most vertices of a skewed graph have small degrees, so
+// global atomics on those bins would serialise)
+constexpr int SMALL_BINS = 2048;
+__global__ void k_deg_hist(const int *__restrict__ deg, int64_t n, unsigned long long *hist) {
+    __shared__ unsigned sh[SMALL_BINS];
+    for (int i = threadIdx.x; i < SMALL_BINS; i += blockDim.x) sh[i] = 0;
+    __syncthreads();
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        const int d = deg[v];
+        if (d < SMALL_BINS) atomicAdd(&sh[d], 1u);
+        else atomicAdd(&hist[d], 1ull);
     }
-    return t1 / tot >= 0.05L && t10 / tot >= 0.40L;
+    __syncthreads();
+    for (int i = threadIdx.x; i < SMALL_BINS; i += blockDim.x)
+        if (sh[i]) atomicAdd(&hist[i], (unsigned long long)sh[i]);
+}
+
+static void report_from_hist(const std::vector<unsigned long long> &h, int64_t n, blest_degree_report *r) {
+    memset(r, 0, sizeof *r);
+    long long tot = 0;
+    for (size_t k = 0; k < h.size(); ++k) tot += (long long)k * (long long)h[k];
+    const long long n1 = std::max<long long>(1, n / 100), n10 = std::max<long long>(1, n / 10);
+    if (n > 0 && tot > 0) {
+        long long take1 = n1, take10 = n10, s1 = 0, s10 = 0;
+        for (size_t kk = h.size(); kk-- > 0;) {
+            const long long c = (long long)h[kk];
+            const long long a = std::min(c, take1), b = std::min(c, take10);
+            s1 += a * (long long)kk;
+            s10 += b * (long long)kk;
+            take1 -= a;
+            take10 -= b;
+            if (take10 == 0) break;
+        }
+        r->top1 = (double)s1 / (double)tot;
+        r->top10 = (double)s10 / (double)tot;
+    }
+    r->concentrated = (r->top1 >= 0.05 && r->top10 >= 0.40) ? 1 : 0;
+    // least squares of y = ln h(k) on x = ln k over k >= 5, h(k) > 0
+    std::vector<double> xs, ys;
+    for (size_t k = 5; k < h.size(); ++k)
+        if (h[k]) {
+            xs.push_back(std::log((double)k));
+            ys.push_back(std::log((double)h[k]));
+        }
+    r->points = (int32_t)xs.size();
+    r->gamma = NAN;
+    r->r2 = NAN;
+    if (xs.size() >= 2) {
+        double mx = 0, my = 0;
+        for (size_t i = 0; i < xs.size(); ++i) { mx += xs[i]; my += ys[i]; }
+        mx /= (double)xs.size();
+        my /= (double)xs.size();
+        double sxx = 0, sxy = 0, syy = 0;
+        for (size_t i = 0; i < xs.size(); ++i) {
+            sxx += (xs[i] - mx) * (xs[i] - mx);
+            sxy += (xs[i] - mx) * (ys[i] - my);
+            syy += (ys[i] - my) * (ys[i] - my);
+        }
+        if (sxx > 0) {
+            const double slope = sxy / sxx, icpt = my - slope * mx;
+            double ssr = 0;
+            for (size_t i = 0; i < xs.size(); ++i) {
+                const double e = ys[i] - (slope * xs[i] + icpt);
+                ssr += e * e;
+            }
+            r->gamma = -slope;
+            r->r2 = syy > 0 ? 1.0 - ssr / syy : NAN;
+        }
+    }
+    r->powerlaw = (std::isfinite(r->gamma) && std::isfinite(r->r2) && r->r2 >= 0.70 && r->gamma >= 1.0 &&
+                   r->gamma <= 5.0) ? 1 : 0;
+    r->heavy = (r->concentrated || r->powerlaw) ? 1 : 0;
+}
+
+// The report of one device degree array (n entries).
+static blest_status degree_report(cudaStream_t st, Tmp &T, const int *deg, int64_t n, blest_degree_report *r) {
+    int *mx = T.get<int>(1);
+    if (T.bad) return BLEST_ERR_OOM;
+    cudaMemsetAsync(mx, 0, 4, st);
+    k_deg_max<<<gridn(n, TB, 4096), TB, 0, st>>>(deg, n, mx);
+    int maxdeg = 0;
+    cudaMemcpyAsync(&maxdeg, mx, 4, cudaMemcpyDeviceToHost, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess) return BLEST_ERR_CUDA;
+    const size_t bins = (size_t)std::max(maxdeg + 1, SMALL_BINS);
+    unsigned long long *hist = T.get<unsigned long long>(bins);
+    if (T.bad) return BLEST_ERR_OOM;
+    cudaMemsetAsync(hist, 0, bins * 8, st);
+    k_deg_hist<<<gridn(n, TB, 4096), TB, 0, st>>>(deg, n, hist);
+    std::vector<unsigned long long> hh((size_t)maxdeg + 1);
+    cudaMemcpyAsync(hh.data(), hist, hh.size() * 8, cudaMemcpyDeviceToHost, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess) return BLEST_ERR_CUDA;
+    report_from_hist(hh, n, r);
+    return BLEST_OK;
+}
+
+// out_deg / in_deg: device arrays (in_deg may be null: undirected)
+static blest_status scale_free_report(cudaStream_t st, Tmp &T, const int *out_deg, const int *in_deg, int64_t n,
+                                      blest_scale_free_report *rep) {
+    memset(rep, 0, sizeof *rep);
+    blest_status s = degree_report(st, T, out_deg, n, &rep->out_deg);
+    if (s != BLEST_OK) return s;
+    if (in_deg) {
+        if ((s = degree_report(st, T, in_deg, n, &rep->in_deg)) != BLEST_OK) return s;
+    } else {
+        rep->in_deg = rep->out_deg;
+    }
+    rep->scale_free = (rep->out_deg.heavy || rep->in_deg.heavy) ? 1 : 0;
+    return BLEST_OK;
 }
 
 blest_status reorder_graph(blest_graph *h, const long long *rp, const int *col, int64_t n, int64_t nnz,
                            const blest_build_opts *o, int *new_of_old, int *applied) {
-    if (h->directed) return BLEST_ERR_UNSUPPORTED;
     Tmp T{h->stream};
     long long *rp2 = nullptr;
     int *col2 = nullptr, *deg = nullptr;
@@ -577,10 +724,24 @@ blest_status reorder_graph(blest_graph *h, const long long *rp, const int *col, 
     if (st != BLEST_OK) return st;
     int which = o->reorder;
     if (which == BLEST_REORDER_AUTO) {
-        std::vector<int> dh((size_t)n);
-        cudaMemcpyAsync(dh.data(), deg, (size_t)n * 4, cudaMemcpyDeviceToHost, h->stream);
-        if (cudaStreamSynchronize(h->stream) != cudaSuccess) return BLEST_ERR_CUDA;
-        which = scale_free_like(dh) ? BLEST_REORDER_JACCARD : BLEST_REORDER_RCM;
+        int *indeg = nullptr;
+        if (h->directed) {
+            long long m = 0;
+            cudaMemcpyAsync(&m, rp2 + n, 8, cudaMemcpyDeviceToHost, h->stream);
+            indeg = T.get<int>((size_t)n + 1);
+            if (T.bad) return BLEST_ERR_OOM;
+            cudaMemsetAsync(indeg, 0, (size_t)n * 4, h->stream);
+            if (cudaStreamSynchronize(h->stream) != cudaSuccess) return BLEST_ERR_CUDA;
+            if (m > 0) k_in_degree<<<gridn(m), TB, 0, h->stream>>>(col2, m, indeg);
+        }
+        blest_scale_free_report rep;
+        if ((st = scale_free_report(h->stream, T, deg, indeg, n, &rep)) != BLEST_OK) return st;
+        which = rep.scale_free ? BLEST_REORDER_JACCARD : BLEST_REORDER_RCM;
+    }
+    if (h->directed) {
+        // the orderings run on the symmetrised pattern G + G^T (RCM is defined
+        // for symmetric patterns; the permutation changes speed, never levels)
+        if ((st = clean_csr(h->stream, T, rp, col, n, nnz, &rp2, &col2, &deg, true)) != BLEST_OK) return st;
     }
     if (which == BLEST_REORDER_RCM) st = rcm_order(h, T, rp2, col2, deg, n, new_of_old);
     else if (which == BLEST_REORDER_JACCARD) st = jaccard_order(h, T, rp2, col2, deg, n, o->jaccard_window, new_of_old);
@@ -588,4 +749,38 @@ blest_status reorder_graph(blest_graph *h, const long long *rp, const int *col, 
     if (st != BLEST_OK) return st;
     *applied = which;
     return cudaStreamSynchronize(h->stream) == cudaSuccess ? BLEST_OK : BLEST_ERR_CUDA;
+}
+
+// ---- C ABI: the classifier on caller degree arrays (host or device)
+extern "C" blest_status blest_scale_free_test(const int32_t *out_deg, const int32_t *in_deg, int64_t n,
+                                              blest_scale_free_report *out) {
+    if (!out_deg || !out || n < 1 || n >= (1ll << 31)) return BLEST_ERR_INVALID;
+    cudaStream_t st = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return BLEST_ERR_CUDA;
+    blest_status s = BLEST_OK;
+    {
+        Tmp T{st};
+        int *d_out = T.get<int>((size_t)n), *d_in = in_deg ? T.get<int>((size_t)n) : nullptr;
+        if (T.bad) s = BLEST_ERR_OOM;
+        if (s == BLEST_OK && cudaMemcpyAsync(d_out, out_deg, (size_t)n * 4, cudaMemcpyDefault, st) != cudaSuccess)
+            s = BLEST_ERR_CUDA;
+        if (s == BLEST_OK && in_deg &&
+            cudaMemcpyAsync(d_in, in_deg, (size_t)n * 4, cudaMemcpyDefault, st) != cudaSuccess)
+            s = BLEST_ERR_CUDA;
+        int *d_bad = s == BLEST_OK ? T.get<int>(1) : nullptr;
+        if (s == BLEST_OK && T.bad) s = BLEST_ERR_OOM;
+        if (s == BLEST_OK) {   // degrees must be non-negative
+            cudaMemsetAsync(d_bad, 0, 4, st);
+            k_neg_check<<<gridn(n, TB, 4096), TB, 0, st>>>(d_out, n, d_bad);
+            if (d_in) k_neg_check<<<gridn(n, TB, 4096), TB, 0, st>>>(d_in, n, d_bad);
+            int bad = 0;
+            cudaMemcpyAsync(&bad, d_bad, 4, cudaMemcpyDeviceToHost, st);
+            if (cudaStreamSynchronize(st) != cudaSuccess) s = BLEST_ERR_CUDA;
+            else if (bad) s = BLEST_ERR_INVALID;
+        }
+        if (s == BLEST_OK) s = scale_free_report(st, T, d_out, d_in, n, out);
+        cudaStreamSynchronize(st);
+    }
+    cudaStreamDestroy(st);
+    return s;
 }

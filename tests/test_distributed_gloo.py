@@ -138,3 +138,37 @@ def test_checkpointed_ranges_sum_to_the_whole_and_reject_foreign_checkpoints(tmp
         closeness_checkpointed(_partial_oracle(g), g.n, str(tmp_path / "r0.npz"), 1, 10)
     with pytest.raises(ValueError):
         closeness_checkpointed(_partial_oracle(g), g.n, str(tmp_path / "x.npz"), 0, g.n + 1)
+
+
+def test_checkpoint_of_another_graph_with_the_same_n_is_refused(tmp_path):
+    from paper_2606_05081_gb300.distributed import closeness_checkpointed, graph_fingerprint
+    g1 = gg.rmat(9, seed=5)
+    g2 = gg.rmat(9, seed=6)                # same vertex count, other arcs
+    assert g1.n == g2.n
+    fp1, fp2 = graph_fingerprint(g1.row_ptr, g1.col), graph_fingerprint(g2.row_ptr, g2.col)
+    assert fp1 != fp2 and fp1 == graph_fingerprint(g1.row_ptr.copy(), g1.col.copy())
+    path = str(tmp_path / "cc.npz")
+    run, _ = _counting(_partial_oracle(g1), fail_after=1)
+    with pytest.raises(_Crash):
+        closeness_checkpointed(run, g1.n, path, chunk=100, fingerprint=fp1)
+    with pytest.raises(ValueError):
+        closeness_checkpointed(_partial_oracle(g2), g2.n, path, chunk=100, fingerprint=fp2)
+    far, reach = closeness_checkpointed(_partial_oracle(g1), g1.n, path, chunk=100, fingerprint=fp1)
+    far_r, reach_r, _ = oracle.closeness(g1)
+    assert np.array_equal(far, far_r) and np.array_equal(reach, reach_r)
+
+
+def test_reduction_runs_on_the_host_for_gloo_and_on_the_gpu_for_nccl():
+    from paper_2606_05081_gb300.distributed import reduce_device
+
+    class FakeDist:
+        def __init__(self, backend):
+            self.backend = backend
+
+        def get_backend(self, group=None):
+            return self.backend
+
+    assert reduce_device(None).type == "cpu"
+    assert reduce_device(FakeDist("gloo")).type == "cpu"
+    if torch.cuda.is_available():
+        assert reduce_device(FakeDist("nccl")).type == "cuda"

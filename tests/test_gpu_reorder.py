@@ -97,8 +97,81 @@ def test_auto_reorder_classifies(blest):
         assert h.info()["reorder"] == blest.REORDER_RCM
 
 
-def test_reorder_directed_is_unsupported(blest):
-    g = gg.er(100, 300, seed=1, directed=True)
+@pytest.mark.parametrize("which", ["rcm", "jaccard"])
+def test_directed_graph_reorders_through_its_symmetrised_pattern(blest, which):
+    g = gg.er(3000, 9000, seed=1, directed=True)
+    if which == "rcm":
+        opt, want = dict(reorder=blest.REORDER_RCM), reorder.rcm(reorder.symmetrized(g))
+    else:
+        opt = dict(reorder=blest.REORDER_JACCARD, jaccard_window=256)
+        want = reorder.jaccard_with_windows(reorder.symmetrized(g), 8, 256)
+    with blest.build_graph(g, **opt) as h:
+        assert np.array_equal(h.perm(), want)
+        srcs = gg.sources(g, 4, 2)
+        for mode in range(5):
+            h.set_policy(blest.POLICY_FIXED, mode)
+            for s in srcs:
+                assert np.array_equal(h.bfs(int(s)), oracle.bfs(g, int(s))), (mode, s)
+        h.set_policy(blest.POLICY_HEURISTIC)
+        assert np.array_equal(h.msbfs(srcs), oracle.bfs_many(g, srcs))
+
+
+def _degree_sequences():
+    """Hand-built sequences (the oracle's pins) and graph families."""
+    from oracle import classify
+    rng = np.random.default_rng(3)
+    seqs = {
+        "regular4": (np.full(1000, 4), None),
+        "concentrated": (np.array([100] * 2 + [10] * 18 + [1] * 180), None),
+        "powerlaw_only": (np.array([4] * 1_000_000 + sum(([k] * int(1e6 * k ** -3.0) for k in range(5, 61)), [])),
+                          None),
+        "steep": (np.array(sum(([k] * int(1e9 * k ** -6.0) for k in range(5, 12)), [])), None),
+        "noisy": (np.array(sum(([k] * int(rng.integers(1, 50)) for k in range(5, 400)), [])), None),
+        "one_point": (np.array([7] * 9), None),
+        "in_star": (np.r_[0, np.ones(499, np.int64)], np.r_[499, np.zeros(499, np.int64)]),
+    }
+    for name, g in [("lattice", gg.lattice(64, 64)), ("grid", gg.grid(128, 128, 0.05, 0.001, seed=1)),
+                    ("star", gg.star(300)), ("rmat14", gg.rmat(14, seed=1)), ("ba", gg.ba(1 << 15, 4, seed=2)),
+                    ("er_directed", gg.er(5000, 40000, seed=3, directed=True))]:
+        o, i = classify.degrees(g)
+        seqs[name] = (o, i if g.directed else None)
+    return seqs
+
+
+def test_scale_free_test_matches_oracle(blest):
+    from oracle import classify
+    for name, (o, i) in _degree_sequences().items():
+        got = blest.scale_free_test(o, i)
+        want = classify.scale_free_like(o, i)
+        assert got["scale_free"] == want["scale_free"], name
+        for side in ("out", "in"):
+            g_, w_ = got[side], want[side]
+            assert g_["top1"] == w_["top1"] and g_["top10"] == w_["top10"], (name, side)   # exact integer sums
+            assert g_["points"] == w_["points"], (name, side)
+            for f in ("gamma", "r2"):
+                if np.isnan(w_[f]):
+                    assert np.isnan(g_[f]), (name, side, f)
+                else:
+                    assert g_[f] == pytest.approx(w_[f], rel=1e-9, abs=1e-12), (name, side, f)
+            for f in ("concentrated", "powerlaw", "heavy"):
+                assert bool(g_[f]) == w_[f], (name, side, f)
+
+
+def test_scale_free_test_takes_device_arrays_and_rejects_negative_degrees(blest):
+    from oracle import classify
+    o, _ = classify.degrees(gg.rmat(12, seed=2))
+    got = blest.scale_free_test(torch.from_numpy(o).cuda())
+    assert got["scale_free"] == classify.scale_free_like(o)["scale_free"]
     with pytest.raises(blest.BlestError) as e:
-        blest.build_graph(g, reorder=blest.REORDER_RCM)
-    assert e.value.code == blest.ERR_UNSUPPORTED
+        blest.scale_free_test(np.array([3, -1, 2]))
+    assert e.value.code == blest.ERR_INVALID
+
+
+def test_auto_reorder_follows_the_oracle_decision(blest):
+    from oracle import classify
+    for g in [gg.rmat(12, seed=1), gg.grid(40, 40, seed=2), gg.ba(3000, 3, seed=4), gg.lattice(30, 30),
+              gg.er(3000, 9000, seed=5, directed=True)]:
+        want = classify.scale_free_like(*classify.degrees(g)) if g.directed else \
+            classify.scale_free_like(classify.degrees(g)[0])
+        with blest.build_graph(g, reorder=blest.REORDER_AUTO, jaccard_window=1024) as h:
+            assert h.info()["reorder"] == (blest.REORDER_JACCARD if want["scale_free"] else blest.REORDER_RCM)
