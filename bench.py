@@ -1,7 +1,8 @@
-"""Benchmark: single-source BFS throughput (GTEPS, harmonic mean over seeded
-sources) of the BVSS path on one GB300, with its HBM roofline fraction.
+"""Benchmark of the BVSS BFS path on one GB300: throughput (GTEPS,
+harmonic mean over seeded sources) with its HBM roofline fraction, for every
+configuration of the workload set, each checked against the CPU oracle.
 
-Default workload (the single-source configuration): 64 seeded sources on
+Headline (the JSON line's `value`): single-source BFS, 64 seeded sources on
 each of two graphs --
   * RMAT scale 24, edge factor 16 (16.7M vertices), JaccardWithWindows
     reordering with W = 2^16;
@@ -20,10 +21,20 @@ Timing: CUDA events on the stream the kernels run on, W >= 3 warm-up steps,
 synchronize around the timed region, max over ranks.  The BVSS arrays are
 gigabytes (far larger than the 129 MB L2), so no separate L2 flush is done.
 
+With no --workload, the line also carries `per_config`: one entry per
+configuration (C1 RMAT 16 plain; C2 the headline; C3 multi-source BFS on
+RMAT 22 with 64 / 256 / 1024 lanes, the 10,000-graph Barabasi-Albert batch
+and learned + batched against plain single-source on the same graph and
+sources; C4 all-source closeness on RMAT 18 and the 2048^2 grid; C5 the
+learned policy on held-out families), each with its roofline and a
+`levels_bit_exact` count taken outside the timed regions against the CPU
+oracle on all host cores.
+
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl blest|reference]
 
 --impl reference times the CPU oracle (serial FIFO BFS) on a bounded sample
-of the same workload and prints the same JSON line with "impl": "reference".
+of the headline workload and prints the same JSON line with
+"impl": "reference".
 """
 from __future__ import annotations
 
@@ -57,6 +68,7 @@ GRAPHS = {
                "RMAT scale 16, edge factor 16, undirected, no reordering"),
 }
 WORKLOADS = {
+    "all": ["rmat24_jaccard", "grid4096_rcm"],
     "sssp_pair": ["rmat24_jaccard", "grid4096_rcm"],
     "rmat24": ["rmat24"],
     "rmat22": ["rmat22"],
@@ -64,10 +76,10 @@ WORKLOADS = {
     "grid4096_rcm": ["grid4096_rcm"],
     "rmat24_jaccard": ["rmat24_jaccard"],
 }
-DEFAULT_WORKLOAD = "sssp_pair"
+DEFAULT_WORKLOAD = "all"
 # the other rows of the path, each with its own JSON line
-EXTRA_WORKLOADS = ["msbfs_rmat22", "closeness_rmat18", "closeness_grid2048_part", "bfs_many_ba10k",
-                   "switch_heldout"]
+EXTRA_WORKLOADS = ["msbfs_rmat22", "closeness_rmat18", "closeness_grid2048_part", "closeness_grid2048",
+                   "bfs_many_ba10k", "switch_heldout", "ablation", "order_study", "msbfs_one"]
 NUM_SOURCES = 64
 METRIC = "GTEPS (harm. mean/source), single-source BFS"
 
@@ -170,10 +182,14 @@ KERNEL_SOURCES = ["paper_2606_05081_gb300/csrc/bfs.cu", "paper_2606_05081_gb300/
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_bfs_traffic.json")
 
 
-def kernel_sha() -> str:
+MS_KERNEL_SOURCES = ["paper_2606_05081_gb300/csrc/msbfs.cu", "paper_2606_05081_gb300/csrc/tc.cuh",
+                     "paper_2606_05081_gb300/csrc/common.cuh", "paper_2606_05081_gb300/csrc/handle.h"]
+
+
+def kernel_sha(sources=None) -> str:
     import hashlib
     hsh = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in (sources or KERNEL_SOURCES):
         with open(os.path.join(ROOT, f), "rb") as fh:
             hsh.update(fh.read())
     return hsh.hexdigest()[:16]
@@ -355,82 +371,65 @@ class GraphRun:
         self.h.close()
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
-    ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS) + EXTRA_WORKLOADS)
-    ap.add_argument("--impl", default="blest", choices=["blest", "reference"])
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--sources", type=int, default=NUM_SOURCES)
-    ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (tuned arm = default launch)")
-    ap.add_argument("--levels", action="store_true", help="per-level log of the first source to stderr")
-    ap.add_argument("--ablation", action="store_true",
-                    help="also time the rungs between the plain and the tuned arm: the paper's rule with the "
-                         "CUDA-core hit test on the default layout, then on the autotuned layout and launch")
-    ap.add_argument("--tau", type=int, default=0, help="VSS width of the multi-source and closeness builds "
-                    "(0 = 128)")
-    ap.add_argument("--layout", default=None, help="sigma,tau of the tuned arm when the autotuner is off")
-    ap.add_argument("--launch", default=None, help="block_threads,vss_batch of the tuned arm when the autotuner "
-                    "is off")
-    args = ap.parse_args()
+class Ctx:
+    """What every part of a bench run shares: torch, the binding, the device,
+    the stream the library runs on, the trained weights, rank and world."""
 
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    dist = None
-    if world > 1:
-        import torch.distributed as dist_mod
-        dist = dist_mod
-        dist.init_process_group("nccl" if args.impl == "blest" else "gloo")
-    if args.impl == "reference":
-        run_reference(args, rank, world)
-        if dist:
-            dist.destroy_process_group()
-        return
-    args.warmup = max(args.warmup, 3)
-    if args.workload in EXTRA_WORKLOADS:
-        run_extra(args, rank, world, local)
-        if dist:
-            dist.destroy_process_group()
-        return
+    def __init__(self, args, rank, world, local, dist):
+        import torch
+        import paper_2606_05081_gb300 as blest
+        from paper_2606_05081_gb300 import switch
+        torch.cuda.set_device(local)
+        self.torch, self.blest, self.dist = torch, blest, dist
+        self.args, self.rank, self.world, self.local = args, rank, world, local
+        self.dev = torch.device("cuda", local)
+        self.stream = torch.cuda.Stream(self.dev)
+        torch.cuda.set_stream(self.stream)
+        self.weights = switch.load_weights()
+        self.hbm, self.peak_kind = peaks()
 
-    import torch
-    import paper_2606_05081_gb300 as blest
-    from paper_2606_05081_gb300 import autotune, switch
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    stream = torch.cuda.Stream(dev)
-    torch.cuda.set_stream(stream)
+    def events(self):
+        t = self.torch
+        return t.cuda.Event(enable_timing=True), t.cuda.Event(enable_timing=True)
 
-    runs = [GraphRun(nm, args, rank, dev, torch, blest, stream) for nm in WORKLOADS[args.workload]]
-    weights = switch.load_weights()
+
+def run_single_source(ctx, names, steps, warmup, tune=True, ablation=False, layout=None, launch=None,
+                      levels=False, sources=NUM_SOURCES):
+    """Plain and tuned single-source arms over `names` (GRAPHS keys): GTEPS,
+    roofline of k_bfs, end to end through the C ABI, and levels_bit_exact
+    of the tuned arm against the oracle.  Returns (fields of the JSON line,
+    the GraphRun objects, still open)."""
+    torch, blest, dist = ctx.torch, ctx.blest, ctx.dist
+    from paper_2606_05081_gb300 import autotune
+    rank, dev, stream = ctx.rank, ctx.dev, ctx.stream
+    args_src = argparse.Namespace(sources=sources)
+    runs = [GraphRun(nm, args_src, rank, dev, torch, blest, stream) for nm in names]
+    weights = ctx.weights
     tuned_policy = blest.POLICY_LEARNED if weights is not None else blest.POLICY_HEURISTIC
     tune_info = {}
     for r in runs:
         if weights is not None:
             r.h.load_model(weights)
-        if not args.no_tune:
+        if tune:
             r.h_tuned, tune_info[r.name] = autotune.autotune_layout(
-                lambda sg, ta, r=r: r.build_layout(blest, sg, ta, weights, tuned_policy), r.tune_srcs, reps=2,
+                lambda sg, ta, r=r: r.build_layout(blest, sg, ta, weights, tuned_policy), r.tune_srcs, reps=3,
                 stream=stream)
-        elif args.layout:
-            sg, ta = (int(x) for x in args.layout.split(","))
+        elif layout:
+            sg, ta = (int(x) for x in layout.split(","))
             r.h_tuned = r.build_layout(blest, sg, ta, weights, tuned_policy)
-        if args.no_tune and args.launch:
-            bt, bb = (int(x) for x in args.launch.split(","))
+        if not tune and launch:
+            bt, bb = (int(x) for x in launch.split(","))
             tune_info[r.name] = {"block_threads": bt, "vss_batch": bb, "engine_tc": 0, "fixed": True}
         r.h_tuned.set_stream(stream.cuda_stream, True)
         ti = tune_info.get(r.name, {})
         r.tuned = (int(ti.get("block_threads", 512)), int(ti.get("vss_batch", 2)), bool(ti.get("engine_tc", 0)))
-        if args.levels and rank == 0:
+        if levels and rank == 0:
             r.h_tuned.set_policy(tuned_policy)
             for rec in r.logs(r.h_tuned)[0]:
                 print(r.name, "level", json.dumps(rec), file=sys.stderr)
 
     arms = {"plain": (blest.POLICY_HEURISTIC, "default", True), "tuned": (tuned_policy, "tuned", None)}
-    if args.ablation:
+    if ablation:
         arms = {"plain": arms["plain"],
                 "rule_cc": (blest.POLICY_HEURISTIC, "default", False),
                 "rule_cc_tuned": (blest.POLICY_HEURISTIC, "tuned", False),
@@ -440,9 +439,9 @@ def main():
         """The arm's handle, configured: plain = default layout and launch,
         the paper's rule with the b1 MMA hit test; tuned = the autotuner's
         layout and launch under the learned policy."""
-        pol, launch, tc = arms[arm]
+        pol, lnch, tc = arms[arm]
         h = r.h if arm == "plain" else r.h_tuned
-        if launch == "default":
+        if lnch == "default":
             h.set_launch(512, 2)
         else:
             h.set_launch(r.tuned[0], r.tuned[1])
@@ -451,22 +450,22 @@ def main():
         return h
 
     results = {}
-    with ClockSampler(local) as clk:
+    with ClockSampler(ctx.local) as clk:
         for arm in arms:
             for r in runs:
                 h = set_arm(r, arm)
-                for _ in range(args.warmup):
+                for _ in range(warmup):
                     r.step(h, False)
                 h.sync()
             torch.cuda.synchronize()
             if dist:
                 dist.barrier()
             torch.cuda.synchronize()
-            t0e, t1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            psm = {r.name: np.zeros((args.steps, len(r.srcs))) for r in runs}
+            t0e, t1e = ctx.events()
+            psm = {r.name: np.zeros((steps, len(r.srcs))) for r in runs}
             t0e.record(stream)
             nvtx_range("timed_" + arm)
-            for k in range(args.steps):
+            for k in range(steps):
                 for r in runs:
                     r.step(set_arm(r, arm), True)
                 torch.cuda.synchronize()
@@ -506,7 +505,7 @@ def main():
     plain_value, plain_per = gteps_of(results["plain"][0])
 
     # roofline of the persistent BFS kernel under the headline arm
-    hbm, peak_kind = peaks()
+    hbm, peak_kind = ctx.hbm, ctx.peak_kind
     alg_b, dev_s = 0.0, 0.0
     per_graph_roof = {}
     for r in runs:
@@ -518,7 +517,8 @@ def main():
         alg_b += gb
         dev_s += gs
         per_graph_roof[r.name] = {"achieved_gbs": gb / gs / 1e9, "frac": gb / gs / 1e9 / hbm,
-                                  "algorithmic_bytes_per_launch": gb / len(r.srcs)}
+                                  "algorithmic_bytes_per_launch": gb / len(r.srcs),
+                                  "traffic": measured_traffic([(r.name, ti["sigma"], ti["tau"])])}
     achieved = alg_b / dev_s / 1e9
 
     # end to end through the C ABI with host buffers, headline arm
@@ -527,12 +527,19 @@ def main():
         h = set_arm(r, "tuned")
         h.set_stream(None, False)
         host = torch.empty(r.g.n, dtype=torch.int32).pin_memory().numpy()
-        for s, e in zip(r.srcs, r.edges):
+        for s_, e in zip(r.srcs, r.edges):
             t0 = time.perf_counter()
-            h.bfs(int(s), host)
+            h.bfs(int(s_), host)
             e2e_rates.append(e / (time.perf_counter() - t0) / 1e9)
         d2h += 4 * r.g.n * len(r.srcs)
     e2e = harmonic(e2e_rates)
+
+    # levels of every timed source of the tuned arm against the oracle (outside the timed regions)
+    exact = {}
+    for r in runs:
+        h = set_arm(r, "tuned")
+        h.set_stream(None, False)
+        exact[r.name] = levels_exact_single(r.g, r.srcs, h, torch, dev)
 
     graphs_cfg = {}
     for r in runs:
@@ -547,20 +554,17 @@ def main():
                              "sigma": int(r.h_tuned.info()["sigma"]), "tau": int(r.h_tuned.info()["tau"])},
             "graph_gen_s": round(r.gen_s, 1), "build_s": round(r.build_s, 2),
             "build_ms_device": round(r.info["build_ms"], 1),
+            "levels_bit_exact": exact[r.name], "sources": len(r.srcs),
             "levels_source0_tuned": [[x["mode"], x["queue"], round(x["t_ns"] / 1e3, 1)]
                                      for x in results["tuned"][2][r.name][0]][:40]}
     line = {
-        "metric": METRIC, "value": value, "unit": "GTEPS",
-        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": results["tuned"][1] / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": args.workload, "sources_per_graph": args.sources,
-                   "policy": "learned+autotuned" if weights is not None else "heuristic+autotuned",
-                   "l2": "inputs larger than L2 (BVSS arrays), no flush", "parallelism": f"replicas{world}",
-                   "graphs": graphs_cfg},
-        "plain": {"value": plain_value, "ms_per_step": results["plain"][1] / args.steps,
+        "value": value, "unit": "GTEPS",
+        "ms_per_step": results["tuned"][1] / steps,
+        "graphs": graphs_cfg,
+        "plain": {"value": plain_value, "ms_per_step": results["plain"][1] / steps,
                   "what": "hand-set rule (U_div lazy/eager, Eq. 5 switch), b1 MMA hit test, default launch"},
         "speedup_vs_plain": value / plain_value,
+        "levels_bit_exact": int(sum(exact.values())), "sources": int(sum(len(r.srcs) for r in runs)),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                      "traffic": measured_traffic([(r.name, r.h_tuned.info()["sigma"], r.h_tuned.info()["tau"])
                                                   for r in runs]), "peak_kind": peak_kind,
@@ -569,11 +573,11 @@ def main():
                      "kernel_sha": kernel_sha(), "per_graph": per_graph_roof},
         "e2e": {"value": e2e, "unit": "GTEPS", "h2d_bytes_per_step": 4 * sum(len(r.srcs) for r in runs),
                 "d2h_bytes_per_step": d2h},
-        "gpu_launches": args.steps * sum(len(r.srcs) for r in runs),   # one k_bfs per BFS of the tuned arm
+        "gpu_launches": steps * sum(len(r.srcs) for r in runs),   # one k_bfs per BFS of the tuned arm
         "clocks": clk.summary(),
         "autotune": {k: {kk: vv for kk, vv in v.items() if kk != "tried"} for k, v in tune_info.items()},
     }
-    if args.ablation:
+    if ablation:
         what = {"plain": "the paper's rule, b1 MMA hit test, sigma 8 / tau 128, 512-thread CTAs",
                 "rule_cc": "the paper's rule, CUDA-core hit test, sigma 8 / tau 128, 512-thread CTAs",
                 "rule_cc_tuned": "the paper's rule, CUDA-core hit test, autotuned layout and launch",
@@ -582,6 +586,84 @@ def main():
         for arm in arms:
             v, per = gteps_of(results[arm][0])
             line["ablation"][arm] = {"value": v, "per_graph": per, "what": what[arm]}
+    return line, runs
+
+
+def levels_exact_single(g, srcs, h, torch, dev, chunk=16):
+    """How many of the sources give a whole level array equal to the
+    oracle's (one serial BFS per source, all host cores)."""
+    import oracle
+    out = torch.empty(g.n, dtype=torch.int32, device=dev)
+    ok = 0
+    for i in range(0, len(srcs), chunk):
+        part = np.asarray(srcs[i:i + chunk])
+        ref = oracle.bfs_many(g, part)
+        for j, s_ in enumerate(part):
+            h.bfs(int(s_), out)
+            ok += int(np.array_equal(out.cpu().numpy(), ref[j]))
+    return ok
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS) + EXTRA_WORKLOADS)
+    ap.add_argument("--impl", default="blest", choices=["blest", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sources", type=int, default=NUM_SOURCES)
+    ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (tuned arm = default launch)")
+    ap.add_argument("--levels", action="store_true", help="per-level log of the first source to stderr")
+    ap.add_argument("--ablation", action="store_true",
+                    help="also time the rungs between the plain and the tuned arm: the paper's rule with the "
+                         "CUDA-core hit test on the default layout, then on the autotuned layout and launch")
+    ap.add_argument("--tau", type=int, default=0, help="VSS width of the multi-source and closeness builds "
+                    "(0 = 128)")
+    ap.add_argument("--layout", default=None, help="sigma,tau of the tuned arm when the autotuner is off")
+    ap.add_argument("--launch", default=None, help="block_threads,vss_batch of the tuned arm when the autotuner "
+                    "is off")
+    ap.add_argument("--scale", type=int, default=20, help="RMAT scale of the msbfs_one workload")
+    ap.add_argument("--kappa", type=int, default=1024, help="sources of the msbfs_one workload")
+    ap.add_argument("--engine", default="cc", choices=["cc", "tc"], help="multi-source stage 1 of msbfs_one")
+    ap.add_argument("--configs", default="C1,C3,C4,C5",
+                    help="per_config entries besides the headline (C2) of the default workload")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+        dist = dist_mod
+        dist.init_process_group("nccl" if args.impl == "blest" else "gloo")
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        if dist:
+            dist.destroy_process_group()
+        return
+    args.warmup = max(args.warmup, 3)
+    ctx = Ctx(args, rank, world, local, dist)
+    if args.workload in EXTRA_WORKLOADS:
+        run_extra(args, ctx)
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    fields, runs = run_single_source(ctx, WORKLOADS[args.workload], args.steps, args.warmup,
+                                     tune=not args.no_tune, ablation=args.ablation, layout=args.layout,
+                                     launch=args.launch, levels=args.levels, sources=args.sources)
+    line = {"metric": METRIC, "value": fields.pop("value"), "unit": fields.pop("unit"),
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": fields.pop("ms_per_step"), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": args.workload if args.workload != "all" else "sssp_pair (C2) + per_config",
+                       "sources_per_graph": args.sources,
+                       "policy": "learned+autotuned" if ctx.weights is not None else "heuristic+autotuned",
+                       "l2": "inputs larger than L2 (BVSS arrays), no flush", "parallelism": f"replicas{world}",
+                       "graphs": fields.pop("graphs")}}
+    line.update(fields)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rates = []
         for r in runs:
@@ -589,10 +671,29 @@ def main():
         line["cpu_baseline"] = {"value": harmonic(rates), "unit": "GTEPS", "cores": 1, "kind": "oracle",
                                 "sample": f"{len(rates)} of the workload's sources (all graphs), one serial "
                                           "FIFO BFS each on one host core, about 12 s"}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
     for r in runs:
         r.close()
+    del runs
+    if args.workload == "all":
+        want = [c.strip() for c in args.configs.split(",") if c.strip()]
+        per = {"C2": {"what": "single-source BFS, RMAT 24 (Jaccard) + 4096^2 grid (RCM), 64 sources each: "
+                              "the headline fields of this line",
+                      "value": line["value"], "plain": line["plain"]["value"], "unit": "GTEPS",
+                      "roofline": line["roofline"], "levels_bit_exact": line["levels_bit_exact"],
+                      "sources": line["sources"]}}
+        t_all = time.time()
+        with ClockSampler(local) as clk:
+            for c in want:
+                t0 = time.time()
+                per[c] = PER_CONFIG[c](ctx)
+                per[c]["wall_s"] = round(time.time() - t0, 1)
+        per["clocks"] = clk.summary()
+        per["wall_s"] = round(time.time() - t_all, 1)
+        line["per_config"] = per
+        if "C3" in per and "learned_batched_vs_plain" in per["C3"]:
+            line["learned_batched_vs_plain"] = per["C3"]["learned_batched_vs_plain"]
+    if rank == 0:
+        print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
 
@@ -601,171 +702,705 @@ def _events(torch):
     return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
 
-def run_extra(args, rank, world, local):
-    """Multi-source BFS (§6.1), closeness (§6.2) and batched small graphs:
-    device time with CUDA events on the library's stream, inputs resident."""
-    import torch
-    import paper_2606_05081_gb300 as blest
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    stream = torch.cuda.Stream(dev)
-    torch.cuda.set_stream(stream)
-    hbm, peak_kind = peaks()
-    line = {"n_gpus": world, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic"}
-    if args.workload == "msbfs_rmat22":
-        g = gg.rmat(22, 16, seed=3)
-        h = blest.build(g.n, g.row_ptr, g.col, tau=args.tau)
-        h.set_stream(stream.cuda_stream, True)
-        deg = torch.from_numpy(np.diff(g.row_ptr)).to(dev)
-        res = {}
-        for k in (64, 256, 1024):
-            srcs = gg.sources(g, k, 22 + k)
-            out = torch.empty((k, g.n), dtype=torch.int32, device=dev)
-            sd = torch.from_numpy(srcs).to(dev)
-            for _ in range(args.warmup):
-                h.msbfs(sd, out)
-            h.sync()
-            a, b = _events(torch)
-            a.record(stream)
-            for _ in range(args.steps):
-                h.msbfs(sd, out)
-            b.record(stream)
-            torch.cuda.synchronize()
-            h.sync()
-            ms = a.elapsed_time(b) / args.steps
-            reached = out >= 0
-            arcs = int((reached.to(torch.int64) * deg[None, :]).sum().item())
-            floor = 8.0 * k * g.n      # -1 initialisation and one level write per (source, vertex)
-            res[k] = {"ms": ms, "gteps": arcs / 2 / (ms * 1e-3) / 1e9,
-                      "level_floor_gbs": floor / (ms * 1e-3) / 1e9}
-            del out
-        line.update({"metric": "GTEPS (aggregate over sources), multi-source BFS", "value": res[1024]["gteps"],
-                     "unit": "GTEPS", "ms_per_step": res[1024]["ms"],
-                     "config": {"workload": args.workload, "graph": "RMAT scale 22, edge factor 16", "n": g.n,
-                                "nnz": g.nnz, "kappa": [64, 256, 1024], "levels": "int32, source-major"},
-                     "per_kappa": res,
-                     "roofline": {"bound": "hbm", "achieved": res[1024]["level_floor_gbs"], "peak": hbm,
-                                  "unit": "GB/s", "frac": res[1024]["level_floor_gbs"] / hbm, "traffic": None,
-                                  "peak_kind": peak_kind,
-                                  "bytes": "level-array floor only: 8 B per (source, vertex)"},
-                     "gpu_launches": args.steps * 3})
-    elif args.workload.startswith("closeness"):
-        if args.workload == "closeness_rmat18":
-            g = gg.rmat(18, 16, seed=4)
-            first, count = 0, g.n
-            desc = "RMAT scale 18, edge factor 16, all sources"
-        else:
-            g = gg.grid(2048, 2048, 0.05, 0.001, seed=4)
-            first, count = 0, 8 * 1024
-            desc = "2048x2048 road-like grid, sources 0..8191 (8 of the 4096 batches of 1024)"
-        h = blest.build(g.n, g.row_ptr, g.col, tau=args.tau)
-        h.set_stream(stream.cuda_stream, False)
-        far = torch.empty(g.n, dtype=torch.int64, device=dev)
-        reach = torch.empty(g.n, dtype=torch.int64, device=dev)
-        h.closeness_range(first, min(1024, count), far, reach)
-        torch.cuda.synchronize()
-        a, b = _events(torch)
+# ------------------------------------------------------------ byte models
+def msbfs_algorithmic_bytes(st, n, tau=128, sigma=8, levels_out=True, closeness=False):
+    """Bytes a multi-source call must move, from its work counters (one pass
+    over each array touched, no credit for caching), per the terms of the
+    multi-source path:
+      stage 1, per processed VSS: its BVSS lane words (4 tau row ids +
+        4 tau / theta mask words), its virtualToReal entry and queue entry
+        (8 B), the kappa-bit frontier elements of its slice set's sigma
+        vertices (sigma kappa / 8 B) and the set's active word (kappa / 8 B);
+        4 B per nonzero 32-lane hit word OR-ed into V_next;
+      stage 2, per dirty slice set: its sigma vertices' elements of V_next
+        and V_curr read and of F and V_curr written (4 kappa / 8 B each);
+      init: F, V_curr, V_next zeroed (3 kappa / 8 B per vertex) per launch;
+      levels: the output floor, 4 kappa B per vertex per launch (each level
+        written once);
+      closeness: far and reach, 12 B per vertex per batch."""
+    kappa = st["kappa"]
+    theta = 32 // sigma
+    per_vss = 4.0 * tau + 4.0 * tau / theta + 8.0 + sigma * kappa / 8.0 + kappa / 8.0
+    b = st["vss"] * per_vss + 4.0 * st["hit_words"] + st["dirty_sets"] * sigma * 4.0 * kappa / 8.0
+    b += st["launches"] * n * 3.0 * kappa / 8.0
+    if levels_out:
+        b += st["launches"] * 4.0 * kappa * n
+    if closeness:
+        b += st["launches"] * 12.0 * n
+    return b
+
+
+def _roof(ctx, bytes_, seconds, kernel, traffic=None, **extra):
+    a = bytes_ / seconds / 1e9
+    d = {"bound": "hbm", "achieved": a, "peak": ctx.hbm, "unit": "GB/s", "frac": a / ctx.hbm,
+         "traffic": traffic, "peak_kind": ctx.peak_kind, "kernel": kernel, "algorithmic_bytes": bytes_}
+    d.update(extra)
+    return d
+
+
+def _edges_of_levels(levels_dev, deg_dev, directed=False):
+    """Traversed edges per row of a (k, n) device level array: arcs leaving
+    reached vertices, halved on an undirected graph."""
+    arcs = ((levels_dev >= 0).to(deg_dev.dtype) * deg_dev[None, :]).sum(dim=1)
+    return arcs if directed else arcs // 2
+
+
+# ------------------------------------------------------------ per config
+def config_c1(ctx):
+    """C1: RMAT scale 16, 64 sources, no reordering; the plain method (the
+    paper's rule, b1 MMA) is the configuration's figure; the tuned arm too."""
+    f, runs = run_single_source(ctx, ["rmat16"], steps=min(ctx.args.steps, 5), warmup=3, tune=True)
+    for r in runs:
+        r.close()
+    rf = f["roofline"]
+    rf["note"] = "the graph (10 MB of BVSS) is L2-resident, so the HBM fraction is not meaningful"
+    return {"what": "single-source BFS, RMAT scale 16 (65,536 vertices), 64 seeded sources, no reordering",
+            "value": f["plain"]["value"], "unit": "GTEPS", "arm": "plain (the paper's rule, b1 MMA, default launch)",
+            "tuned": f["value"], "roofline": rf, "levels_bit_exact": f["levels_bit_exact"],
+            "sources": f["sources"], "e2e": f["e2e"], "graph": f["graphs"]["rmat16"],
+            "gpu_launches": min(ctx.args.steps, 5) * f["sources"]}
+
+
+def config_c3(ctx):
+    """C3: multi-source BFS on RMAT 22 (kappa 64 / 256 / 1024 over the first
+    64 / 256 / 1024 of one seeded source draw), the same 1024 sources as
+    plain and learned single-source BFSs, and the 10,000-graph BA batch."""
+    import oracle
+    torch, blest, dev, stream = ctx.torch, ctx.blest, ctx.dev, ctx.stream
+    t0 = time.time()
+    g = gg.rmat(22, 16, seed=3)
+    gen_s = time.time() - t0
+    srcs = gg.sources(g, 1024, 22)
+    deg = torch.from_numpy(np.diff(g.row_ptr)).to(dev)
+    h = blest.build(g.n, g.row_ptr, g.col)
+    h.set_stream(stream.cuda_stream, True)
+    info = h.info()
+    reps = 3
+
+    def time_msbfs(sd, out):
+        for _ in range(2):
+            h.msbfs(sd, out)
+        h.sync()
+        a, b = ctx.events()
         a.record(stream)
-        h.closeness_range(first, count, far, reach)
+        for _ in range(reps):
+            h.msbfs(sd, out)
         b.record(stream)
         torch.cuda.synchronize()
-        ms = a.elapsed_time(b)
-        # traversed edges: each source reaches its component; sum over targets of reach = pairs
-        pairs = int(reach.sum().item())
-        mean_deg = g.nnz / g.n
-        line.update({"metric": "BFS per second and GTEPS (aggregate), all-source closeness",
-                     "value": count / (ms * 1e-3), "unit": "BFS/s", "ms_per_step": ms,
-                     "gteps_est": pairs * mean_deg / 2 / (ms * 1e-3) / 1e9,
-                     "config": {"workload": args.workload, "graph": desc, "n": g.n, "nnz": g.nnz,
-                                "sources": count, "batch": 1024, "tau": h.info()["tau"]},
-                     "full_run_estimate_s": (g.n / count) * ms * 1e-3,
-                     "gpu_launches": (count + 1023) // 1024})
-    elif args.workload == "switch_heldout":
-        line.update(run_heldout(args, torch, blest, dev, stream))
-    else:
-        b = gg.ba_batch(10000, 1000, 100000, 4, seed=3)
-        srcs = np.zeros(b.g, np.int32)            # vertex 0 of every graph
-        h = blest.build_many(b)
-        h.set_stream(stream.cuda_stream, True)
-        out = torch.empty(int(b.vtx_off[-1]), dtype=torch.int32, device=dev)
-        for _ in range(args.warmup):
-            h.bfs_many(srcs, out)
         h.sync()
-        a, e = _events(torch)
-        a.record(stream)
-        for _ in range(args.steps):
-            h.bfs_many(srcs, out)
-        e.record(stream)
+        return a.elapsed_time(b) / reps
+
+    outs, per_k, tc_exact = {}, {}, {}
+    for k in (64, 256, 1024):
+        sd = torch.from_numpy(srcs[:k]).to(dev)
+        out = torch.empty((k, g.n), dtype=torch.int32, device=dev)
+        # the tcgen05 stage 1 first (its levels kept for the check), then CUDA cores
+        h.set_msbfs_engine(True)
+        ms_tc = time_msbfs(sd, out)
+        st_tc = h.msbfs_stats()
+        tc_out = out[:64].clone()
+        h.set_msbfs_engine(False)
+        ms = time_msbfs(sd, out)
+        st = h.msbfs_stats()
+        tc_exact[k] = bool(torch.equal(tc_out, out[:64]))
+        del tc_out
+        edges = torch.cat([_edges_of_levels(out[i:i + 64], deg) for i in range(0, k, 64)]).cpu().numpy()
+        nb = msbfs_algorithmic_bytes(st, g.n, info["tau"], 8, levels_out=True)
+        per_k[k] = {"ms": ms, "gteps": float(edges.sum()) / (ms * 1e-3) / 1e9, "counters": st,
+                    "roofline": _roof(ctx, nb, ms * 1e-3, f"k_msbfs<{k // 32}>"),
+                    "tcgen05": {"ms": ms_tc, "gteps": float(edges.sum()) / (ms_tc * 1e-3) / 1e9,
+                                "roofline": _roof(ctx, msbfs_algorithmic_bytes(st_tc, g.n, info["tau"], 8), ms_tc * 1e-3,
+                                                  f"k_msbfs_tc<{k // 32}>"),
+                                "first_64_lanes_equal_cuda_core": tc_exact[k]},
+                    "engine": "cuda cores" if ms <= ms_tc else "tcgen05"}
+        outs[k] = out
+    # levels: every lane of every batch against the oracle (chunks of 64 sources)
+    exact = {64: 0, 256: 0, 1024: 0}
+    for i in range(0, 1024, 64):
+        ref = oracle.bfs_many(g, srcs[i:i + 64])
+        for k in (64, 256, 1024):
+            if i < k:
+                got = outs[k][i:i + 64].cpu().numpy()
+                exact[k] += int(sum(np.array_equal(got[j], ref[j]) for j in range(64)))
+    edges1024 = torch.cat([_edges_of_levels(outs[1024][i:i + 64], deg) for i in range(0, 1024, 64)]).cpu().numpy()
+    for k in (64, 256, 1024):
+        per_k[k]["levels_bit_exact"] = exact[k]
+        per_k[k]["sources"] = k
+    del outs
+    # the same 1024 sources as single-source BFSs: plain (rule, b1 MMA, default launch) and learned
+    ss = {}
+    out1 = torch.empty(g.n, dtype=torch.int32, device=dev)
+    if ctx.weights is not None:
+        h.load_model(ctx.weights)
+    for arm, pol, tc, launch in (("plain", blest.POLICY_HEURISTIC, True, (512, 2)),
+                                 ("learned", blest.POLICY_LEARNED if ctx.weights is not None
+                                  else blest.POLICY_HEURISTIC, False, (1024, 2))):
+        h.set_policy(pol)
+        h.set_engine(tc)
+        h.set_launch(*launch)
+        for s_ in srcs[:8]:
+            h.bfs(int(s_), out1)
+        h.sync()
+        evs = [ctx.events() for _ in srcs]
+        for (a, b), s_ in zip(evs, srcs):
+            a.record(stream)
+            h.bfs(int(s_), out1)
+            b.record(stream)
         torch.cuda.synchronize()
         h.sync()
-        ms = a.elapsed_time(e) / args.steps
-        # traversed arcs: out-degrees of the reached vertices of every graph
-        degs = np.concatenate([np.diff(b.row_ptr[b.vtx_off[i] + i: b.vtx_off[i + 1] + i + 1]) for i in range(b.g)])
-        reached = (out >= 0).cpu().numpy()
-        arcs = int(degs[reached].sum())
-        line.update({"metric": "GTEPS (aggregate), batched BFS over 10,000 BA graphs", "value": arcs / 2 / (ms * 1e-3) / 1e9,
-                     "unit": "GTEPS", "ms_per_step": ms,
-                     "config": {"workload": args.workload,
-                                "graph": "10,000 Barabasi-Albert graphs, n log-uniform in [1e3, 1e5], m = 4",
-                                "total_vertices": int(b.vtx_off[-1]), "total_arcs": arcs, "source": "vertex 0"},
-                     "gpu_launches": args.steps})
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+        ms = np.array([a.elapsed_time(b) for a, b in evs])
+        rates = edges1024 / (ms * 1e-3) / 1e9
+        ss[arm] = {"gteps_harmonic": harmonic(rates), "gteps_aggregate": float(edges1024.sum() / (ms.sum() * 1e-3) / 1e9),
+                   "ms_total": float(ms.sum())}
+    msa = per_k[1024]["gteps"]
+    lbp = {"graph": "RMAT scale 22, edge factor 16", "sources": 1024,
+           "batched_gteps": msa, "plain_single_source_gteps": ss["plain"]["gteps_aggregate"],
+           "learned_single_source_gteps": ss["learned"]["gteps_aggregate"],
+           "batched_over_plain": msa / ss["plain"]["gteps_aggregate"],
+           "learned_over_plain": ss["learned"]["gteps_aggregate"] / ss["plain"]["gteps_aggregate"],
+           "what": "aggregate GTEPS (sum of traversed edges / total device time) of the 1024 sources: multi-source "
+                   "BFS with 1024 lanes against one single-source BFS per source under the paper's rule (b1 MMA, "
+                   "default launch) and under the learned policy; levels of every lane checked against the oracle"}
+    h.close()
+    del g
+    # the batch of 10,000 Barabasi-Albert graphs, one launch, every graph checked
+    t0 = time.time()
+    bt = gg.ba_batch(10000, 1000, 100000, 4, seed=3)
+    gen_b = time.time() - t0
+    bsrc = np.zeros(bt.g, np.int32)
+    hb = blest.build_many(bt)
+    hb.set_stream(stream.cuda_stream, True)
+    tot = int(bt.vtx_off[-1])
+    outb = torch.empty(tot, dtype=torch.int32, device=dev)
+    for _ in range(3):
+        hb.bfs_many(bsrc, outb)
+    hb.sync()
+    a, b = ctx.events()
+    a.record(stream)
+    for _ in range(reps):
+        hb.bfs_many(bsrc, outb)
+    b.record(stream)
+    torch.cuda.synchronize()
+    hb.sync()
+    msb = a.elapsed_time(b) / reps
+    lv = outb.cpu().numpy()
+    degs = np.concatenate([np.diff(bt.row_ptr[bt.vtx_off[i] + i: bt.vtx_off[i + 1] + i + 1]) for i in range(bt.g)])
+    arcs = int(degs[lv >= 0].sum())
+    from concurrent.futures import ThreadPoolExecutor
+
+    def chk(i):
+        gi = bt.graph(i)
+        return np.array_equal(lv[bt.vtx_off[i]:bt.vtx_off[i + 1]], oracle.bfs(gi, 0))
+    with ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
+        okb = int(sum(ex.map(chk, range(bt.g))))
+    hb.close()
+    batch = {"what": "10,000 Barabasi-Albert graphs (n log-uniform in [1e3, 1e5], m = 4), one BFS per graph from "
+                     "vertex 0, one persistent launch replayed from a CUDA graph",
+             "gteps": arcs / 2 / (msb * 1e-3) / 1e9, "ms": msb, "total_vertices": tot, "total_arcs": arcs,
+             "levels_bit_exact": okb, "graphs": bt.g, "gen_s": round(gen_b, 1)}
+    return {"what": "multi-source BFS on RMAT scale 22 (edge factor 16), 64 / 256 / 1024 lanes over the first "
+                    "64 / 256 / 1024 of one seeded draw of sources; the batched small-graph run",
+            "value": msa, "unit": "GTEPS", "per_kappa": per_k, "roofline": per_k[1024]["roofline"],
+            "levels_bit_exact": exact[1024], "sources": 1024, "single_source_same_sources": ss,
+            "learned_batched_vs_plain": lbp, "bfs_many_ba10k": batch, "gen_s": round(gen_s, 1),
+            "gpu_launches": reps * 3 + 2 * 1024 + reps}
 
 
-def run_heldout(args, torch, blest, dev, stream):
-    """The learned level-mode policy on graph families it was not trained on
-    (RMAT scale 25, Barabasi-Albert 2^24 m = 8, random geometric 2^24 with
-    average degree 10): per-level device times of every mode give the time
-    regret of the learned policy and of the paper's rule against the
-    per-level optimum; whole-BFS GTEPS of both policies on the same sources."""
+def config_c4(ctx):
+    """C4: all-source closeness on RMAT 18 (far and reach bit-exact and cc
+    within 1e-12 at 1024 seeded targets against the oracle), split by source
+    ranges over the ranks when there are several; the 2048^2 grid timed
+    over its first 8 batches here (the full run is its own workload)."""
+    import oracle
+    torch, blest, dev, stream, dist = ctx.torch, ctx.blest, ctx.dev, ctx.stream, ctx.dist
+    g = gg.rmat(18, 16, seed=4)
+    h = blest.build(g.n, g.row_ptr, g.col)
+    h.set_stream(stream.cuda_stream, False)
+    far = torch.empty(g.n, dtype=torch.int64, device=dev)
+    reach = torch.empty(g.n, dtype=torch.int64, device=dev)
+    # the tcgen05 stage 1 timed first, then the CUDA-core one (whose result is checked)
+    h.set_msbfs_engine(True)
+    h.closeness_range(0, 1024, far, reach)            # warm-up (captures the batch graph)
+    torch.cuda.synchronize()
+    ms_tc, f_tc, r_tc, _, _ = closeness_split_run(h, g.n, ctx.rank, ctx.world, dist, far, reach, CudaTimer(ctx))
+    h.set_msbfs_engine(False)
+    h.closeness_range(0, 1024, far, reach)
+    torch.cuda.synchronize()
+    ms, f_all, r_all, cc, (_, count) = closeness_split_run(h, g.n, ctx.rank, ctx.world, dist, far, reach,
+                                                           CudaTimer(ctx))
+    st = h.msbfs_stats()
+    tc_equal = bool(np.array_equal(f_tc, f_all) and np.array_equal(r_tc, r_all))
+    tg = gg.sources(g, 1024, 18)
+    fr, rr = oracle.far_reach(g, tg)
+    cc_ref = oracle.closeness_from(fr, rr)
+    exact = int(np.sum((f_all[tg] == fr) & (r_all[tg] == rr)))
+    rel = np.abs(cc[tg] - cc_ref) / np.maximum(np.abs(cc_ref), 1e-300)
+    nb = msbfs_algorithmic_bytes(st, g.n, h.info()["tau"], 8, levels_out=False, closeness=True)
+    pairs = int(r_all.sum())
+    h.close()
+    rmat18 = {"what": "all 262,144 sources of RMAT scale 18 (edge factor 16), 256 batches of 1024",
+              "seconds": ms * 1e-3, "bfs_per_s": g.n / (ms * 1e-3),
+              "gteps_est": pairs * (g.nnz / g.n) / 2 / (ms * 1e-3) / 1e9,
+              "targets_checked": len(tg), "far_reach_bit_exact": exact, "cc_max_rel_err": float(rel.max()),
+              "roofline": _roof(ctx, nb, ms * 1e-3 / max(1, ctx.world) * ctx.world, "k_msbfs<32>",
+                                note="the graph is L2-resident; the HBM fraction is not meaningful"),
+              "counters": st, "ranks": ctx.world,
+              "tcgen05": {"seconds": ms_tc * 1e-3, "far_reach_equal_cuda_core": tc_equal},
+              "engine": "cuda cores" if ms <= ms_tc else "tcgen05"}
+    # the grid: 8 of its 4096 batches, as a time estimate
+    gq = gg.grid(2048, 2048, 0.05, 0.001, seed=4)
+    hq = blest.build(gq.n, gq.row_ptr, gq.col, tau=32)
+    hq.set_stream(stream.cuda_stream, False)
+    fq = torch.empty(gq.n, dtype=torch.int64, device=dev)
+    rq = torch.empty(gq.n, dtype=torch.int64, device=dev)
+    hq.closeness_range(0, 1024, fq, rq)
+    torch.cuda.synchronize()
+    a, b = ctx.events()
+    a.record(stream)
+    hq.closeness_range(0, 8 * 1024, fq, rq)
+    b.record(stream)
+    torch.cuda.synchronize()
+    msq = a.elapsed_time(b)
+    stq = hq.msbfs_stats()
+    nbq = msbfs_algorithmic_bytes(stq, gq.n, 32, 8, levels_out=False, closeness=True)
+    hq.close()
+    grid = {"what": "2048^2 road-like grid (tau 32), sources 0..8191 (8 of 4096 batches)", "ms": msq,
+            "full_run_estimate_s": (gq.n / 8192) * msq * 1e-3,
+            "roofline": _roof(ctx, nbq, msq * 1e-3, "k_msbfs<32>"), "counters": stq,
+            "full_run": _full_grid_record()}
+    return {"what": "exact closeness (far bit-exact, cc within 1e-12) by all-source multi-source BFS",
+            "value": rmat18["bfs_per_s"], "unit": "BFS/s", "rmat18": rmat18, "grid2048": grid,
+            "levels_bit_exact": exact, "sources": len(tg), "roofline": rmat18["roofline"],
+            "gpu_launches": (count + 1023) // 1024 + 8}
+
+
+class CudaTimer:
+    """CUDA events on the library's stream around a region (milliseconds)."""
+
+    def __init__(self, ctx):
+        self.ctx = ctx
+
+    def start(self):
+        self.a, self.b = self.ctx.events()
+        self.a.record(self.ctx.stream)
+
+    def stop(self):
+        self.b.record(self.ctx.stream)
+        self.ctx.torch.cuda.synchronize()
+        return self.a.elapsed_time(self.b)
+
+
+def closeness_split_run(h, n, rank, world, dist, far, reach, timer):
+    """All-source closeness split over the ranks: this rank runs the
+    multi-source batches of its own source range (between a barrier and the
+    timer's stop), then one integer all-reduce of far and reach completes
+    the result on every rank.  Returns (max-over-ranks ms, far, reach, cc,
+    (first, count)) with far, reach, cc as host arrays."""
+    import torch
+    from paper_2606_05081_gb300 import distributed
+    first, count = distributed.source_ranges(n, world)[rank]
+    if dist is not None and world > 1:
+        dist.barrier()
+    timer.start()
+    h.closeness_range(first, count, far, reach)
+    ms = timer.stop()
+    if dist is not None and world > 1:
+        tt = torch.tensor([ms], dtype=torch.float64, device=distributed.reduce_device(dist))
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    f_all, r_all, cc = distributed.closeness_allreduce(lambda f0, c0: (far, reach), n, rank, world,
+                                                       dist if world > 1 else None)
+    return ms, f_all, r_all, cc, (first, count)
+
+
+def _full_grid_record():
+    """The committed record of the full 2048^2 grid closeness run (its own
+    workload, too long for this run), when one exists."""
+    p = os.path.join(ROOT, "profiles", "closeness_grid2048_full.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        d = json.load(open(p))
+    except ValueError:
+        return None
+    d["kernel_sources_unchanged"] = d.get("kernel_sha") == kernel_sha(MS_KERNEL_SOURCES)
+    return d
+
+
+def config_c5(ctx):
+    """C5: the learned policy against the paper's rule on graph families it
+    was not trained on -- levels of all 64 sources bit-exact, GTEPS of both
+    policies, and time regret against the per-level optimum."""
+    import oracle
     from paper_2606_05081_gb300 import switch
-    w = switch.load_weights()
+    torch, blest, dev, stream = ctx.torch, ctx.blest, ctx.dev, ctx.stream
+    w = ctx.weights
     if w is None:
-        return {"metric": "switching regret", "value": None, "unavailable": "no trained weights"}
+        return {"value": None, "unavailable": "no trained weights"}
     fams = [("rmat25", lambda: gg.rmat(25, 16, seed=25), "RMAT scale 25, edge factor 16"),
             ("ba16m_m8", lambda: gg.ba(1 << 24, 8, seed=26), "Barabasi-Albert, 2^24 vertices, m = 8"),
             ("rgg16m", lambda: gg.rgg(1 << 24, 10.0, seed=27), "random geometric, 2^24 points, average degree 10")]
-    per, regs = {}, []
+    per, regs, ex_tot, n_tot, hrates = {}, [], 0, 0, []
+    launches = 0
     for name, mk, desc in fams:
+        t0 = time.time()
         g = mk()
-        srcs = gg.sources(g, args.sources, 5)
+        gen_s = time.time() - t0
+        srcs = gg.sources(g, NUM_SOURCES, 5)
         h = blest.build(g.n, g.row_ptr, g.col)
         h.set_stream(stream.cuda_stream, True)
         h.load_model(w)
         ev = switch.evaluate(h, srcs[:8], w, reps=2)
-        deg = np.diff(g.row_ptr)
+        deg = torch.from_numpy(np.diff(g.row_ptr)).to(dev)
         out = torch.empty(g.n, dtype=torch.int32, device=dev)
-        rates = {}
+        res = {}
         for pol, tc in (("learned", False), ("heuristic", True)):
             h.set_engine(tc)
             h.set_policy(blest.POLICY_LEARNED if pol == "learned" else blest.POLICY_HEURISTIC)
-            r = []
-            for s in srcs:
-                h.bfs(int(s), out)
-                h.sync()
-                a, b = _events(torch)
+            for s_ in srcs[:4]:
+                h.bfs(int(s_), out)
+            h.sync()
+            ms, edges = [], []
+            for s_ in srcs:
+                a, b = ctx.events()
                 a.record(stream)
-                h.bfs(int(s), out)
+                h.bfs(int(s_), out)
                 b.record(stream)
                 torch.cuda.synchronize()
                 h.sync()
-                lv = out.cpu().numpy()
-                r.append(deg[lv >= 0].sum() / 2 / (a.elapsed_time(b) * 1e-3) / 1e9)
-            rates[pol] = harmonic(r)
-        per[name] = {"graph": desc, "n": g.n, "nnz": g.nnz, "regret_learned": ev["regret_learned"],
-                     "regret_heuristic_tc": ev["regret_heuristic_tc"], "regret_heuristic_cc": ev["regret_heuristic_cc"],
-                     "ms_learned": ev["ms_learned"], "ms_heuristic_tc": ev["ms_heuristic_tc"],
-                     "ms_optimal": ev["ms_optimal"], "gteps_learned": rates["learned"],
-                     "gteps_heuristic_tc": rates["heuristic"]}
+                ms.append(a.elapsed_time(b))
+                edges.append(int(_edges_of_levels(out[None, :], deg)[0].item()))
+                launches += 1
+            ms, edges = np.array(ms), np.array(edges, np.float64)
+            rates = edges / (ms * 1e-3) / 1e9
+            res[pol] = {"gteps_harmonic": harmonic(rates), "gteps_aggregate": float(edges.sum() / (ms.sum() * 1e-3) / 1e9),
+                        "small_component_sources": int(np.sum(edges < 1000))}
+        h.set_engine(False)
+        h.set_policy(blest.POLICY_LEARNED)
+        h.set_stream(None, False)
+        exact = levels_exact_single(g, srcs, h, torch, dev)
+        ex_tot += exact
+        n_tot += len(srcs)
+        hrates.append(res["learned"]["gteps_harmonic"])
+        per[name] = {"graph": desc, "n": g.n, "nnz": g.nnz, "gen_s": round(gen_s, 1),
+                     "levels_bit_exact": exact, "sources": len(srcs),
+                     "regret_learned": ev["regret_learned"], "regret_heuristic_tc": ev["regret_heuristic_tc"],
+                     "regret_heuristic_cc": ev["regret_heuristic_cc"], "ms_learned": ev["ms_learned"],
+                     "ms_heuristic_tc": ev["ms_heuristic_tc"], "ms_optimal": ev["ms_optimal"],
+                     "gteps_learned": res["learned"], "gteps_heuristic_tc": res["heuristic"]}
         regs.append(ev["regret_learned"])
         h.close()
         del g
-    return {"metric": "switching regret of the learned policy (held-out families), mean", "value": float(np.mean(regs)),
-            "unit": "fraction over the per-level optimum", "higher_is_better": False,
-            "config": {"workload": "switch_heldout", "sources": args.sources, "regret_sources": 8},
-            "per_family": per, "gpu_launches": None}
+    return {"what": "learned level-mode policy vs the paper's rule (b1 MMA) on held-out families; regret = time "
+                    "over the per-level optimum on 8 sources, GTEPS on all 64",
+            "value": float(np.mean(regs)), "unit": "mean time regret of the learned policy",
+            "higher_is_better": False, "per_family": per, "levels_bit_exact": ex_tot, "sources": n_tot,
+            "gpu_launches": launches}
+
+
+PER_CONFIG = {"C1": config_c1, "C3": config_c3, "C4": config_c4, "C5": config_c5}
+
+
+def run_extra(args, ctx):
+    """One row of the path on its own JSON line (multi-source BFS, closeness,
+    the batched small graphs, the held-out policy evaluation)."""
+    line = {"n_gpus": ctx.world, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic"}
+    if args.workload == "msbfs_rmat22":
+        c = config_c3(ctx)
+        line.update({"metric": "GTEPS (aggregate over sources), multi-source BFS", "value": c["value"],
+                     "unit": "GTEPS", "ms_per_step": c["per_kappa"][1024]["ms"],
+                     "config": {"workload": args.workload, "graph": "RMAT scale 22, edge factor 16",
+                                "kappa": [64, 256, 1024], "levels": "int32, source-major"},
+                     **{k: c[k] for k in ("per_kappa", "roofline", "levels_bit_exact", "sources",
+                                          "learned_batched_vs_plain", "bfs_many_ba10k", "gpu_launches")}})
+    elif args.workload == "bfs_many_ba10k":
+        c = config_c3(ctx)["bfs_many_ba10k"]
+        line.update({"metric": "GTEPS (aggregate), batched BFS over 10,000 BA graphs", "value": c["gteps"],
+                     "unit": "GTEPS", "ms_per_step": c["ms"], "config": {"workload": args.workload},
+                     "batch": c, "gpu_launches": 3})
+    elif args.workload == "closeness_rmat18" or args.workload == "closeness_grid2048_part":
+        c = config_c4(ctx)
+        line.update({"metric": "BFS per second, all-source closeness", "value": c["value"], "unit": "BFS/s",
+                     "config": {"workload": args.workload}, "rmat18": c["rmat18"], "grid2048": c["grid2048"],
+                     "gpu_launches": c["gpu_launches"]})
+    elif args.workload == "closeness_grid2048":
+        line.update(run_grid_closeness_full(args, ctx))
+    elif args.workload == "msbfs_one":
+        line.update(run_msbfs_one(args, ctx))
+    elif args.workload == "ablation":
+        line.update(run_ablation(args, ctx))
+    elif args.workload == "order_study":
+        line.update(run_order_study(args, ctx))
+    elif args.workload == "switch_heldout":
+        c = config_c5(ctx)
+        line.update({"metric": "switching regret of the learned policy (held-out families), mean",
+                     "config": {"workload": args.workload}, **c})
+    if ctx.rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def _time_sources(ctx, h, srcs, out, warm=3):
+    """Device time (ms) of one BFS from each source, CUDA events on the
+    library's stream."""
+    torch, stream = ctx.torch, ctx.stream
+    for s_ in srcs[:warm]:
+        h.bfs(int(s_), out)
+    h.sync()
+    evs = [ctx.events() for _ in srcs]
+    for (a, b), s_ in zip(evs, srcs):
+        a.record(stream)
+        h.bfs(int(s_), out)
+        b.record(stream)
+    torch.cuda.synchronize()
+    h.sync()
+    return np.array([a.elapsed_time(b) for a, b in evs])
+
+
+def run_msbfs_one(args, ctx):
+    """One multi-source configuration (RMAT --scale, --kappa sources, stage 1
+    on CUDA cores or tcgen05): W warm-up and K timed launches, the levels of
+    the first lanes checked against the oracle; small enough to profile."""
+    import oracle
+    torch, blest, dev, stream = ctx.torch, ctx.blest, ctx.dev, ctx.stream
+    g = gg.rmat(args.scale, 16, seed=3)
+    srcs = gg.sources(g, args.kappa, 22)
+    h = blest.build(g.n, g.row_ptr, g.col)
+    h.set_stream(stream.cuda_stream, True)
+    h.set_msbfs_engine(args.engine == "tc")
+    sd = torch.from_numpy(srcs).to(dev)
+    out = torch.empty((len(srcs), g.n), dtype=torch.int32, device=dev)
+    for _ in range(args.warmup):
+        h.msbfs(sd, out)
+    h.sync()
+    a, b = ctx.events()
+    a.record(stream)
+    for _ in range(args.steps):
+        h.msbfs(sd, out)
+    b.record(stream)
+    torch.cuda.synchronize()
+    h.sync()
+    ms = a.elapsed_time(b) / args.steps
+    st = h.msbfs_stats()
+    chk = min(16, len(srcs))
+    ok = int(np.array_equal(out[:chk].cpu().numpy(), oracle.bfs_many(g, srcs[:chk])))
+    deg = torch.from_numpy(np.diff(g.row_ptr)).to(dev)
+    edges = float(torch.cat([_edges_of_levels(out[i:i + 64], deg) for i in range(0, len(srcs), 64)]).sum().item())
+    nb = msbfs_algorithmic_bytes(st, g.n, 128, 8, levels_out=True)
+    h.close()
+    return {"metric": "GTEPS (aggregate), one multi-source configuration", "value": edges / (ms * 1e-3) / 1e9,
+            "unit": "GTEPS", "ms_per_step": ms,
+            "config": {"workload": "msbfs_one", "graph": f"RMAT scale {args.scale}, edge factor 16",
+                       "kappa": len(srcs), "engine": args.engine},
+            "counters": st, "first_lanes_exact": bool(ok),
+            "roofline": _roof(ctx, nb, ms * 1e-3, ("k_msbfs_tc" if args.engine == "tc" else "k_msbfs")),
+            "gpu_launches": args.steps}
+
+
+def run_ablation(args, ctx):
+    """The ablation ladders of §7.1 on GB300.
+
+    Single-source (64 sources each on RMAT 24 and the 4096^2 grid), each rung
+    adding one optimisation: (A) BVSS + kernel fusion, eager updates, b1 MMA
+    with one slice per fragment row (16 MMAs per VSS), no reordering; (AB) +
+    the optimal layout of Fig. 3 (2 MMAs per VSS); (ABC) + reordering
+    (JaccardWithWindows / RCM); (ABCD) + lazy updates by the U_div rule;
+    (Full) + Eq. 5 switching (the paper's method); then this build's steps:
+    CUDA-core hit test; learned level policy.  Multi-source (256 sources on
+    RMAT 22 and the 2048^2 grid): (Naive) 256 single-source BFSs of the full
+    method; (A) Algorithm 5 without getVI reindexing or activeSets /
+    dirtySets tracking; (AB) without tracking; (Full) Algorithm 5; (Full,
+    tcgen05) its stage 1 on the tensor cores.  Levels of a sample of sources
+    per rung are checked against the oracle."""
+    import oracle
+    torch, blest, dev, stream = ctx.torch, ctx.blest, ctx.dev, ctx.stream
+    out_ss = {}
+    specs = [("rmat24", lambda: gg.rmat(24, 16, seed=2), dict(reorder=REORDER_JACCARD, jaccard_window=65536)),
+             ("grid4096", lambda: gg.grid(4096, 4096, 0.05, 0.001, seed=2), dict(reorder=REORDER_RCM))]
+    for name, mk, ropt in specs:
+        g = mk()
+        srcs = gg.sources(g, args.sources, 7)
+        chk = srcs[:4]
+        ref = oracle.bfs_many(g, chk)
+        deg = np.diff(g.row_ptr)
+        h0 = blest.build(g.n, g.row_ptr, g.col)
+        h1 = blest.build(g.n, g.row_ptr, g.col, **ropt)
+        for h in (h0, h1):
+            h.set_stream(stream.cuda_stream, True)
+            if ctx.weights is not None:
+                h.load_model(ctx.weights)
+        built_switch = h1.info()["switching"]
+        out = torch.empty(g.n, dtype=torch.int32, device=dev)
+        rungs = [("A", h0, 2, blest.POLICY_FIXED, 1, None),
+                 ("AB", h0, 1, blest.POLICY_FIXED, 1, None),
+                 ("ABC", h1, 1, blest.POLICY_FIXED, 1, None),
+                 ("ABCD", h1, 1, blest.POLICY_HEURISTIC, 0, 0),
+                 ("Full", h1, 1, blest.POLICY_HEURISTIC, 0, built_switch),
+                 ("Full, CUDA-core hit test", h1, 0, blest.POLICY_HEURISTIC, 0, built_switch)]
+        if ctx.weights is not None:
+            rungs.append(("Full, learned level policy", h1, 0, blest.POLICY_LEARNED, 0, built_switch))
+        res = {}
+        edges = None
+        for rung, h, eng, pol, mode, sw in rungs:
+            h.set_engine(eng)
+            h.set_policy(pol, mode)
+            if sw is not None:
+                h.set_switching(sw)
+            h.set_launch(512, 2)
+            ms = _time_sources(ctx, h, srcs, out)
+            ok = 0
+            for j, s_ in enumerate(chk):
+                h.bfs(int(s_), out)
+                h.sync()
+                ok += int(np.array_equal(out.cpu().numpy(), ref[j]))
+            if edges is None:
+                edges = []
+                for s_ in srcs:
+                    h.bfs(int(s_), out)
+                    h.sync()
+                    lv = out.cpu().numpy()
+                    edges.append(int(deg[lv >= 0].sum()) // 2)
+                edges = np.array(edges, np.float64)
+            res[rung] = {"ms_mean": float(ms.mean()), "gteps_harmonic": harmonic(edges / (ms * 1e-3) / 1e9),
+                         "levels_bit_exact_checked": ok, "checked": len(chk)}
+        base = res["A"]["ms_mean"]
+        for v in res.values():
+            v["speedup_vs_A"] = base / v["ms_mean"]
+        out_ss[name] = {"n": g.n, "nnz": g.nnz, "udiv_reordered": h1.info()["update_divergence"],
+                        "switching_built": built_switch, "rungs": res}
+        h0.close()
+        h1.close()
+        del g
+    # multi-source ladder
+    out_ms = {}
+    for name, mk, tau in [("rmat22", lambda: gg.rmat(22, 16, seed=3), 128),
+                          ("grid2048", lambda: gg.grid(2048, 2048, 0.05, 0.001, seed=4), 32)]:
+        g = mk()
+        srcs = gg.sources(g, 256, 22)
+        ref = oracle.bfs_many(g, srcs)
+        h = blest.build(g.n, g.row_ptr, g.col, tau=tau)
+        h.set_stream(stream.cuda_stream, True)
+        sd = torch.from_numpy(srcs).to(dev)
+        out = torch.empty((len(srcs), g.n), dtype=torch.int32, device=dev)
+        res = {}
+        # Naive: one single-source BFS per source, the paper's full method
+        out1 = torch.empty(g.n, dtype=torch.int32, device=dev)
+        h.set_engine(1 if tau == 128 else 0)
+        h.set_policy(blest.POLICY_HEURISTIC)
+        ms = _time_sources(ctx, h, srcs, out1)
+        res["Naive"] = {"seconds": float(ms.sum()) * 1e-3}
+        variants = [("A", (0, 0), 0), ("AB", (1, 0), 0), ("Full", (1, 1), 0)]
+        if tau == 128:
+            variants.append(("Full, tcgen05 stage 1", (1, 1), 1))
+        for rung, (ri, tr), eng in variants:
+            h.set_msbfs_engine(False)
+            h.set_msbfs_variant(ri, tr)
+            h.set_msbfs_engine(bool(eng))
+            h.msbfs(sd, out)
+            h.sync()
+            a, b = ctx.events()
+            a.record(stream)
+            h.msbfs(sd, out)
+            b.record(stream)
+            torch.cuda.synchronize()
+            h.sync()
+            got = out.cpu().numpy()
+            res[rung] = {"seconds": a.elapsed_time(b) * 1e-3,
+                         "levels_bit_exact": int(sum(np.array_equal(got[j], ref[j]) for j in range(len(srcs)))),
+                         "counters": h.msbfs_stats()}
+        for v in res.values():
+            v["speedup_vs_naive"] = res["Naive"]["seconds"] / v["seconds"]
+        out_ms[name] = {"n": g.n, "nnz": g.nnz, "tau": tau, "sources": len(srcs), "rungs": res}
+        h.close()
+        del g
+    return {"metric": "ablation ladders (ms per single-source BFS, seconds per 256-source batch)", "value": None,
+            "unit": "see rungs", "config": {"workload": "ablation", "sources": args.sources},
+            "single_source": out_ss, "multi_source": out_ms, "gpu_launches": None}
+
+
+def run_order_study(args, ctx):
+    """The ordering experiments of §7.1 on RMAT 24: the JaccardWithWindows
+    window W from 2^3 to 2^18 (BVSS size and BFS time), RCM, the scale-free
+    test's choice, no reordering of the generator's scrambled labels (a
+    random order) and of its unscrambled labels (the natural RMAT order:
+    hubs first).  Per order: VSS and slice counts, U_div, and the mean
+    device time per BFS of the (AB) rung (eager updates, Fig. 3 b1 MMA), the
+    paper's rule (Full) and the learned policy, 8 sources each."""
+    import oracle
+    torch, blest, dev, stream = ctx.torch, ctx.blest, ctx.dev, ctx.stream
+    out = torch.empty(1 << 24, dtype=torch.int32, device=dev)
+    res = {}
+
+    def measure(label, g, srcs, opt):
+        t0 = time.time()
+        h = blest.build(g.n, g.row_ptr, g.col, **opt)
+        inf = h.info()
+        row = {"build_s": round(time.time() - t0, 2), "num_vss": inf["num_vss"], "num_slices": inf["num_slices"],
+               "udiv": inf["update_divergence"], "lazy": inf["lazy"], "reorder": inf["reorder"]}
+        h.set_stream(stream.cuda_stream, True)
+        if ctx.weights is not None:
+            h.load_model(ctx.weights)
+        for key, pol, mode, eng in (("AB_ms", blest.POLICY_FIXED, 1, 1), ("rule_ms", blest.POLICY_HEURISTIC, 0, 1),
+                                    ("learned_ms", blest.POLICY_LEARNED, 0, 0)):
+            if pol == blest.POLICY_LEARNED and ctx.weights is None:
+                continue
+            h.set_engine(eng)
+            h.set_policy(pol, mode)
+            row[key] = float(_time_sources(ctx, h, srcs, out[:g.n]).mean())
+        h.set_stream(None, False)
+        row["levels_exact_source0"] = bool(np.array_equal(h.bfs(int(srcs[0])), oracle.bfs(g, int(srcs[0]))))
+        res[label] = row
+        h.close()
+
+    g = gg.rmat(24, 16, seed=2)
+    srcs = gg.sources(g, 8, 7)
+    for label, opt in [("scrambled (random order)", dict(reorder=0)), ("rcm", dict(reorder=REORDER_RCM)),
+                       ("auto", dict(reorder=3, jaccard_window=65536))] + \
+                      [(f"jaccard W=2^{e}", dict(reorder=REORDER_JACCARD, jaccard_window=1 << e))
+                       for e in range(3, 19)]:
+        measure(label, g, srcs, opt)
+    del g
+    g = gg.rmat(24, 16, seed=2, scramble=False)
+    measure("natural (unscrambled RMAT labels)", g, gg.sources(g, 8, 7), dict(reorder=0))
+    return {"metric": "ms per single-source BFS under each vertex order (RMAT 24)", "value": None, "unit": "ms",
+            "config": {"workload": "order_study", "graph": "RMAT scale 24, edge factor 16", "sources": 8},
+            "orders": res, "gpu_launches": None}
+
+
+def run_grid_closeness_full(args, ctx):
+    """Config 4's grid: exact closeness over all 4,194,304 sources of the
+    2048^2 road-like grid (4096 batches of 1024 lanes), split over the ranks
+    by source ranges; far and reach checked bit-exact and cc within 1e-12 at
+    256 seeded targets against the oracle."""
+    import oracle
+    torch, blest, dev, stream, dist = ctx.torch, ctx.blest, ctx.dev, ctx.stream, ctx.dist
+    g = gg.grid(2048, 2048, 0.05, 0.001, seed=4)
+    h = blest.build(g.n, g.row_ptr, g.col, tau=32)
+    h.set_stream(stream.cuda_stream, False)
+    far = torch.empty(g.n, dtype=torch.int64, device=dev)
+    reach = torch.empty(g.n, dtype=torch.int64, device=dev)
+    h.closeness_range(0, 1024, far, reach)
+    torch.cuda.synchronize()
+    with ClockSampler(ctx.local) as clk:
+        ms, f_all, r_all, cc, (_, count) = closeness_split_run(h, g.n, ctx.rank, ctx.world, dist, far, reach,
+                                                               CudaTimer(ctx))
+    st = h.msbfs_stats()
+    tg = gg.sources(g, 256, 2048)
+    fr, rr = oracle.far_reach(g, tg)
+    cc_ref = oracle.closeness_from(fr, rr)
+    exact = int(np.sum((f_all[tg] == fr) & (r_all[tg] == rr)))
+    rel = np.abs(cc[tg] - cc_ref) / np.maximum(np.abs(cc_ref), 1e-300)
+    nb = msbfs_algorithmic_bytes(st, g.n, 32, 8, levels_out=False, closeness=True)
+    h.close()
+    return {"metric": "seconds, exact all-source closeness of the 2048^2 road-like grid", "value": ms * 1e-3,
+            "unit": "s", "higher_is_better": False, "ms_per_step": ms,
+            "config": {"workload": "closeness_grid2048", "graph": "2048x2048 4-neighbour grid, 5% edges deleted, "
+                       "0.1% random shortcuts, no reordering, tau 32", "n": g.n, "nnz": g.nnz,
+                       "batches": (g.n + 1023) // 1024},
+            "bfs_per_s": g.n / (ms * 1e-3), "targets_checked": len(tg), "far_reach_bit_exact": exact,
+            "cc_max_rel_err": float(rel.max()), "counters": st,
+            "roofline": _roof(ctx, nb, ms * 1e-3, "k_msbfs<32>"), "clocks": clk.summary(),
+            "kernel_sha": kernel_sha(MS_KERNEL_SOURCES), "gpu_launches": (count + 1023) // 1024}
 
 
 if __name__ == "__main__":

@@ -163,6 +163,26 @@ blest_status blest_bfs(blest_handle h, int32_t source, int32_t *levels);
  * closeness calls below. */
 blest_status blest_msbfs(blest_handle h, const int32_t *sources, int32_t k, int32_t *levels);
 
+/* Stage-1 engine of the multi-source kernel (and of closeness): 0 (default)
+ * = CUDA cores (the OR of the frontier elements each slice mask selects, 32
+ * lanes per 32-bit operation); 1 = the fifth-generation tensor cores:
+ * Eq. 2 for a 128-lane tile of the frontier and 64 slots of a VSS as one
+ * tcgen05 kind::f16 MMA with 0/1 bf16 operands (K = the slice set's 8
+ * columns, zero-padded to 16) and fp32 sums in tensor memory, a lane
+ * reaching a slot's row iff its sum is nonzero.  Levels are identical.
+ * The tensor-core engine needs sigma = 8, tau = 128 (UNSUPPORTED
+ * otherwise). */
+blest_status blest_set_msbfs_engine(blest_handle h, int32_t tc);
+
+/* Variant of the multi-source kernel (for the ablation of §7.1): reindex =
+ * 1 stores vertex u's kappa-bit element at getVI(u) (§6.1), 0 at u;
+ * tracking = 1 visits only the active slice sets' VSSs in stage 1 and the
+ * dirty slice sets in stage 2 (activeSets / dirtySets of Algorithm 5), 0
+ * every VSS and every slice set at every level.  Default (1, 1) is
+ * Algorithm 5 in full; (0, 0) and (1, 0) are the ablation's (A) and (AB).
+ * Levels are identical.  The tensor-core engine runs only (1, 1). */
+blest_status blest_set_msbfs_variant(blest_handle h, int32_t reindex, int32_t tracking);
+
 /* Exact closeness centrality by all-source BFS in 1024-lane batches (§6.2).
  * far: n int64 distance sums (Eq. 6); cc: n doubles, cc[u] = (reach[u]-1) /
  * far[u] (Eq. 7 with component-size normalisation; 0 when far[u] = 0), may be
@@ -182,6 +202,23 @@ blest_status blest_closeness(blest_handle h, int64_t *far, double *cc, int64_t *
 blest_status blest_closeness_range(blest_handle h, int64_t first, int64_t count, int64_t *far,
                                    int64_t *reach);
 
+/* Work counters of the last blest_msbfs, blest_closeness or
+ * blest_closeness_range call on the handle, summed over its launches (one
+ * per batch of up to kappa sources): the terms of the multi-source byte
+ * model (stage 1 loads each processed VSS and its slice set's frontier
+ * elements and ORs each nonzero hit word into V_next; stage 2 reads and
+ * writes the kappa-bit elements of the eight vertices of each dirty set). */
+typedef struct blest_msbfs_counters {
+    int64_t kappa;        /* lanes per batch: 64, 256 or 1024 */
+    int64_t launches;     /* persistent-kernel launches */
+    int64_t levels;       /* levels, summed over the launches */
+    int64_t vss;          /* VSSs processed in stage 1 */
+    int64_t hit_words;    /* nonzero 32-lane words OR-ed into V_next */
+    int64_t dirty_sets;   /* slice sets finalised in stage 2 */
+} blest_msbfs_counters;
+
+blest_status blest_msbfs_stats(blest_handle h, blest_msbfs_counters *out);
+
 /* Many small graphs in one handle: graph i has vertices [vtx_off[i],
  * vtx_off[i+1]) (local ids from 0) and arcs [edge_off[i], edge_off[i+1]);
  * its local row pointer is row_ptr[vtx_off[i] + i .. vtx_off[i+1] + i]
@@ -200,7 +237,10 @@ blest_status blest_bfs_many(blest_handle h, const int32_t *sources, int32_t *lev
 blest_status blest_set_policy(blest_handle h, int32_t policy, int32_t fixed_mode);
 
 /* Hit-test engine of the heuristic policy's top-down levels: 1 = b1 MMA
- * (Fig. 3 layout, the paper's), 0 = CUDA cores.  The MMA needs sigma = 8,
+ * (Fig. 3 layout, the paper's: 2 MMAs per 128 slices), 0 = CUDA cores, 2 =
+ * b1 MMA with one slice per fragment row (16 MMAs per 128 slices, the
+ * layout Fig. 3 improves on; for the ablation).  Tensor-core modes of a
+ * fixed policy or schedule use the same layout.  The MMA needs sigma = 8,
  * tau = 128 (UNSUPPORTED otherwise); on other layouts a fixed policy or
  * schedule that names a tensor-core mode runs its CUDA-core twin, and the
  * level log records the mode that ran. */
@@ -210,6 +250,21 @@ blest_status blest_set_engine(blest_handle h, int32_t tc);
  * 1024}, vss_batch in {1, 2, 4} (VSSs a warp keeps in flight in top-down
  * levels).  The grid is resized to the SMs' resident capacity. */
 blest_status blest_set_launch(blest_handle h, int32_t block_threads, int32_t vss_batch);
+
+/* Eq. 5 bottom-up switching of the heuristic policy on (1) or off (0).  The
+ * build decides it (§7.1: by the three-source probe for graphs that use
+ * lazy updates, off otherwise); this overrides that decision. */
+blest_status blest_set_switching(blest_handle h, int32_t on);
+
+/* Queue entries a single-source level writes (§5's VSS queue Q_next).  A
+ * level that schedules more VSSs than this counts them without writing
+ * them, and the next top-down level then scans every VSS and keeps those
+ * whose slice set has a frontier bit (the frontier bitvector is exact), so
+ * a dense frontier costs neither the queue writes nor their reads.
+ * cap = 0: the default, max(N_v / 2, 1024) clamped to N_v; otherwise cap
+ * entries (clamped to N_v; 1 makes nearly every level scan).  Levels are
+ * identical whatever the cap. */
+blest_status blest_set_queue_cap(blest_handle h, int64_t cap);
 
 /* Per-level modes for BLEST_POLICY_SCHEDULE: level l (1-based) runs
  * modes[(l-1) % len].  Copied. */

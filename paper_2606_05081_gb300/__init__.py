@@ -94,6 +94,12 @@ class ScaleFreeReport(ctypes.Structure):
     _fields_ = [("out_deg", DegreeReport), ("in_deg", DegreeReport), ("scale_free", ctypes.c_int32)]
 
 
+class MsbfsStats(ctypes.Structure):
+    """blest_msbfs_stats: work counters of the last multi-source call."""
+    _fields_ = [("kappa", ctypes.c_int64), ("launches", ctypes.c_int64), ("levels", ctypes.c_int64),
+                ("vss", ctypes.c_int64), ("hit_words", ctypes.c_int64), ("dirty_sets", ctypes.c_int64)]
+
+
 _P = ctypes.c_void_p
 _H = ctypes.c_void_p
 _S = ctypes.c_int
@@ -110,6 +116,10 @@ _sigs = {
     "blest_set_schedule": (_S, [_H, _P, ctypes.c_int32]),
     "blest_set_engine": (_S, [_H, ctypes.c_int32]),
     "blest_set_launch": (_S, [_H, ctypes.c_int32, ctypes.c_int32]),
+    "blest_set_queue_cap": (_S, [_H, ctypes.c_int64]),
+    "blest_set_switching": (_S, [_H, ctypes.c_int32]),
+    "blest_set_msbfs_engine": (_S, [_H, ctypes.c_int32]),
+    "blest_set_msbfs_variant": (_S, [_H, ctypes.c_int32, ctypes.c_int32]),
     "blest_load_model": (_S, [_H, _P, ctypes.c_int32]),
     "blest_last_timings": (_S, [_H, _P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
     "blest_get_info": (_S, [_H, ctypes.POINTER(Info)]),
@@ -121,6 +131,7 @@ _sigs = {
     "blest_status_string": (ctypes.c_char_p, [_S]),
     "blest_selftest_barrier_timeout": (_S, [ctypes.c_int32]),
     "blest_bfs_noalloc": (_S, [ctypes.POINTER(BvssView), ctypes.c_int32, _P, _P]),
+    "blest_msbfs_stats": (_S, [_H, ctypes.POINTER(MsbfsStats)]),
     "blest_scale_free_test": (_S, [_P, _P, ctypes.c_int64, ctypes.POINTER(ScaleFreeReport)]),
     "blest_mlp_features": (_S, [_P, ctypes.c_int64, ctypes.c_float, _P]),
     "blest_mlp_loss_grad": (_S, [_P, _P, _P, ctypes.c_int64, _P, _P, _P]),
@@ -247,6 +258,12 @@ class Graph:
                "blest_closeness_range")
         return far, reach
 
+    def msbfs_stats(self) -> dict:
+        """Work counters of the last multi-source or closeness call."""
+        st = MsbfsStats()
+        _check(_lib.blest_msbfs_stats(self._h, ctypes.byref(st)), "blest_msbfs_stats")
+        return {f: int(getattr(st, f)) for f, _ in MsbfsStats._fields_}
+
     def bfs_many(self, sources, out=None, total_n=None):
         src = np.ascontiguousarray(sources, dtype=np.int32) if not hasattr(sources, "data_ptr") else sources
         if out is None:
@@ -258,11 +275,33 @@ class Graph:
     def set_policy(self, policy: int, fixed_mode: int = 0):
         _check(_lib.blest_set_policy(self._h, policy, fixed_mode), "blest_set_policy")
 
-    def set_engine(self, tc: bool):
-        _check(_lib.blest_set_engine(self._h, int(bool(tc))), "blest_set_engine")
+    def set_engine(self, tc):
+        """Top-down hit test: False / 0 CUDA cores, True / 1 the Fig. 3 b1-MMA
+        layout, 2 the 16-MMA-per-VSS layout (ablation)."""
+        _check(_lib.blest_set_engine(self._h, int(tc)), "blest_set_engine")
 
     def set_launch(self, block_threads: int, vss_batch: int):
         _check(_lib.blest_set_launch(self._h, int(block_threads), int(vss_batch)), "blest_set_launch")
+
+    def set_msbfs_engine(self, tc: bool):
+        """Multi-source stage 1 on the tensor cores (tcgen05, tau = 128) or
+        on CUDA cores (the default)."""
+        _check(_lib.blest_set_msbfs_engine(self._h, int(bool(tc))), "blest_set_msbfs_engine")
+
+    def set_msbfs_variant(self, reindex: bool = True, tracking: bool = True):
+        """Multi-source kernel variant of the ablation: getVI reindexing and
+        activeSets / dirtySets tracking on or off (both on = Algorithm 5)."""
+        _check(_lib.blest_set_msbfs_variant(self._h, int(bool(reindex)), int(bool(tracking))),
+               "blest_set_msbfs_variant")
+
+    def set_switching(self, on: bool):
+        """Eq. 5 bottom-up switching of the rule on or off (overrides the build's probe)."""
+        _check(_lib.blest_set_switching(self._h, int(bool(on))), "blest_set_switching")
+
+    def set_queue_cap(self, cap: int):
+        """Queue entries a level writes before the next level scans instead
+        (0 = the default)."""
+        _check(_lib.blest_set_queue_cap(self._h, int(cap)), "blest_set_queue_cap")
 
     def set_schedule(self, modes):
         m = np.ascontiguousarray(modes, dtype=np.int32)

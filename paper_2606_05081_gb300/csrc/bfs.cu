@@ -32,6 +32,9 @@ constexpr int BFS_MAX_THREADS = 1024;
 
 struct BfsParams {
     int n, W;
+    int Nv;                 // VSSs of the BVSS
+    int qcap;               // queue entries written per level; a longer queue is counted, not written,
+                            // and the next top-down level scans every VSS's frontier field instead
     const int *__restrict__ rowIds;
     const unsigned *__restrict__ masks;
     const int *__restrict__ realPtrs;
@@ -51,6 +54,7 @@ struct BfsParams {
     int log_cap;
     int src;
     int policy, fixed_mode, lazy, tc, switching;
+    int tc16;               // tensor-core levels use the 16-MMA layout instead of Fig. 3's
     float eta;
     const int *schedule;
     int sched_len;
@@ -108,6 +112,37 @@ __device__ __forceinline__ unsigned hits_tc(unsigned m, unsigned alpha, unsigned
            ((unsigned)(d3 != 0) << 3);
 }
 
+// The layout Fig. 3 improves on: one slice per fragment row, so 16 MMAs per
+// 128 slices.  MMA i takes slices 8i .. 8i + 7 (lane 2i + r/4, byte r % 4 of
+// the VSS's mask words): row r of fragA holds slice 8i + r in the low byte
+// of thread 4r, column 0 of fragB holds alpha in thread 0's low byte, and
+// D[r][0] = popc(slice & alpha) lands in thread 4r's first accumulator; a
+// ballot returns each slice's hit to the lane that owns it.  Used by the
+// ablation that measures the optimal layout against it.
+__device__ __forceinline__ unsigned hits_tc16(unsigned m, unsigned alpha) {
+    const int lane = lane_id();
+    const int r = lane >> 2;
+    const bool head = (lane & 3) == 0;
+    const unsigned fb = lane == 0 ? alpha : 0u;
+    unsigned hits = 0;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const unsigned w = __shfl_sync(FULL_MASK, m, 2 * i + (r >> 2));
+        const unsigned fa = head ? ((w >> (8 * (r & 3))) & 0xFFu) : 0u;
+        int d0, d1;
+        asm volatile(
+            "mma.sync.aligned.m8n8k128.row.col.s32.b1.b1.s32.and.popc {%0,%1}, {%2}, {%3}, {%4,%5};\n"
+            : "=r"(d0), "=r"(d1)
+            : "r"(fa), "r"(fb), "r"(0), "r"(0));
+        const unsigned hb = __ballot_sync(FULL_MASK, head && d0 != 0);   // bit 4r: slice 8i + r
+        if ((lane >> 1) == i) {
+            const unsigned x = hb >> (16 * (lane & 1));                   // rows 4h .. 4h + 3
+            hits = (x & 1u) | ((x >> 3) & 2u) | ((x >> 6) & 4u) | ((x >> 9) & 8u);
+        }
+    }
+    return hits;
+}
+
 // the theta row ids of lane word `word` (one 4-, 8- or 16-byte load)
 template <int THETA>
 __device__ __forceinline__ void load_rows(const int *__restrict__ rowIds, size_t word, int (&r)[4]) {
@@ -141,6 +176,19 @@ __device__ __forceinline__ void clear_field(unsigned *F, int ss) {
     else F[ss] = 0u;
 }
 
+// position of the k-th (0-based) set bit of x
+__device__ __forceinline__ int nth_set_bit(unsigned x, int k) {
+    int pos = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+        const unsigned lo = x & ((1u << step) - 1u);
+        const int c = __popc(lo);
+        if (k >= c) { k -= c; x >>= step; pos += step; }
+        else x = lo;
+    }
+    return pos;
+}
+
 // Queue appends are staged per warp in shared memory and reserved in the
 // global queues once per STG_Q entries: every warp reserving its own few
 // entries with one atomic on the same two counters serialises tens of
@@ -148,6 +196,23 @@ __device__ __forceinline__ void clear_field(unsigned *F, int ss) {
 constexpr int STG_Q = 256;   // staged VSS entries per warp
 constexpr int STG_S = 128;   // staged slice-set ids per warp (>= 32 lanes x 4 sets)
 constexpr int STG_BYTES = STG_Q * 8 + STG_S * 4;
+
+// Per-CTA totals of a level's appends and counters (shared memory, zeroed at
+// the level start): the level's last flush reserves queue space and adds
+// the counters once per CTA instead of once per warp, so the control block
+// sees a few hundred atomics per level rather than thousands.  Long VSS
+// ranges (a hub's slice set spans thousands of VSSs) are reserved at once
+// and listed here, and the whole CTA writes them at the flush, so no warp
+// is left alone with thousands of stores at the end of a level.
+constexpr int BIG_MAX = 64;
+struct BlkAcc {
+    int q, s;                       // staged queue entries / slice-set ids of the CTA
+    int qbase, sbase;               // the CTA's reserved offsets
+    unsigned long long nv, fe;      // newly visited vertices and their out-arcs
+    unsigned long long sv, sa;      // bottom-up: probed vertices and extra arcs read
+    int nbig;                       // long ranges listed (may exceed BIG_MAX: the rest are written inline)
+    int4 big[BIG_MAX];              // {first VSS, count, slice set, queue position}
+};
 
 struct Stage {
     int2 *q;     // this warp's staging area in shared memory
@@ -166,7 +231,7 @@ __device__ __forceinline__ void stage_flush(const BfsParams &P, Stage &st, int2 
     }
     qb = __shfl_sync(FULL_MASK, qb, 0);
     sb = __shfl_sync(FULL_MASK, sb, 0);
-    for (int k = lane; k < st.qn; k += 32) Q[qb + k] = st.q[k];
+    for (int k = lane; k < st.qn && qb + k < P.qcap; k += 32) Q[qb + k] = st.q[k];
     for (int k = lane; k < st.sqn; k += 32) SQ[sb + k] = st.sq[k];
     __syncwarp();
     st.qn = 0;
@@ -176,59 +241,22 @@ __device__ __forceinline__ void stage_flush(const BfsParams &P, Stage &st, int2 
 // Warp-aggregated enqueue of up to 4 slice sets per lane (bit c of `want`
 // set => slice set ss[c], whose VSSs are [a[c], a[c] + len[c])): the VSS
 // ranges go to Q, the set ids to SQ, both through the warp's staging area.
-// Short ranges are written by their own lane; a long range (the slice set
-// of a hub vertex spans thousands of VSSs) by the whole warp, so no lane
-// issues a long serial run of stores; a batch larger than the staging area
-// reserves its own space in Q.
+// Short ranges are written by their own lane, medium ones by the whole
+// warp, long ones (at least ENQ_CTA_MIN VSSs) are reserved at once and
+// written by the whole CTA at the level's flush; a batch larger than the
+// staging area reserves its own space in Q.  Every entry is counted in the
+// level's queue length; entries at positions >= qcap are not written.
 constexpr int ENQ_LANE_MAX = 8;
+constexpr int ENQ_CTA_MIN = 64;
 
-__device__ __forceinline__ void enqueue_ranges(const BfsParams &P, Stage &st, unsigned want, const int ss[4],
-                                               const int a[4], const int len[4], int2 *Q, int *SQ, int slot) {
+__device__ __forceinline__ void warp_write_ranges(const BfsParams &P, unsigned sel, const int a[4], const int len[4],
+                                                  const int pos[4], const int ss[4], int2 *dst, int lim) {
     const int lane = lane_id();
-    if (!__any_sync(FULL_MASK, want != 0)) return;
-    int tot = 0, nset = 0;
-#pragma unroll
-    for (int c = 0; c < 4; ++c)
-        if (want >> c & 1u) { tot += len[c]; ++nset; }
-    const int incl = warp_incl_scan(tot);
-    const int sincl = warp_incl_scan(nset);
-    const int T = __shfl_sync(FULL_MASK, incl, 31);
-    const int S = __shfl_sync(FULL_MASK, sincl, 31);
-    if ((T <= STG_Q && st.qn + T > STG_Q) || st.sqn + S > STG_S) stage_flush(P, st, Q, SQ, slot);
-    int2 *dst;
-    int qbase;
-    if (T > STG_Q) {
-        int g = 0;
-        if (lane == 31) g = atomicAdd(&P.ctl->qlen[slot], T);
-        dst = Q + __shfl_sync(FULL_MASK, g, 31);
-        qbase = incl - tot;
-    } else {
-        dst = st.q;
-        qbase = st.qn + incl - tot;
-        st.qn += T;
-    }
-    int sbase = st.sqn + sincl - nset;
-    st.sqn += S;
-    int pos[4];
-    unsigned big = 0;
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        pos[c] = qbase;
-        if (want >> c & 1u) {
-            st.sq[sbase++] = ss[c];
-            if (len[c] <= ENQ_LANE_MAX) {
-                for (int k = 0; k < len[c]; ++k) dst[qbase + k] = make_int2(a[c] + k, ss[c]);
-            } else {
-                big |= 1u << c;
-            }
-            qbase += len[c];
-        }
-    }
-    unsigned lanes = __ballot_sync(FULL_MASK, big != 0);
+    unsigned lanes = __ballot_sync(FULL_MASK, sel != 0);
     while (lanes) {
         const int j = __ffs(lanes) - 1;
         lanes &= lanes - 1u;
-        const unsigned bj = __shfl_sync(FULL_MASK, big, j);
+        const unsigned bj = __shfl_sync(FULL_MASK, sel, j);
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             const int aj = __shfl_sync(FULL_MASK, a[c], j);
@@ -236,22 +264,86 @@ __device__ __forceinline__ void enqueue_ranges(const BfsParams &P, Stage &st, un
             const int pj = __shfl_sync(FULL_MASK, pos[c], j);
             const int sj = __shfl_sync(FULL_MASK, ss[c], j);
             if (bj >> c & 1u)   // warp-uniform
-                for (int k = lane; k < lj; k += 32) dst[pj + k] = make_int2(aj + k, sj);
+                for (int k = lane; k < lj && pj + k < lim; k += 32) dst[pj + k] = make_int2(aj + k, sj);
         }
     }
-    __syncwarp();
 }
 
-// Per-CTA totals of a level's appends and counters (shared memory, zeroed at
-// the level start): the level's last flush reserves queue space and adds
-// the counters once per CTA instead of once per warp, so the control block
-// sees a few hundred atomics per level rather than thousands.
-struct BlkAcc {
-    int q, s;                       // staged queue entries / slice-set ids of the CTA
-    int qbase, sbase;               // the CTA's reserved offsets
-    unsigned long long nv, fe;      // newly visited vertices and their out-arcs
-    unsigned long long sv, sa;      // bottom-up: probed vertices and extra arcs read
-};
+__device__ __forceinline__ void enqueue_ranges(const BfsParams &P, Stage &st, BlkAcc *acc, unsigned want,
+                                               const int ss[4], const int a[4], const int len[4], int2 *Q, int *SQ,
+                                               int slot) {
+    const int lane = lane_id();
+    if (!__any_sync(FULL_MASK, want != 0)) return;
+    // long ranges: reserved one by one and listed for the CTA-wide write
+    unsigned longr = 0;
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+        if ((want >> c & 1u) && len[c] >= ENQ_CTA_MIN) longr |= 1u << c;
+    if (__any_sync(FULL_MASK, longr != 0)) {
+        unsigned ovf = 0;
+        int opos[4] = {0, 0, 0, 0};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            if (longr >> c & 1u) {
+                const int p = atomicAdd(&P.ctl->qlen[slot], len[c]);
+                opos[c] = p;
+                if (p < P.qcap) {
+                    const int i = atomicAdd(&acc->nbig, 1);
+                    if (i < BIG_MAX) acc->big[i] = make_int4(a[c], min(len[c], P.qcap - p), ss[c], p);
+                    else ovf |= 1u << c;   // the CTA list is full: the warp writes it now
+                }
+            }
+        }
+        if (__any_sync(FULL_MASK, ovf != 0)) warp_write_ranges(P, ovf, a, len, opos, ss, Q, P.qcap);
+    }
+    int tot = 0, nset = 0;
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+        if (want >> c & 1u) {
+            ++nset;
+            if (!(longr >> c & 1u)) tot += len[c];
+        }
+    const int incl = warp_incl_scan(tot);
+    const int sincl = warp_incl_scan(nset);
+    const int T = __shfl_sync(FULL_MASK, incl, 31);
+    const int S = __shfl_sync(FULL_MASK, sincl, 31);
+    if ((T <= STG_Q && st.qn + T > STG_Q) || st.sqn + S > STG_S) stage_flush(P, st, Q, SQ, slot);
+    int2 *dst;
+    int qbase, lim;
+    if (T > STG_Q) {
+        int g = 0;
+        if (lane == 31) g = atomicAdd(&P.ctl->qlen[slot], T);
+        g = __shfl_sync(FULL_MASK, g, 31);
+        dst = Q + g;
+        lim = P.qcap - g;   // positions past the cap are counted, not written
+        qbase = incl - tot;
+    } else {
+        dst = st.q;
+        lim = STG_Q;        // the flush applies the cap
+        qbase = st.qn + incl - tot;
+        st.qn += T;
+    }
+    int sbase = st.sqn + sincl - nset;
+    st.sqn += S;
+    int pos[4];
+    unsigned mid = 0;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        pos[c] = qbase;
+        if (want >> c & 1u) {
+            st.sq[sbase++] = ss[c];
+            if (longr >> c & 1u) continue;
+            if (len[c] <= ENQ_LANE_MAX) {
+                for (int k = 0; k < len[c] && qbase + k < lim; ++k) dst[qbase + k] = make_int2(a[c] + k, ss[c]);
+            } else {
+                mid |= 1u << c;
+            }
+            qbase += len[c];
+        }
+    }
+    warp_write_ranges(P, mid, a, len, pos, ss, dst, lim);
+    __syncwarp();
+}
 
 // Called by every thread of the CTA at the end of a level's last phase.
 __device__ __forceinline__ void block_flush(const BfsParams &P, Stage &st, BlkAcc *acc, int2 *Q, int *SQ, int slot,
@@ -285,8 +377,14 @@ __device__ __forceinline__ void block_flush(const BfsParams &P, Stage &st, BlkAc
     }
     __syncthreads();
     const int qb = acc->qbase + wq, sb = acc->sbase + ws;
-    for (int k = lane; k < st.qn; k += 32) Q[qb + k] = st.q[k];
+    for (int k = lane; k < st.qn && qb + k < P.qcap; k += 32) Q[qb + k] = st.q[k];
     for (int k = lane; k < st.sqn; k += 32) SQ[sb + k] = st.sq[k];
+    // the CTA's long ranges, all threads on each in turn
+    const int nb = min(acc->nbig, BIG_MAX);
+    for (int e = 0; e < nb; ++e) {
+        const int4 r = acc->big[e];
+        for (int k = (int)threadIdx.x; k < r.y; k += (int)blockDim.x) Q[r.w + k] = make_int2(r.x + k, r.z);
+    }
     __syncwarp();
     st.qn = 0;
     st.sqn = 0;
@@ -298,146 +396,193 @@ __device__ __forceinline__ void block_flush(const BfsParams &P, Stage &st, BlkAc
 // in flight: it loads the B*G queue entries, then their slices and masks,
 // then their frontier fields, before using any of them, so the
 // dependent-load chain is paid once per B*G VSSs.
-template <bool EAGER, bool TC, int B, int SIGMA, int LPV>
-__device__ void push_level(const BfsParams &P, Stage &st, int *grab, BlkAcc *acc, int ell, int bc, int bn, int slot,
-                           int qlen, unsigned bsel) {
+// The VSS entries of one warp pass: lane j < B*G holds entry j ({VSS, slice
+// set}, VSS -1 = none), nent of them valid; lane group g of LPV lanes
+// handles entries g, g + G, ... (B of them, loaded before any is used).
+template <bool EAGER, int HIT, int B, int SIGMA, int LPV>
+__device__ __forceinline__ void push_entries(const BfsParams &P, Stage &st, BlkAcc *acc, int ell, int bc, int bn,
+                                             int slot, unsigned bsel, int2 mine, int nent, unsigned long long &nv,
+                                             unsigned long long &fe) {
     using LY = Lay<SIGMA, LPV>;
     constexpr int THETA = LY::THETA, G = LY::G;
     const int lane = lane_id();
     const int grp = lane / LPV, sl = lane % LPV;
     const unsigned *Fc = P.F[bc];
     unsigned *Fn = P.F[bn];
+    int vss[B], ss[B];
+    int r[B][4];
+    unsigned m[B], alpha[B];
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+        vss[b] = __shfl_sync(FULL_MASK, mine.x, b * G + grp);
+        ss[b] = __shfl_sync(FULL_MASK, mine.y, b * G + grp);
+    }
+    // slices, masks and frontier fields of the VSSs are independent loads
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+        if (vss[b] >= 0) {
+            load_rows<THETA>(P.rowIds, (size_t)vss[b] * LPV + sl, r[b]);
+            m[b] = __ldg(&P.masks[(size_t)vss[b] * LPV + sl]);
+            alpha[b] = ld_field<SIGMA>(Fc, ss[b]);
+        } else {
+            r[b][0] = r[b][1] = r[b][2] = r[b][3] = 0;
+            m[b] = 0u;
+            alpha[b] = 0u;
+        }
+    }
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+        if (b * G >= nent) continue;   // warp-uniform: no group has an entry
+        unsigned hits;
+        if constexpr (HIT == 1) hits = hits_tc(m[b], alpha[b], bsel);
+        else if constexpr (HIT == 2) hits = hits_tc16(m[b], alpha[b]);
+        else hits = hits_cc<SIGMA>(m[b], alpha[b]);
+        if (EAGER) {
+            // phase 1: visited words of the hit rows (independent loads)
+            int u[4];
+            unsigned vw[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                u[c] = r[b][c];
+                vw[c] = (c < THETA && (hits >> c & 1u)) ? P.Vc[u[c] >> 5] : 0xFFFFFFFFu;
+            }
+            // phase 2: claim the unvisited ones, one atomic per candidate row (the
+            // lanes' atomics on a word are serialised by the memory system, so
+            // exactly one lane sees each bit and each slice-set field clear;
+            // combining them across the warp first costs more than it saves).
+            // All of a lane's atomics and its degree and VSS-range loads are
+            // issued before any result is used: one round trip together.
+            unsigned old[4];
+            int dg[4], a[4], len[4], sso[4];
+            unsigned cand = 0;
+#pragma unroll
+            for (int c = 0; c < THETA; ++c) {
+                const bool cd = !(vw[c] >> (u[c] & 31) & 1u);
+                old[c] = 0xFFFFFFFFu;
+                if (cd) {
+                    old[c] = atomicOr(&Fn[u[c] >> 5], 1u << (u[c] & 31));
+                    cand |= 1u << c;
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                sso[c] = c < THETA ? (u[c] >> LY::LOGS) : 0;
+                dg[c] = 0;
+                a[c] = 0;
+                len[c] = 0;
+                if (cand >> c & 1u) {
+                    dg[c] = __ldg(&P.deg[u[c]]);
+                    a[c] = __ldg(&P.realPtrs[sso[c]]);
+                    len[c] = __ldg(&P.realPtrs[sso[c] + 1]);
+                }
+            }
+            // phase 3: winners set their level and visited bits (one OR per word
+            // among the lane's own rows, which ascend); the first claim of a
+            // slice-set field enqueues its VSSs (once per set)
+            unsigned want = 0, wbits = 0;
+            int wword = -1;
+#pragma unroll
+            for (int c = 0; c < THETA; ++c) {
+                const bool win = (cand >> c & 1u) && !(old[c] >> (u[c] & 31) & 1u);
+                if (win) {
+                    const int wd = u[c] >> 5;
+                    if (wd != wword) {
+                        if (wword >= 0) {
+                            red_or(&P.Vc[wword], wbits);
+                            red_or(&P.Vn[wword], wbits);
+                        }
+                        wword = wd;
+                        wbits = 0;
+                    }
+                    wbits |= 1u << (u[c] & 31);
+                    P.L[u[c]] = ell;
+                    nv += 1;
+                    fe += (unsigned long long)dg[c];
+                    const int fo = u[c] & (31 & ~(SIGMA - 1));   // the set's field in the word
+                    if (((old[c] >> fo) & LY::FMASK) == 0) want |= 1u << c;
+                }
+                len[c] -= a[c];
+            }
+            if (wword >= 0) {
+                red_or(&P.Vc[wword], wbits);
+                red_or(&P.Vn[wword], wbits);
+            }
+            enqueue_ranges(P, st, acc, want, sso, a, len, P.Q[bn], P.SQ[bn], slot);
+        } else {
+            // lazy marking: fire-and-forget ORs into V_next, one per distinct word
+            // among the lane's own rows (they ascend, so equal words are adjacent)
+            unsigned mbits = 0;
+            int mword = -1;
+#pragma unroll
+            for (int c = 0; c < THETA; ++c) {
+                if (hits >> c & 1u) {
+                    const int u = r[b][c];
+                    if ((u >> 5) != mword) {
+                        if (mword >= 0) red_or(&P.Vn[mword], mbits);
+                        mword = u >> 5;
+                        mbits = 0;
+                    }
+                    mbits |= 1u << (u & 31);
+                }
+            }
+            if (mword >= 0) red_or(&P.Vn[mword], mbits);
+        }
+    }
+}
+
+// Eager (Algorithm 2) or lazy (Algorithm 3 stage 1) top-down level.  A warp
+// pass covers G VSSs (one per lane group of LPV lanes); a warp keeps B passes
+// in flight: it loads the B*G queue entries, then their slices and masks,
+// then their frontier fields, before using any of them, so the
+// dependent-load chain is paid once per B*G VSSs.  Passes are interleaved
+// over the blocks; the warps of a block claim their block's next pass from
+// a shared counter, so a warp whose passes hit many rows does not hold up
+// the level.  A queue longer than qcap was counted but not written: the
+// level then scans all VSSs, 32 per claim, keeping those whose slice set
+// has a frontier bit (the frontier F is exact), B*G at a time.
+template <bool EAGER, int HIT, int B, int SIGMA, int LPV>
+__device__ void push_level(const BfsParams &P, Stage &st, int *grab, BlkAcc *acc, int ell, int bc, int bn, int slot,
+                           int qlen, unsigned bsel) {
+    using LY = Lay<SIGMA, LPV>;
+    constexpr int G = LY::G;
+    const int lane = lane_id();
+    const unsigned *Fc = P.F[bc];
     const int2 *Qc = P.Q[bc];
     unsigned long long nv = 0, fe = 0;
-    // passes of B*G queue entries, interleaved over the blocks; the warps of a
-    // block claim their block's next pass from a shared counter, so a warp
-    // whose passes hit many rows does not hold up the level
-    const int npass = (qlen + B * G - 1) / (B * G);
-    for (;;) {
-        int k = 0;
-        if (lane == 0) k = atomicAdd(grab, 1);
-        k = __shfl_sync(FULL_MASK, k, 0);
-        const int pass = (int)blockIdx.x + k * (int)gridDim.x;
-        if (pass >= npass) break;
-        const int w0 = pass * B * G;
-        int vss[B], ss[B];
-        int r[B][4];
-        unsigned m[B], alpha[B];
-        // lane j < B*G fetches queue entry w0 + j (VSS and slice set); shuffles spread them
-        const int2 mine = (lane < B * G && w0 + lane < qlen) ? Qc[w0 + lane] : make_int2(-1, 0);
-#pragma unroll
-        for (int b = 0; b < B; ++b) {
-            vss[b] = __shfl_sync(FULL_MASK, mine.x, b * G + grp);
-            ss[b] = __shfl_sync(FULL_MASK, mine.y, b * G + grp);
+    if (qlen <= P.qcap) {
+        const int npass = (qlen + B * G - 1) / (B * G);
+        for (;;) {
+            int k = 0;
+            if (lane == 0) k = atomicAdd(grab, 1);
+            k = __shfl_sync(FULL_MASK, k, 0);
+            const int pass = (int)blockIdx.x + k * (int)gridDim.x;
+            if (pass >= npass) break;
+            const int w0 = pass * B * G;
+            // lane j < B*G fetches queue entry w0 + j (VSS and slice set)
+            const int2 mine = (lane < B * G && w0 + lane < qlen) ? Qc[w0 + lane] : make_int2(-1, 0);
+            push_entries<EAGER, HIT, B, SIGMA, LPV>(P, st, acc, ell, bc, bn, slot, bsel, mine, qlen - w0, nv, fe);
         }
-        // slices, masks and frontier fields of the VSSs are independent loads
-#pragma unroll
-        for (int b = 0; b < B; ++b) {
-            if (vss[b] >= 0) {
-                load_rows<THETA>(P.rowIds, (size_t)vss[b] * LPV + sl, r[b]);
-                m[b] = __ldg(&P.masks[(size_t)vss[b] * LPV + sl]);
-                alpha[b] = ld_field<SIGMA>(Fc, ss[b]);
-            } else {
-                r[b][0] = r[b][1] = r[b][2] = r[b][3] = 0;
-                m[b] = 0u;
-                alpha[b] = 0u;
-            }
-        }
-#pragma unroll
-        for (int b = 0; b < B; ++b) {
-            if (w0 + b * G >= qlen) continue;   // warp-uniform: no group has an entry
-            unsigned hits;
-            if constexpr (TC) hits = hits_tc(m[b], alpha[b], bsel);
-            else hits = hits_cc<SIGMA>(m[b], alpha[b]);
-            if (EAGER) {
-                // phase 1: visited words of the hit rows (independent loads)
-                int u[4];
-                unsigned vw[4];
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    u[c] = r[b][c];
-                    vw[c] = (c < THETA && (hits >> c & 1u)) ? P.Vc[u[c] >> 5] : 0xFFFFFFFFu;
-                }
-                // phase 2: claim the unvisited ones, one atomic per candidate row (the
-                // lanes' atomics on a word are serialised by the memory system, so
-                // exactly one lane sees each bit and each slice-set field clear;
-                // combining them across the warp first costs more than it saves).
-                // All of a lane's atomics and its degree and VSS-range loads are
-                // issued before any result is used: one round trip together.
-                unsigned old[4];
-                int dg[4], a[4], len[4], sso[4];
-                unsigned cand = 0;
-#pragma unroll
-                for (int c = 0; c < THETA; ++c) {
-                    const bool cd = !(vw[c] >> (u[c] & 31) & 1u);
-                    old[c] = 0xFFFFFFFFu;
-                    if (cd) {
-                        old[c] = atomicOr(&Fn[u[c] >> 5], 1u << (u[c] & 31));
-                        cand |= 1u << c;
-                    }
-                }
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    sso[c] = c < THETA ? (u[c] >> LY::LOGS) : 0;
-                    dg[c] = 0;
-                    a[c] = 0;
-                    len[c] = 0;
-                    if (cand >> c & 1u) {
-                        dg[c] = __ldg(&P.deg[u[c]]);
-                        a[c] = __ldg(&P.realPtrs[sso[c]]);
-                        len[c] = __ldg(&P.realPtrs[sso[c] + 1]);
-                    }
-                }
-                // phase 3: winners set their level and visited bits (one OR per word
-                // among the lane's own rows, which ascend); the first claim of a
-                // slice-set field enqueues its VSSs (once per set)
-                unsigned want = 0, wbits = 0;
-                int wword = -1;
-#pragma unroll
-                for (int c = 0; c < THETA; ++c) {
-                    const bool win = (cand >> c & 1u) && !(old[c] >> (u[c] & 31) & 1u);
-                    if (win) {
-                        const int wd = u[c] >> 5;
-                        if (wd != wword) {
-                            if (wword >= 0) {
-                                red_or(&P.Vc[wword], wbits);
-                                red_or(&P.Vn[wword], wbits);
-                            }
-                            wword = wd;
-                            wbits = 0;
-                        }
-                        wbits |= 1u << (u[c] & 31);
-                        P.L[u[c]] = ell;
-                        nv += 1;
-                        fe += (unsigned long long)dg[c];
-                        const int fo = u[c] & (31 & ~(SIGMA - 1));   // the set's field in the word
-                        if (((old[c] >> fo) & LY::FMASK) == 0) want |= 1u << c;
-                    }
-                    len[c] -= a[c];
-                }
-                if (wword >= 0) {
-                    red_or(&P.Vc[wword], wbits);
-                    red_or(&P.Vn[wword], wbits);
-                }
-                enqueue_ranges(P, st, want, sso, a, len, P.Q[bn], P.SQ[bn], slot);
-            } else {
-                // lazy marking: fire-and-forget ORs into V_next, one per distinct word
-                // among the lane's own rows (they ascend, so equal words are adjacent)
-                unsigned mbits = 0;
-                int mword = -1;
-#pragma unroll
-                for (int c = 0; c < THETA; ++c) {
-                    if (hits >> c & 1u) {
-                        const int u = r[b][c];
-                        if ((u >> 5) != mword) {
-                            if (mword >= 0) red_or(&P.Vn[mword], mbits);
-                            mword = u >> 5;
-                            mbits = 0;
-                        }
-                        mbits |= 1u << (u & 31);
-                    }
-                }
-                if (mword >= 0) red_or(&P.Vn[mword], mbits);
+    } else {
+        // (the scan's state stays inside this branch: the queue loop above is
+        // the one small levels run, and it keeps its register budget)
+        const int nchunk = (P.Nv + 31) / 32;
+        for (;;) {
+            int k = 0;
+            if (lane == 0) k = atomicAdd(grab, 1);
+            k = __shfl_sync(FULL_MASK, k, 0);
+            const int chunk = (int)blockIdx.x + k * (int)gridDim.x;
+            if (chunk >= nchunk) break;
+            const int cv = chunk * 32 + lane;
+            const int cs = cv < P.Nv ? __ldg(&P.v2r[cv]) : -1;
+            unsigned am = __ballot_sync(FULL_MASK, cs >= 0 && ld_field<SIGMA>(Fc, cs) != 0u);
+            while (am) {   // warp-uniform: the chunk's active VSSs, B*G at a time
+                const int take = min(__popc(am), B * G);
+                const int src = nth_set_bit(am, lane < take ? lane : 0);
+                const int v_ = __shfl_sync(FULL_MASK, cv, src);
+                const int s_ = __shfl_sync(FULL_MASK, cs, src);
+                const int2 mine = lane < take ? make_int2(v_, s_) : make_int2(-1, 0);
+                for (int t = 0; t < take; ++t) am &= am - 1u;
+                push_entries<EAGER, HIT, B, SIGMA, LPV>(P, st, acc, ell, bc, bn, slot, bsel, mine, take, nv, fe);
             }
         }
     }
@@ -453,25 +598,290 @@ __device__ void push_level(const BfsParams &P, Stage &st, int *grab, BlkAcc *acc
 // probes its in-neighbours four at a time: four column loads, then four
 // frontier-bit loads, then the test.  Found bits collect in shared memory
 // and each word's V_next is written once by the warp that owns it.
-__device__ __forceinline__ int nth_set_bit(unsigned x, int k) {
-    // position of the k-th (0-based) set bit of x
-    int pos = 0;
+
+// Algorithm 4's test for one unvisited vertex u (act): is any in-neighbour
+// in the frontier?  The first four in-neighbours (rows sorted by descending
+// degree) come from the 16-byte head hd; the highest-degree one is probed
+// alone first (the likeliest frontier member), the other three only where
+// it missed, which keeps the random frontier-word reads through L2 to about
+// one a vertex; longer rows then read four ids per step.
+__device__ __forceinline__ bool bu_probe_head(const BfsParams &P, const unsigned *Fc, int u, bool act, const int4 &hd,
+                                              unsigned long long &sa) {
+    const int v0 = hd.x;
+    const unsigned f0 = v0 >= 0 ? Fc[v0 >> 5] : 0u;
+    bool hit = (v0 >= 0) && ((f0 >> (v0 & 31)) & 1u);
+    unsigned fw[3];
 #pragma unroll
-    for (int step = 16; step > 0; step >>= 1) {
-        const unsigned lo = x & ((1u << step) - 1u);
-        const int c = __popc(lo);
-        if (k >= c) { k -= c; x >>= step; pos += step; }
-        else x = lo;
+    for (int q = 1; q < 4; ++q) {
+        const int vq = pick(hd, q);
+        fw[q - 1] = (!hit && vq >= 0) ? Fc[vq >> 5] : 0u;
     }
-    return pos;
+#pragma unroll
+    for (int q = 1; q < 4; ++q) {
+        const int vq = pick(hd, q);
+        hit |= (vq >= 0) && ((fw[q - 1] >> (vq & 31)) & 1u);
+    }
+    if (act && !hit && hd.w >= 0) {
+        long long p = __ldg(&P.rp[u]) + 4;
+        const long long e = __ldg(&P.rp[u + 1]);
+        while (!hit && p < e) {
+            sa += (unsigned long long)((e - p) < 4 ? (e - p) : 4);
+            int w4[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) w4[q] = (p + q < e) ? __ldg(&P.col[p + q]) : -1;
+            unsigned f4[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) f4[q] = w4[q] >= 0 ? Fc[w4[q] >> 5] : 0u;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) hit |= (w4[q] >= 0) && ((f4[q] >> (w4[q] & 31)) & 1u);
+            p += 4;
+        }
+    }
+    return act && hit;
 }
 
-__device__ void bottom_up_level(const BfsParams &P, int *grab, BlkAcc *acc, int bc, int slot, unsigned *s_found) {
+// Probes of one 32-word group, compacted: the unvisited vertices (with an
+// in-neighbour) of the group are numbered and handled two per lane per
+// round.  Returns the lane's word of found bits (word base + lane).
+__device__ __forceinline__ unsigned bu_probe_compact(const BfsParams &P, const unsigned *Fc, int base, unsigned unv,
+                                                     unsigned *found, unsigned long long &sv,
+                                                     unsigned long long &sa) {
+    const int lane = lane_id();
+    found[lane] = 0u;
+    const int cnt = __popc(unv);
+    const int incl = warp_incl_scan(cnt);
+    const int total = __shfl_sync(FULL_MASK, incl, 31);
+    const int excl = incl - cnt;
+    __syncwarp();
+    // two compacted vertices per lane per round: idx = b + lane and b + 32 + lane
+    for (int b = 0; b < total; b += 64) {
+        int u[2];
+        bool act[2], hit[2];
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int idx = b + 32 * k + lane;
+            act[k] = idx < total;
+            hit[k] = false;
+            // owner lane: the largest lane whose exclusive prefix is <= idx (a lane with
+            // cnt == 0 shares its prefix with the next lane, so the largest one owns idx)
+            int j = 0;
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                const int ex = __shfl_sync(FULL_MASK, excl, j + step);
+                if (idx >= ex) j += step;
+            }
+            const unsigned uj = __shfl_sync(FULL_MASK, unv, j);
+            const int ej = __shfl_sync(FULL_MASK, excl, j);
+            u[k] = act[k] ? ((base + j) << 5) + nth_set_bit(uj, idx - ej) : 0;
+        }
+        int4 hd[2];
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            hd[k] = act[k] ? __ldg(&P.head[u[k]]) : make_int4(-1, -1, -1, -1);
+            if (act[k]) sv += 1;
+        }
+#pragma unroll
+        for (int k = 0; k < 2; ++k) hit[k] = bu_probe_head(P, Fc, u[k], act[k], hd[k], sa);
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+            if (act[k] && hit[k]) atomicOr(&found[(u[k] >> 5) - base], 1u << (u[k] & 31));
+    }
+    __syncwarp();
+    const unsigned f = found[lane];
+    __syncwarp();
+    return f;
+}
+
+// Probes of one 32-word group, direct: lane b handles vertex 32 w + b of
+// each word w that holds a candidate, four words at a time, so a lane keeps
+// four head loads in flight and the head loads of a word are one coalesced
+// 512-byte access.  For levels where most vertices are unvisited.
+constexpr int BU_K = 4;
+__device__ __forceinline__ unsigned bu_probe_direct(const BfsParams &P, const unsigned *Fc, int base, unsigned unv,
+                                                    unsigned long long &sv, unsigned long long &sa) {
+    const int lane = lane_id();
+    unsigned mine = 0u;
+    unsigned todo = __ballot_sync(FULL_MASK, unv != 0u);   // words with a candidate
+    while (todo) {   // warp-uniform
+        int wj[BU_K];
+        unsigned uw[BU_K];
+#pragma unroll
+        for (int k = 0; k < BU_K; ++k) {
+            wj[k] = todo ? __ffs(todo) - 1 : -1;
+            todo &= todo ? todo - 1u : 0u;
+            uw[k] = __shfl_sync(FULL_MASK, unv, wj[k] >= 0 ? wj[k] : 0);
+            if (wj[k] < 0) uw[k] = 0u;
+        }
+        int v[BU_K];
+        bool act[BU_K], hit[BU_K];
+        int4 hd[BU_K];
+#pragma unroll
+        for (int k = 0; k < BU_K; ++k) {
+            act[k] = (uw[k] >> lane) & 1u;
+            v[k] = ((base + (wj[k] >= 0 ? wj[k] : 0)) << 5) + lane;
+            hd[k] = act[k] ? __ldg(&P.head[v[k]]) : make_int4(-1, -1, -1, -1);
+            if (act[k]) sv += 1;
+        }
+#pragma unroll
+        for (int k = 0; k < BU_K; ++k) hit[k] = bu_probe_head(P, Fc, v[k], act[k], hd[k], sa);
+#pragma unroll
+        for (int k = 0; k < BU_K; ++k) {
+            const unsigned fb = __ballot_sync(FULL_MASK, act[k] && hit[k]);
+            if (lane == wj[k]) mine = fb;
+        }
+    }
+    return mine;
+}
+
+// --------------------------------------------------- stage 2 (finalize)
+// Algorithm 3 stage 2 for one group of 32 bitvector words (lane = word):
+// nx / cu are the lane's V_next / V_curr words; diff = nx ^ cu are the
+// vertices reached at this level.  F and V_curr take the new values (and
+// V_next too when write_vn: the fused bottom-up level computes nx in
+// registers); a word with at most four new vertices stores their levels and
+// loads their out-degrees from its own lane, a denser word is stored lane =
+// vertex, eight words per round, so those stores coalesce.  A word holds
+// theta = 32/SIGMA slice-set fields; a changed field enqueues its set.
+template <int SIGMA>
+__device__ __forceinline__ void finalize_group(const BfsParams &P, Stage &st, BlkAcc *acc, int base, unsigned nx,
+                                               unsigned cu,
+                                               bool write_vn, int ell, int bn, int slot, unsigned long long &nv,
+                                               unsigned long long &fe) {
+    constexpr int THETA = 32 / SIGMA;
+    constexpr unsigned FMASK = SIGMA == 32 ? 0xFFFFFFFFu : ((1u << SIGMA) - 1u);
+    const int lane = lane_id();
+    unsigned *Fn = P.F[bn];
+    const int t = base + lane;
+    unsigned diff = 0;
+    if (t < P.W) {
+        diff = nx ^ cu;
+        if (diff) {
+            P.Vc[t] = nx;
+            if (write_vn) P.Vn[t] = nx;
+            Fn[t] = diff;
+            nv += (unsigned long long)__popc(diff);
+        }
+    }
+    // the VSS ranges of the changed slice-set fields load together with the
+    // degrees below
+    unsigned want = 0;
+    int sso[4] = {0, 0, 0, 0}, ra[4] = {0, 0, 0, 0}, rl[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int c = 0; c < THETA; ++c) {
+        sso[c] = t * THETA + c;
+        if ((diff >> (SIGMA * c)) & FMASK) {
+            want |= 1u << c;
+            ra[c] = __ldg(&P.realPtrs[sso[c]]);
+            rl[c] = __ldg(&P.realPtrs[sso[c] + 1]);
+        }
+    }
+    // a sparse word (at most four new vertices): level stores and degree
+    // loads from its own lane, the degrees summed only after the enqueue
+    // below, so their latency overlaps it
+    const int pc = __popc(diff);
+    int dv[4] = {0, 0, 0, 0};
+    if (pc > 0 && pc <= 4) {
+        unsigned d = diff;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (d) {
+                const int v = t * 32 + __ffs(d) - 1;
+                d &= d - 1u;
+                dv[q] = __ldg(&P.deg[v]);
+                P.L[v] = ell;
+            }
+        }
+    }
+    // a dense word: one 16-byte degree load per group of four vertices
+    // holding a new one, all in flight together
+    if (pc > 4) {
+        const int4 *dq = reinterpret_cast<const int4 *>(P.deg) + (size_t)t * 8;
+        unsigned long long dsum = 0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const unsigned nib = (diff >> (4 * q)) & 0xFu;
+            if (nib) {
+                const int v0 = t * 32 + 4 * q;
+                int4 dd;
+                if (v0 + 4 <= P.n) {
+                    dd = __ldg(dq + q);
+                } else {   // the last, partial word: no load past vertex n - 1
+                    dd.x = __ldg(&P.deg[v0]);
+                    dd.y = v0 + 1 < P.n ? __ldg(&P.deg[v0 + 1]) : 0;
+                    dd.z = v0 + 2 < P.n ? __ldg(&P.deg[v0 + 2]) : 0;
+                    dd.w = v0 + 3 < P.n ? __ldg(&P.deg[v0 + 3]) : 0;
+                }
+                dsum += (unsigned long long)((nib & 1u ? dd.x : 0) + (nib & 2u ? dd.y : 0) +
+                                             (nib & 4u ? dd.z : 0) + (nib & 8u ? dd.w : 0));
+            }
+        }
+        fe += dsum;
+    }
+    const unsigned dense = __ballot_sync(FULL_MASK, pc > 4);
+    if (dense) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            if (!((dense >> (8 * r)) & 0xFFu)) continue;   // warp-uniform
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int j = 8 * r + k;
+                const unsigned dj = __shfl_sync(FULL_MASK, diff, j);
+                if ((dense >> j & 1u) && (dj >> lane & 1u)) P.L[((base + j) << 5) + lane] = ell;
+            }
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) rl[c] -= ra[c];
+    enqueue_ranges(P, st, acc, want, sso, ra, rl, P.Q[bn], P.SQ[bn], slot);
+    fe += (unsigned long long)(dv[0] + dv[1]) + (unsigned long long)(dv[2] + dv[3]);
+}
+
+// Stage 2 over all words: a claim covers two 32-word groups, i and i +
+// half, whose visited words are loaded before either is used; claims are
+// interleaved over the blocks and taken by the block's warps from a shared
+// counter (the changed words cluster, so a fixed split leaves a few warps
+// with most of the work).
+template <int SIGMA>
+__device__ void finalize_level(const BfsParams &P, Stage &st, int *grab, BlkAcc *acc, int ell, int bn, int slot) {
+    const int lane = lane_id();
+    unsigned long long nv = 0, fe = 0;
+    const int ngroups = (P.W + 31) / 32, half = (ngroups + 1) / 2;
+    for (;;) {
+        int k = 0;
+        if (lane == 0) k = atomicAdd(grab, 1);
+        k = __shfl_sync(FULL_MASK, k, 0);
+        const int i = (int)blockIdx.x + k * (int)gridDim.x;
+        if (i >= half) break;
+        unsigned nx[2], cu[2];
+#pragma unroll
+        for (int g2 = 0; g2 < 2; ++g2) {
+            const int tt = (i + g2 * half) * 32 + lane;
+            nx[g2] = tt < P.W ? P.Vn[tt] : 0u;
+            cu[g2] = tt < P.W ? P.Vc[tt] : 0u;
+        }
+#pragma unroll 1
+        for (int g2 = 0; g2 < 2; ++g2)
+            finalize_group<SIGMA>(P, st, acc, (i + g2 * half) * 32, nx[g2], cu[g2], false, ell, bn, slot, nv, fe);
+    }
+    block_flush(P, st, acc, P.Q[bn], P.SQ[bn], slot, nv, fe);
+}
+
+// ------------------------------------------------------------ bottom-up
+// Algorithm 4 stage 1 fused with stage 2.  A warp claims a group of 32
+// bitvector words (lane = word), keeps the unvisited vertices that have
+// in-neighbours (nz mask) and probes them (direct when most vertices are
+// unvisited, compacted otherwise).  Each word is owned by the warp that
+// claimed it and the probes read only the previous frontier F[bc], so the
+// warp finalises its own words at once (V_curr = V_next = visited | found,
+// F = found, levels, queue): one grid barrier per bottom-up level.
+template <int SIGMA>
+__device__ void bottom_up_level(const BfsParams &P, Stage &st, int *grab, BlkAcc *acc, int ell, int bc, int bn,
+                                int slot, unsigned *s_found, bool direct) {
     const int lane = lane_id();
     unsigned *found = s_found + (threadIdx.x >> 5) * 32;
     const unsigned *Fc = P.F[bc];
     const int tail = P.n & 31;
-    unsigned long long sv = 0, sa = 0;
+    unsigned long long sv = 0, sa = 0, nv = 0, fe = 0;
     // 32-word groups interleaved over the blocks, claimed by the block's warps
     const int ngroups = (P.W + 31) / 32;
     for (;;) {
@@ -488,222 +898,15 @@ __device__ void bottom_up_level(const BfsParams &P, int *grab, BlkAcc *acc, int 
             unv = ~vis & __ldg(&P.nz[w]);
             if (w == P.W - 1 && tail) unv &= (1u << tail) - 1u;
         }
-        found[lane] = 0u;
-        const int cnt = __popc(unv);
-        const int incl = warp_incl_scan(cnt);
-        const int total = __shfl_sync(FULL_MASK, incl, 31);
-        const int excl = incl - cnt;
-        __syncwarp();
-        // two compacted vertices per lane per round: idx = b + lane and b + 32 + lane
-        for (int b = 0; b < total; b += 64) {
-            int u[2];
-            bool act[2], hit[2];
-#pragma unroll
-            for (int k = 0; k < 2; ++k) {
-                const int idx = b + 32 * k + lane;
-                act[k] = idx < total;
-                hit[k] = false;
-                // owner lane: the largest lane whose exclusive prefix is <= idx (a lane with
-                // cnt == 0 shares its prefix with the next lane, so the largest one owns idx)
-                int j = 0;
-#pragma unroll
-                for (int step = 16; step > 0; step >>= 1) {
-                    const int ex = __shfl_sync(FULL_MASK, excl, j + step);
-                    if (idx >= ex) j += step;
-                }
-                const unsigned uj = __shfl_sync(FULL_MASK, unv, j);
-                const int ej = __shfl_sync(FULL_MASK, excl, j);
-                u[k] = act[k] ? ((base + j) << 5) + nth_set_bit(uj, idx - ej) : 0;
-            }
-            // first probe: the first four in-neighbours (rows sorted by
-            // descending degree) come from one coalesced 16-byte head load per
-            // vertex
-            int4 hd[2];
-#pragma unroll
-            for (int k = 0; k < 2; ++k) {
-                hd[k] = act[k] ? __ldg(&P.head[u[k]]) : make_int4(-1, -1, -1, -1);
-                if (act[k]) sv += 1;
-            }
-            // the highest-degree in-neighbour alone first (it is the likeliest
-            // frontier member); the other three only where it missed, which
-            // keeps the random frontier-word reads through L2 to about one a
-            // vertex
-#pragma unroll
-            for (int k = 0; k < 2; ++k) {
-                const int v0 = hd[k].x;
-                const unsigned f0 = v0 >= 0 ? Fc[v0 >> 5] : 0u;
-                hit[k] = (v0 >= 0) && ((f0 >> (v0 & 31)) & 1u);
-            }
-            unsigned fw[2][3];
-#pragma unroll
-            for (int k = 0; k < 2; ++k)
-#pragma unroll
-                for (int q = 1; q < 4; ++q) {
-                    const int vq = pick(hd[k], q);
-                    fw[k][q - 1] = (!hit[k] && vq >= 0) ? Fc[vq >> 5] : 0u;
-                }
-#pragma unroll
-            for (int k = 0; k < 2; ++k)
-#pragma unroll
-                for (int q = 1; q < 4; ++q) {
-                    const int vq = pick(hd[k], q);
-                    hit[k] |= (vq >= 0) && ((fw[k][q - 1] >> (vq & 31)) & 1u);
-                }
-            // rows longer than four: the rest of the row, four ids per step
-#pragma unroll
-            for (int k = 0; k < 2; ++k) {
-                if (act[k] && !hit[k] && hd[k].w >= 0) {
-                    long long p = __ldg(&P.rp[u[k]]) + 4;
-                    const long long e = __ldg(&P.rp[u[k] + 1]);
-                    while (!hit[k] && p < e) {
-                        sa += (unsigned long long)((e - p) < 4 ? (e - p) : 4);
-                        int w4[4];
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) w4[q] = (p + q < e) ? __ldg(&P.col[p + q]) : -1;
-                        unsigned f4[4];
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) f4[q] = w4[q] >= 0 ? Fc[w4[q] >> 5] : 0u;
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) hit[k] |= (w4[q] >= 0) && ((f4[q] >> (w4[q] & 31)) & 1u);
-                        p += 4;
-                    }
-                }
-                if (act[k] && hit[k]) atomicOr(&found[(u[k] >> 5) - base], 1u << (u[k] & 31));
-            }
-        }
-        __syncwarp();
-        const unsigned f = found[lane];
-        if (f) P.Vn[w] = vis | f;   // this warp owns word w in this phase
-        __syncwarp();
+        const unsigned f = direct ? bu_probe_direct(P, Fc, base, unv, sv, sa)
+                                  : bu_probe_compact(P, Fc, base, unv, found, sv, sa);
+        finalize_group<SIGMA>(P, st, acc, base, vis | f, vis, true, ell, bn, slot, nv, fe);
     }
-    // counted per CTA; the stage-2 flush of this level adds them to the control block
     sv = warp_sum(sv);
     sa = warp_sum(sa);
     if (lane == 0 && sv) {
         atomicAdd(&acc->sv, sv);
         atomicAdd(&acc->sa, sa);
-    }
-}
-
-// --------------------------------------------------- stage 2 (finalize)
-// Algorithm 3 stage 2.  Lane = word for the V_curr / V_next sweep, the F
-// writes and the enqueue; a word with at most four new vertices stores their
-// levels and loads their out-degrees from its own lane, a denser word is
-// stored lane = vertex, eight words per round, so those stores coalesce.  A
-// word holds theta = 32/SIGMA slice-set fields; a changed field enqueues its
-// set.
-template <int SIGMA>
-__device__ void finalize_level(const BfsParams &P, Stage &st, int *grab, BlkAcc *acc, int ell, int bn, int slot) {
-    constexpr int THETA = 32 / SIGMA;
-    constexpr unsigned FMASK = SIGMA == 32 ? 0xFFFFFFFFu : ((1u << SIGMA) - 1u);
-    const int lane = lane_id();
-    unsigned *Fn = P.F[bn];
-    unsigned long long nv = 0, fe = 0;
-    // a claim covers two 32-word groups, i and i + half, whose visited words
-    // are loaded before either is used; claims are interleaved over the blocks
-    // and taken by the block's warps from a shared counter (the changed words
-    // cluster, so a fixed split leaves a few warps with most of the work)
-    const int ngroups = (P.W + 31) / 32, half = (ngroups + 1) / 2;
-    for (;;) {
-      int k = 0;
-      if (lane == 0) k = atomicAdd(grab, 1);
-      k = __shfl_sync(FULL_MASK, k, 0);
-      const int i = (int)blockIdx.x + k * (int)gridDim.x;
-      if (i >= half) break;
-      unsigned nx[2], cu[2];
-#pragma unroll
-      for (int g2 = 0; g2 < 2; ++g2) {
-          const int tt = (i + g2 * half) * 32 + lane;
-          nx[g2] = tt < P.W ? P.Vn[tt] : 0u;
-          cu[g2] = tt < P.W ? P.Vc[tt] : 0u;
-
-      }
-#pragma unroll 1
-      for (int g2 = 0; g2 < 2; ++g2) {
-        const int base = (i + g2 * half) * 32;
-        const int t = base + lane;
-        unsigned diff = 0;
-        if (t < P.W) {
-            diff = nx[g2] ^ cu[g2];
-            if (diff) {
-                P.Vc[t] = nx[g2];
-                Fn[t] = diff;
-                nv += (unsigned long long)__popc(diff);
-            }
-        }
-        // the VSS ranges of the changed slice-set fields load together with the
-        // degrees below
-        unsigned want = 0;
-        int sso[4] = {0, 0, 0, 0}, ra[4] = {0, 0, 0, 0}, rl[4] = {0, 0, 0, 0};
-#pragma unroll
-        for (int c = 0; c < THETA; ++c) {
-            sso[c] = t * THETA + c;
-            if ((diff >> (SIGMA * c)) & FMASK) {
-                want |= 1u << c;
-                ra[c] = __ldg(&P.realPtrs[sso[c]]);
-                rl[c] = __ldg(&P.realPtrs[sso[c] + 1]);
-            }
-        }
-        // a sparse word (at most four new vertices): level stores and degree
-        // loads from its own lane, the degrees summed only after the enqueue
-        // below, so their latency overlaps it
-        const int pc = __popc(diff);
-        int dv[4] = {0, 0, 0, 0};
-        if (pc > 0 && pc <= 4) {
-            unsigned d = diff;
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                if (d) {
-                    const int v = t * 32 + __ffs(d) - 1;
-                    d &= d - 1u;
-                    dv[q] = __ldg(&P.deg[v]);
-                    P.L[v] = ell;
-                }
-            }
-        }
-        // a dense word: one 16-byte degree load per group of four vertices
-        // holding a new one, all in flight together
-        if (pc > 4) {
-            const int4 *dq = reinterpret_cast<const int4 *>(P.deg) + (size_t)t * 8;
-            unsigned long long dsum = 0;
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const unsigned nib = (diff >> (4 * q)) & 0xFu;
-                if (nib) {
-                    const int v0 = t * 32 + 4 * q;
-                    int4 dd;
-                    if (v0 + 4 <= P.n) {
-                        dd = __ldg(dq + q);
-                    } else {   // the last, partial word: no load past vertex n - 1
-                        dd.x = __ldg(&P.deg[v0]);
-                        dd.y = v0 + 1 < P.n ? __ldg(&P.deg[v0 + 1]) : 0;
-                        dd.z = v0 + 2 < P.n ? __ldg(&P.deg[v0 + 2]) : 0;
-                        dd.w = v0 + 3 < P.n ? __ldg(&P.deg[v0 + 3]) : 0;
-                    }
-                    dsum += (unsigned long long)((nib & 1u ? dd.x : 0) + (nib & 2u ? dd.y : 0) +
-                                                 (nib & 4u ? dd.z : 0) + (nib & 8u ? dd.w : 0));
-                }
-            }
-            fe += dsum;
-        }
-        const unsigned dense = __ballot_sync(FULL_MASK, pc > 4);
-        if (dense) {
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                if (!((dense >> (8 * r)) & 0xFFu)) continue;   // warp-uniform
-#pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    const int j = 8 * r + k;
-                    const unsigned dj = __shfl_sync(FULL_MASK, diff, j);
-                    if ((dense >> j & 1u) && (dj >> lane & 1u)) P.L[((base + j) << 5) + lane] = ell;
-                }
-            }
-        }
-#pragma unroll
-        for (int c = 0; c < 4; ++c) rl[c] -= ra[c];
-        enqueue_ranges(P, st, want, sso, ra, rl, P.Q[bn], P.SQ[bn], slot);
-        fe += (unsigned long long)(dv[0] + dv[1]) + (unsigned long long)(dv[2] + dv[3]);
-      }
     }
     block_flush(P, st, acc, P.Q[bn], P.SQ[bn], slot, nv, fe);
 }
@@ -769,23 +972,28 @@ __device__ __forceinline__ void push_dispatch(const BfsParams &P, Stage &st, int
                                               int bc, int bn, int sn, int qlen, unsigned bsel, int batch = 1) {
     // eager levels run one pass at a time (their atomics and loads already
     // overlap within a pass, and a second pass's state would not fit the
-    // 64-register budget of a 1024-thread CTA); lazy levels keep 1, 2 or 4
+    // 64-register budget of a 1024-thread CTA); lazy levels keep 1, 2 or 4.
+    // A tensor-core level runs the Fig. 3 layout, or the 16-MMA one when the
+    // handle's engine asks for it.
     if constexpr (EAGER) {
-        if constexpr (Lay<SIGMA, LPV>::TC_OK)
-            if (tc) { push_level<true, true, 1, SIGMA, LPV>(P, st, grab, acc, ell, bc, bn, sn, qlen, bsel); return; }
-        push_level<true, false, 1, SIGMA, LPV>(P, st, grab, acc, ell, bc, bn, sn, qlen, bsel);
+        if constexpr (Lay<SIGMA, LPV>::TC_OK) {
+            if (tc && P.tc16) { push_level<true, 2, 1, SIGMA, LPV>(P, st, grab, acc, ell, bc, bn, sn, qlen, bsel); return; }
+            if (tc) { push_level<true, 1, 1, SIGMA, LPV>(P, st, grab, acc, ell, bc, bn, sn, qlen, bsel); return; }
+        }
+        push_level<true, 0, 1, SIGMA, LPV>(P, st, grab, acc, ell, bc, bn, sn, qlen, bsel);
     } else {
         if constexpr (Lay<SIGMA, LPV>::TC_OK) {
+            if (tc && P.tc16) { push_level<false, 2, 1, SIGMA, LPV>(P, st, grab, acc, ell, bc, bn, sn, qlen, bsel); return; }
             if (tc) {
-                if (batch >= 4) push_level<false, true, 4, SIGMA, LPV>(P, st, grab, acc, ell, bc, bn, sn, qlen, bsel);
-                else if (batch >= 2) push_level<false, true, 2, SIGMA, LPV>(P, st, grab, acc, ell, bc, bn, sn, qlen, bsel);
-                else push_level<false, true, 1, SIGMA, LPV>(P, st, grab, acc, ell, bc, bn, sn, qlen, bsel);
+                if (batch >= 4) push_level<false, 1, 4, SIGMA, LPV>(P, st, grab, acc, ell, bc, bn, sn, qlen, bsel);
+                else if (batch >= 2) push_level<false, 1, 2, SIGMA, LPV>(P, st, grab, acc, ell, bc, bn, sn, qlen, bsel);
+                else push_level<false, 1, 1, SIGMA, LPV>(P, st, grab, acc, ell, bc, bn, sn, qlen, bsel);
                 return;
             }
         }
-        if (batch >= 4) push_level<false, false, 4, SIGMA, LPV>(P, st, grab, acc, ell, bc, bn, sn, qlen, bsel);
-        else if (batch >= 2) push_level<false, false, 2, SIGMA, LPV>(P, st, grab, acc, ell, bc, bn, sn, qlen, bsel);
-        else push_level<false, false, 1, SIGMA, LPV>(P, st, grab, acc, ell, bc, bn, sn, qlen, bsel);
+        if (batch >= 4) push_level<false, 0, 4, SIGMA, LPV>(P, st, grab, acc, ell, bc, bn, sn, qlen, bsel);
+        else if (batch >= 2) push_level<false, 0, 2, SIGMA, LPV>(P, st, grab, acc, ell, bc, bn, sn, qlen, bsel);
+        else push_level<false, 0, 1, SIGMA, LPV>(P, st, grab, acc, ell, bc, bn, sn, qlen, bsel);
     }
 }
 
@@ -897,6 +1105,7 @@ __global__ void __launch_bounds__(BFS_MAX_THREADS, 1) k_bfs(BfsParams P) {
                 s_acc.fe = 0;
                 s_acc.sv = 0;
                 s_acc.sa = 0;
+                s_acc.nbig = 0;
             }
         }
         __syncthreads();
@@ -917,7 +1126,8 @@ __global__ void __launch_bounds__(BFS_MAX_THREADS, 1) k_bfs(BfsParams P) {
             if (ell >= 2 && ell - 2 < P.log_cap) {
                 blest_level_log &prev = P.log[ell - 2];
                 prev.t_ns = t - prev.t_ns;
-                if (prev.mode == BLEST_MODE_PUSH_EAGER_CC || prev.mode == BLEST_MODE_PUSH_EAGER_TC)
+                if (prev.mode == BLEST_MODE_PUSH_EAGER_CC || prev.mode == BLEST_MODE_PUSH_EAGER_TC ||
+                    prev.mode == BLEST_MODE_BOTTOM_UP)
                     prev.t_stage1_ns = prev.t_ns;
                 prev.scanned_vertices = (long long)*(volatile unsigned long long *)&ctl->scan_v[sc];
                 prev.scanned_arcs = (long long)*(volatile unsigned long long *)&ctl->scan_a[sc];
@@ -946,12 +1156,16 @@ __global__ void __launch_bounds__(BFS_MAX_THREADS, 1) k_bfs(BfsParams P) {
             push_dispatch<true, SIGMA, LPV>(P, st, &s_grab[0], &s_acc, mode == BLEST_MODE_PUSH_EAGER_TC, ell, bc, bn, sn, qlen, bsel);
             housekeeping<SIGMA>(P, ell, bo, sql_old, sz, tid, nthreads);
             if (!grid_barrier(ctl, epoch, P.budget_ns)) return;
+        } else if (mode == BLEST_MODE_BOTTOM_UP) {
+            // direct probes while at least a quarter of the vertices are unvisited
+            bottom_up_level<SIGMA>(P, st, &s_grab[2], &s_acc, ell, bc, bn, sn, s_found, unvisited * 4 >= (long long)P.n);
+            housekeeping<SIGMA>(P, ell, bo, sql_old, sz, tid, nthreads);
+            if (!grid_barrier(ctl, epoch, P.budget_ns)) return;
         } else {
-            if (mode == BLEST_MODE_BOTTOM_UP)
-                bottom_up_level(P, &s_grab[2], &s_acc, bc, sn, s_found);
-            else
+            {
                 push_dispatch<false, SIGMA, LPV>(P, st, &s_grab[0], &s_acc, mode == BLEST_MODE_PUSH_LAZY_TC, ell, bc, bn, sn, qlen,
                                                  bsel, batch);
+            }
             housekeeping<SIGMA>(P, ell, bo, sql_old, sz, tid, nthreads);
             if (!grid_barrier(ctl, epoch, P.budget_ns)) return;
             if (logger && ell - 1 < P.log_cap)
@@ -1061,12 +1275,28 @@ blest_status bfs_prepare(blest_graph *h) {
     return BLEST_OK;
 }
 
+// Queue entries a level writes: half of the VSSs (at least 1024, at most
+// all of them).  A level whose queue is longer is dense enough that the next
+// top-down level scans every VSS instead of reading a queue (measured: on
+// the road-like grid, whose narrow VSSs make the queue cheap, a scan at an
+// eighth of the VSSs was 20 us a level slower than the queue; dense RMAT
+// levels, where a hub's slice set spans thousands of VSSs, queue about 70 %
+// of them and are followed by bottom-up levels that read no queue).
+static int bfs_queue_cap(int64_t Nv) {
+    int64_t c = Nv / 2;
+    if (c < 1024) c = 1024;
+    if (c > Nv) c = Nv;
+    return (int)c;
+}
+
 // Enqueue one BFS on h->stream; levels (original ids) land in dev_out.
 blest_status bfs_run(blest_graph *h, int32_t source, int32_t *dev_out) {
     BfsParams P;
     memset(&P, 0, sizeof P);
     P.n = (int)h->n;
     P.W = (int)((h->n + 31) / 32);
+    P.Nv = (int)h->Nv;
+    P.qcap = h->qcap > 0 ? (int)h->qcap : bfs_queue_cap(h->Nv);
     const void *kern = bfs_kernel_for(h->sigma, h->tau, h->block);
     if (!kern) return BLEST_ERR_INTERNAL;
     P.rowIds = h->g.rowIds;
@@ -1089,7 +1319,8 @@ blest_status bfs_run(blest_graph *h, int32_t source, int32_t *dev_out) {
     P.policy = h->policy;
     P.fixed_mode = h->fixed_mode;
     P.lazy = h->lazy;
-    P.tc = h->engine_tc;
+    P.tc = h->engine_tc != 0;
+    P.tc16 = h->engine_tc == 2;
     P.switching = h->switching;
     P.eta = h->eta;
     P.schedule = h->d_schedule;
@@ -1221,6 +1452,8 @@ extern "C" blest_status blest_bfs_noalloc(const blest_bvss_view *g, int32_t sour
     if (off > NOALLOC_BYTES) return BLEST_ERR_INTERNAL;
     P.n = (int)n;
     P.W = (int)W;
+    P.Nv = (int)g->num_vss;
+    P.qcap = (int)nv;   // the scratch queues hold every VSS: always written
     P.rowIds = g->row_ids;
     P.masks = g->masks;
     P.realPtrs = g->real_ptrs;

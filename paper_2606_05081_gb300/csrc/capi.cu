@@ -231,7 +231,7 @@ extern "C" blest_status blest_set_policy(blest_handle h, int32_t policy, int32_t
 }
 
 extern "C" blest_status blest_set_engine(blest_handle h, int32_t tc) {
-    if (!h || (tc != 0 && tc != 1)) return BLEST_ERR_INVALID;
+    if (!h || tc < 0 || tc > 2) return BLEST_ERR_INVALID;
     if (tc && !(h->sigma == 8 && h->tau == 128)) return BLEST_ERR_UNSUPPORTED;
     h->engine_tc = tc;
     return BLEST_OK;
@@ -247,6 +247,19 @@ extern "C" blest_status blest_set_launch(blest_handle h, int32_t block_threads, 
     h->block = block_threads;
     h->grid = g;
     h->vss_batch = vss_batch;
+    return BLEST_OK;
+}
+
+extern "C" blest_status blest_set_switching(blest_handle h, int32_t on) {
+    if (!h || h->many || (on != 0 && on != 1)) return BLEST_ERR_INVALID;
+    h->switching = on;
+    return BLEST_OK;
+}
+
+extern "C" blest_status blest_set_queue_cap(blest_handle h, int64_t cap) {
+    if (!h || h->many || cap < 0) return BLEST_ERR_INVALID;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return BLEST_ERR_CUDA;
+    h->qcap = cap > h->Nv ? h->Nv : cap;
     return BLEST_OK;
 }
 

@@ -26,6 +26,7 @@
 #include <vector>
 
 #include "msbfs.h"
+#include "tc.cuh"
 
 struct MsCtl {
     unsigned long long bar;
@@ -34,6 +35,16 @@ struct MsCtl {
     int timeout_where;
     int qlen[2];
     int dlen[2];
+};
+
+// Work counters of the multi-source launches of one call (host-visible
+// through blest_msbfs_stats): the terms of the kernel's byte model.
+struct MsStats {
+    unsigned long long launches;    // persistent-kernel launches (batches)
+    unsigned long long levels;      // levels run, summed over the launches
+    unsigned long long vss;         // VSSs processed in stage 1
+    unsigned long long hit_words;   // nonzero kappa-bit words OR-ed into V_next
+    unsigned long long dirty_sets;  // slice sets finalised in stage 2
 };
 
 struct MsbfsWork {
@@ -45,8 +56,10 @@ struct MsbfsWork {
     int *Q[2] = {nullptr, nullptr};
     MsCtl *ctl = nullptr;
     MsCtl *h_ctl = nullptr;
+    MsStats *stats = nullptr;      // device counters of the current call
     int *d_src = nullptr;
     int grid = 0;
+    int grid_tc = -1;              // grid of the tensor-core kernel (-1: not computed yet)
     long long *far = nullptr, *reach = nullptr;   // closeness accumulators (reordered ids)
     // closeness: one batch (source ids from a device cursor, the persistent
     // kernel, cursor advance) captured once in a CUDA graph and replayed
@@ -56,6 +69,7 @@ struct MsbfsWork {
     cudaGraph_t cc_graph = nullptr;
     cudaGraphExec_t cc_exec = nullptr;
     cudaStream_t cc_stream = nullptr;
+    int cc_engine = -1;            // stage-1 engine the captured batch graph launches
 };
 
 namespace {
@@ -80,7 +94,17 @@ struct MsParams {
     const int *k_dev;             // non-null: the batch size is read here (graph replays)
     int *levels;                  // k*n, source-major, original ids; may be null
     long long *far, *reach;       // may be null
+    MsStats *stats;               // work counters (added once per CTA and level)
+    int Nv;                       // VSSs of the BVSS
+    int remap;                    // 1: getVI element order of §6.1; 0: element u at index u (ablation)
+    int track;                    // 1: activeSets / dirtySets of Algorithm 5; 0: every VSS and every
+                                  //    slice set at every level (ablation)
     unsigned long long budget_ns;
+};
+
+// per-CTA work counts of the current level: VSSs, hit words, dirty sets
+struct MsAcc {
+    unsigned long long vss, hitw, dirty;
 };
 
 __device__ __forceinline__ bool ms_barrier(MsCtl *ctl, unsigned &epoch, unsigned long long budget) {
@@ -88,6 +112,10 @@ __device__ __forceinline__ bool ms_barrier(MsCtl *ctl, unsigned &epoch, unsigned
 }
 
 __device__ __forceinline__ int get_vi(int u, int rho) { return (u & 7) * rho + (u >> 3); }
+// the bit-array element of vertex u: getVI, or u itself without reindexing
+__device__ __forceinline__ int elem(const MsParams &P, int u) { return P.remap ? get_vi(u, P.rho) : u; }
+// the slice set of an element index
+__device__ __forceinline__ int elem_set(const MsParams &P, int e) { return P.remap ? e % P.rho : e >> 3; }
 
 // Appends to the VSS queue and the dirty-set list are staged per warp in
 // shared memory and reserved in the global arrays once per MS_STG entries
@@ -225,7 +253,8 @@ constexpr size_t MS_TAB_BYTES = (size_t)(MS_BLOCK / 32) * MS_TAB * 32 * sizeof(u
 
 template <int KW>
 __device__ void ms_stage1(const MsParams &P, MsStage &st, int *grab, int *s_tot, int qlen, const int *Qc, int dl,
-                          int *s_rows, unsigned char *s_m, unsigned *s_tab) {
+                          int *s_rows, unsigned char *s_m, unsigned *s_tab, MsAcc *acc) {
+    unsigned long long nvss = 0, nhit = 0;
     constexpr int G = 32 / KW;
     const int lane = lane_id();
     const int g = lane / KW, w = lane % KW;
@@ -239,9 +268,10 @@ __device__ void ms_stage1(const MsParams &P, MsStage &st, int *grab, int *s_tot,
         if (lane == 0) kc = atomicAdd(grab, 1);
         kc = __shfl_sync(FULL_MASK, kc, 0);
         const int it = (int)blockIdx.x + kc * (int)gridDim.x;
-        if (it >= qlen) break;
-        const int vss = Qc[it];
+        if (it >= (P.track ? qlen : P.Nv)) break;
+        const int vss = P.track ? Qc[it] : it;
         const int ss = __ldg(&P.v2r[vss]);
+        ++nvss;
         const bool own = lane < P.lpv;
         const int4 r = own ? __ldg(reinterpret_cast<const int4 *>(P.rowIds) + (size_t)vss * P.lpv + lane)
                            : make_int4(0, 0, 0, 0);
@@ -254,12 +284,12 @@ __device__ void ms_stage1(const MsParams &P, MsStage &st, int *grab, int *s_tot,
         // of the row, for the dirty claims, is that index mod rho) and its
         // 8-bit slice mask (byte i of the lane word, little-endian)
         reinterpret_cast<int4 *>(rows)[lane] =
-            make_int4(get_vi(r.x, P.rho), get_vi(r.y, P.rho), get_vi(r.z, P.rho), get_vi(r.w, P.rho));
+            make_int4(elem(P, r.x), elem(P, r.y), elem(P, r.z), elem(P, r.w));
         reinterpret_cast<unsigned *>(m8s)[lane] = m;
-        const unsigned aw = P.active[(size_t)ss * KW + w];
+        const unsigned aw = P.track ? P.active[(size_t)ss * KW + w] : ~0u;
         unsigned f[8];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) f[j] = aw ? P.F[(size_t)get_vi(ss * 8 + j, P.rho) * KW + w] : 0u;
+        for (int j = 0; j < 8; ++j) f[j] = aw ? P.F[(size_t)elem(P, ss * 8 + j) * KW + w] : 0u;
         // each lane writes and reads only its own column: no warp sync needed
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
@@ -284,7 +314,10 @@ __device__ void ms_stage1(const MsParams &P, MsStage &st, int *grab, int *s_tot,
                 const int kk = t * G + g;
                 const unsigned m8 = m8s[kk];
                 const unsigned hit = tab[(m8 & 15u) * 32] | tab[(16u + (m8 >> 4)) * 32];
-                if (hit) red_or(&P.Vn[(size_t)rows[kk] * KW + w], hit);
+                if (hit) {
+                    red_or(&P.Vn[(size_t)rows[kk] * KW + w], hit);
+                    ++nhit;
+                }
                 // one bit per group (any of its KW lanes hit): slots t*G .. t*G+G-1,
                 // G divides 32, so they sit in this chunk's word
                 hm |= group_bits<KW>(__ballot_sync(FULL_MASK, hit != 0)) << ((t * G) & 31);
@@ -297,22 +330,28 @@ __device__ void ms_stage1(const MsParams &P, MsStage &st, int *grab, int *s_tot,
 #pragma unroll
         for (int r4 = 0; r4 < 4; ++r4) {
             const unsigned hm = r4 == 0 ? hm0 : (r4 == 1 ? hm1 : (r4 == 2 ? hm2 : hm3));
-            if (!hm) continue;   // warp-uniform
+            if (!hm || !P.track) continue;   // warp-uniform
             bool claimed = false;
             int so = 0;
             if (hm >> lane & 1u) {
-                so = rows[32 * r4 + lane] % P.rho;
+                so = elem_set(P, rows[32 * r4 + lane]);
                 claimed = ld_volatile_i32(&P.dirty[so]) == 0 && atomicExch(&P.dirty[so], 1) == 0;
             }
             ms_mark_dirty(P, st, claimed, so, dl);
         }
+    }
+    nhit = warp_sum(nhit);
+    if (lane == 0) {
+        atomicAdd(&acc->vss, nvss);
+        atomicAdd(&acc->hitw, nhit);
     }
     ms_block_flush(P.dlist[dl], &P.ctl->dlen[dl], st.d, st.dn, s_tot);
 }
 
 template <int KW>
 __device__ void ms_stage2(const MsParams &P, MsStage &st, int *grab, int *s_tot, int ell, int dl, int qn, int dcount,
-                          int k) {
+                          int k, MsAcc *acc) {
+    unsigned long long nd = 0, nact = 0;
     constexpr int G = 32 / KW;
     const int lane = lane_id();
     const int g = lane / KW, w = lane % KW;
@@ -327,7 +366,7 @@ __device__ void ms_stage2(const MsParams &P, MsStage &st, int *grab, int *s_tot,
         if (chunk >= nchunk) break;
         const int i = chunk * G + g;
         const bool valid = i < dcount;
-        const int ss = valid ? dlist[i] : 0;
+        const int ss = valid ? (P.track ? dlist[i] : i) : 0;
         unsigned A = 0;
         // four vertices at a time: their V_next / V_curr words load together
 #pragma unroll 1
@@ -339,7 +378,7 @@ __device__ void ms_stage2(const MsParams &P, MsStage &st, int *grab, int *s_tot,
               nx4[q] = 0u;
               cu4[q] = 0u;
               if (valid && u < P.n) {
-                  const size_t e = (size_t)get_vi(u, P.rho) * KW + w;
+                  const size_t e = (size_t)elem(P, u) * KW + w;
                   nx4[q] = P.Vn[e];
                   cu4[q] = P.Vc[e];
               }
@@ -350,7 +389,7 @@ __device__ void ms_stage2(const MsParams &P, MsStage &st, int *grab, int *s_tot,
             const int u = ss * 8 + j;
             unsigned diff = 0;
             if (valid && u < P.n) {
-                const size_t e = (size_t)get_vi(u, P.rho) * KW + w;
+                const size_t e = (size_t)elem(P, u) * KW + w;
                 const unsigned next = nx4[q];
                 const unsigned cur = cu4[q];
                 diff = next ^ cur;
@@ -386,21 +425,198 @@ __device__ void ms_stage2(const MsParams &P, MsStage &st, int *grab, int *s_tot,
         }
         const unsigned bal = __ballot_sync(FULL_MASK, A != 0);
         const bool any = ((bal >> (g * KW)) & (KW == 32 ? 0xFFFFFFFFu : ((1u << KW) - 1u))) != 0;
-        if (valid && w == 0) P.dirty[ss] = 0;
-        ms_enqueue(P, st, valid && w == 0 && any, ss, P.Q[qn], qn);
+        if (valid && w == 0) {
+            if (P.track) P.dirty[ss] = 0;
+            ++nd;
+        }
+        if (P.track) ms_enqueue(P, st, valid && w == 0 && any, ss, P.Q[qn], qn);
+        else if (valid && w == 0 && any) ++nact;   // without tracking only the count ends the loop
     }
+    nact = warp_sum(nact);
+    if (lane_id() == 0 && nact) atomicAdd(&P.ctl->qlen[qn], (int)nact);
+    nd = warp_sum(nd);
+    if (lane_id() == 0 && nd) atomicAdd(&acc->dirty, nd);
     ms_block_flush(P.Q[qn], &P.ctl->qlen[qn], st.q, st.qn, s_tot);
 }
 
-// two 512-thread CTAs per SM (64 registers a thread)
+// ------------------------------------------------------------------
+// Stage 1 on the tensor cores (tcgen05), for the tau = 128 layout.
+// Eq. 2 for kappa lanes at once is a 0/1 product: hits[lane j][slot s] =
+// sum over the slice set's columns c of F[c](bit j) * mask[s](bit c), and a
+// lane reaches a slot's row iff its sum is nonzero.  Each warpgroup (4
+// warps) takes one VSS: B = its 128 slots x K (the 8 mask bits as bf16
+// 0/1, K padded to 16 with zeros), and for every 128-lane tile of the
+// frontier whose active words are nonzero, A = 128 lanes x K (bit j of the
+// 8 frontier elements as bf16 0/1); one kind::f16 MMA per 64 slots writes
+// D = A B^T (128 lanes x 64 slots, fp32, exact: sums <= 8) to tensor
+// memory.  Warp w of the group reads lanes 32w .. 32w + 31 of D; a ballot
+// over its 32 threads of D[.][s] != 0 is the hit word of those lanes for
+// slot s, OR-ed into V_next like the CUDA-core path's.  kind::i8 does not
+// exist on sm_103a; bf16 0/1 operands with fp32 sums are exact.
+constexpr int TC_WG = MS_BLOCK / 128;                 // warpgroups per CTA
+constexpr int TC_N = 64;                              // slots per MMA = D columns per warpgroup
+constexpr uint32_t TC_COLS = TC_WG * TC_N;            // tensor-memory columns per CTA (2 CTAs / SM: 512)
+constexpr size_t TC_TILE_BYTES = 128 * 16 * 2;        // 128 rows x 16 bf16
+constexpr size_t TC_SMEM = (size_t)TC_WG * 2 * TC_TILE_BYTES;
+// per warpgroup: halves [0, 4), tile activity [4, 12) (double-buffered by
+// tile parity: a warp past a tile with no MMA may write the next tile's
+// flag before a slower warp has read this one), wait ok [12]
+constexpr int TC_FLAGS = 13;
+
+// byte offset of row r (K-group 0) in a no-swizzle K-major tile: 8-row core
+// groups 256 bytes apart (SBO), the two K-groups of 8 bf16 128 bytes apart
+// (LBO), rows of a core group 16 bytes apart
+__device__ __forceinline__ uint32_t tc_row_off(int r) { return (uint32_t)((r >> 3) * 256 + (r & 7) * 16); }
+
+struct TcState {
+    uint32_t tmem;          // the CTA's tensor-memory base
+    unsigned char *tiles;   // A and B tiles of each warpgroup
+    uint64_t *mbar;         // MMA completion barrier of each warpgroup
+    int *flags;             // TC_FLAGS ints per warpgroup
+    int *claim;             // the claimed queue position of each warpgroup
+};
+
 template <int KW>
-__global__ void __launch_bounds__(MS_BLOCK, 2) k_msbfs(MsParams P) {
+__device__ void ms_stage1_tc(const MsParams &P, MsStage &st, int *grab, int *s_tot, int qlen, const int *Qc, int dl,
+                             int *s_rows, unsigned char *s_m, const TcState &tc, uint32_t &phase, MsAcc *acc) {
+    constexpr int NT = (KW + 3) / 4;   // 128-lane tiles of the kappa lanes
+    const int lane = lane_id();
+    const int wib = threadIdx.x >> 5;
+    const int g = wib >> 2, q = wib & 3;
+    const int t = threadIdx.x & 127;
+    const int bar = 1 + g;             // named barrier of the warpgroup (0 is __syncthreads)
+    int *rows = s_rows + g * 128;
+    unsigned char *hmk = s_m + g * 128;   // slot s had a hit in some tile
+    unsigned char *A = tc.tiles + (size_t)g * 2 * TC_TILE_BYTES;
+    unsigned char *B = A + TC_TILE_BYTES;
+    uint64_t *mbar = tc.mbar + g;
+    int *fl = tc.flags + g * TC_FLAGS;
+    const uint32_t dcol = tc.tmem + (uint32_t)(g * TC_N);
+    constexpr uint32_t IDESC = idesc_bf16_f32(128, TC_N);
+    const uint64_t adesc = smem_desc_kmajor(A, 128, 256);
+    unsigned long long nvss = 0, nhit = 0;
+    bool bad = false;
+    for (;;) {
+        if (t == 0) tc.claim[g] = atomicAdd(grab, 1);
+        named_barrier(bar, 128);
+        const int it = (int)blockIdx.x + tc.claim[g] * (int)gridDim.x;
+        if (it >= qlen) break;   // uniform in the warpgroup
+        const int vss = Qc[it];
+        const int ss = __ldg(&P.v2r[vss]);
+        if (t == 0) ++nvss;
+        // slot t: its row and mask byte (lane word t / 4 of the VSS, byte t % 4)
+        const int r = __ldg(&P.rowIds[(size_t)vss * 128 + t]);
+        const unsigned m8 = (__ldg(&P.masks[(size_t)vss * 32 + (t >> 2)]) >> (8 * (t & 3))) & 0xFFu;
+        rows[t] = elem(P, r);
+        hmk[t] = 0;
+        *reinterpret_cast<uint4 *>(B + tc_row_off(t)) = bits_to_bf16x8(m8);
+        const unsigned anym = __ballot_sync(FULL_MASK, m8 != 0u);
+        if (lane == 0) fl[q] = anym != 0u;
+        fence_proxy_async_smem();
+        named_barrier(bar, 128);
+        const bool half0 = (fl[0] | fl[1]) != 0, half1 = (fl[2] | fl[3]) != 0;   // slots 0-63 / 64-127
+        for (int m = 0; m < NT && !bad; ++m) {
+            const int w = m * 4 + q;   // this warp's 32-lane word of the tile
+            const unsigned aw = w < KW ? P.active[(size_t)ss * KW + w] : 0u;
+            unsigned bits = 0;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const unsigned f = aw ? P.F[(size_t)elem(P, ss * 8 + c) * KW + w] : 0u;
+                bits |= ((f >> lane) & 1u) << c;
+            }
+            *reinterpret_cast<uint4 *>(A + tc_row_off(t)) = bits_to_bf16x8(bits);
+            int *tf = fl + 4 + 4 * (m & 1);
+            if (lane == 0) tf[q] = aw != 0u;
+            fence_proxy_async_smem();
+            tc_fence_before();
+            named_barrier(bar, 128);
+            const bool tile_on = (tf[0] | tf[1] | tf[2] | tf[3]) != 0;
+            if (!tile_on) continue;   // uniform: no frontier lane of the tile
+#pragma unroll 1
+            for (int h = 0; h < 2; ++h) {
+                if (!(h ? half1 : half0)) continue;   // uniform: padding slots only
+                if (t == 0) {
+                    tc_fence_after();
+                    mma_bf16_commit(dcol, adesc, smem_desc_kmajor(B + h * 2048, 128, 256), IDESC, mbar);
+                    // bounded wait: a wait past the budget records a timeout, then waits
+                    // once more (bounded) so no MMA is left writing the tensor memory
+                    const uint64_t t0 = global_ns();
+                    int ok = 1;
+                    unsigned spins = 0;
+                    while (!mbar_try_wait(mbar, phase)) {
+                        if ((++spins & 255u) == 0 && global_ns() - t0 > P.budget_ns) {
+                            ok = 0;
+                            const uint64_t t1 = global_ns();
+                            while (!mbar_try_wait(mbar, phase) && global_ns() - t1 < P.budget_ns) {
+                            }
+                            break;
+                        }
+                    }
+                    fl[12] = ok;
+                }
+                named_barrier(bar, 128);
+                phase ^= 1u;
+                if (!fl[12]) {
+                    if (t == 0) atomicCAS(&P.ctl->err, 0, (int)BLEST_ERR_TIMEOUT);
+                    bad = true;
+                    break;
+                }
+                tc_fence_after();
+                if (w < KW) {   // warp-uniform: the warp's lanes exist
+#pragma unroll 1
+                    for (int cc = 0; cc < 2; ++cc) {
+                        uint32_t d[32];
+                        tmem_ld32(dcol + ((uint32_t)(32 * q) << 16) + (uint32_t)(cc * 32), d);
+                        unsigned hw = 0;
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) {
+                            const unsigned b = __ballot_sync(FULL_MASK, d[i] != 0u);
+                            if (lane == i) hw = b;
+                        }
+                        const int sl = h * 64 + cc * 32 + lane;
+                        if (hw) {
+                            red_or(&P.Vn[(size_t)rows[sl] * KW + w], hw);
+                            ++nhit;
+                            hmk[sl] = 1;
+                        }
+                    }
+                }
+                tc_fence_before();
+                named_barrier(bar, 128);   // D read by every warp before the next MMA
+            }
+        }
+        if (bad) break;
+        named_barrier(bar, 128);   // the hit marks of every tile
+        bool claimed = false;
+        int so = 0;
+        if (hmk[t]) {
+            so = elem_set(P, rows[t]);
+            claimed = ld_volatile_i32(&P.dirty[so]) == 0 && atomicExch(&P.dirty[so], 1) == 0;
+        }
+        ms_mark_dirty(P, st, claimed, so, dl);
+        named_barrier(bar, 128);   // rows, marks and B are rewritten by the next VSS
+    }
+    nhit = warp_sum(nhit);
+    if (lane == 0) {
+        atomicAdd(&acc->vss, nvss);
+        atomicAdd(&acc->hitw, nhit);
+    }
+    ms_block_flush(P.dlist[dl], &P.ctl->dlen[dl], st.d, st.dn, s_tot);
+}
+
+// The whole multi-source BFS of one launch (every block calls it; a block
+// returns early only at a grid barrier that failed, all its threads
+// together).  tc: the tensor-core stage 1 (its tensor memory is allocated
+// by the caller); else the CUDA-core stage 1 with the subset-OR tables in
+// s_tab.
+template <int KW, bool TC>
+__device__ __forceinline__ void ms_run(MsParams P, unsigned *s_tab, const TcState *tc) {
     __shared__ __align__(16) int s_rows[(MS_BLOCK / 32) * 128];
     __shared__ __align__(16) unsigned char s_m[(MS_BLOCK / 32) * 128];
     __shared__ int s_stg[(MS_BLOCK / 32) * 2 * MS_STG];
-    extern __shared__ unsigned s_tab[];   // MS_TAB_BYTES: the warps' subset-OR tables
     __shared__ int s_grab[2];
     __shared__ int s_tot[2][2];   // per stage: the CTA's staged total and its reserved base
+    __shared__ MsAcc s_acc;       // this CTA's work counts of the current level
     MsStage st;
     st.q = s_stg + (threadIdx.x >> 5) * 2 * MS_STG;
     st.d = st.q + MS_STG;
@@ -429,7 +645,7 @@ __global__ void __launch_bounds__(MS_BLOCK, 2) k_msbfs(MsParams P) {
         const int c = (int)tid;
         const int so = __ldg(&P.srcs[c]);
         const int u = P.new_of_old ? __ldg(&P.new_of_old[so]) : so;
-        const size_t e = (size_t)get_vi(u, P.rho) * KW + (c >> 5);
+        const size_t e = (size_t)elem(P, u) * KW + (c >> 5);
         const unsigned bit = 1u << (c & 31);
         atomicOr(&P.Vc[e], bit);
         atomicOr(&P.Vn[e], bit);
@@ -461,11 +677,22 @@ __global__ void __launch_bounds__(MS_BLOCK, 2) k_msbfs(MsParams P) {
     if (!ms_barrier(ctl, epoch, P.budget_ns)) return;
 
     int ell = 1;
+    uint32_t tc_phase = 0;   // parity of the warpgroup's next MMA completion (tensor-core stage 1)
     __shared__ int s_cnt;
     for (;; ++ell) {
         const int qc = (ell - 1) & 1, qn = ell & 1, dl = ell & 1;
         // one thread per block reads the shared counter (see k_bfs)
         if (threadIdx.x == 0) {
+            // the previous level's counts of this CTA (all warps passed two
+            // block barriers since they added them)
+            if (P.stats && ell > 1 && (s_acc.vss | s_acc.hitw | s_acc.dirty) != 0) {
+                red_add_u64(&P.stats->vss, s_acc.vss);
+                red_add_u64(&P.stats->hit_words, s_acc.hitw);
+                red_add_u64(&P.stats->dirty_sets, s_acc.dirty);
+            }
+            s_acc.vss = 0;
+            s_acc.hitw = 0;
+            s_acc.dirty = 0;
             s_cnt = ld_volatile_i32(&ctl->qlen[qc]);
             s_grab[0] = 0;
             s_grab[1] = 0;
@@ -477,17 +704,68 @@ __global__ void __launch_bounds__(MS_BLOCK, 2) k_msbfs(MsParams P) {
         __syncthreads();
         if (qlen == 0) break;
         if (tid == 0) ctl->qlen[qn] = 0;
-        ms_stage1<KW>(P, st, &s_grab[0], s_tot[0], qlen, P.Q[qc], dl, s_rows, s_m, s_tab);
+        if constexpr (TC)
+            ms_stage1_tc<KW>(P, st, &s_grab[0], s_tot[0], qlen, P.Q[qc], dl, s_rows, s_m, *tc, tc_phase, &s_acc);
+        else
+            ms_stage1<KW>(P, st, &s_grab[0], s_tot[0], qlen, P.Q[qc], dl, s_rows, s_m, s_tab, &s_acc);
         if (!ms_barrier(ctl, epoch, P.budget_ns)) return;
-        if (threadIdx.x == 0) s_cnt = ld_volatile_i32(&ctl->dlen[dl]);
+        if (threadIdx.x == 0) s_cnt = P.track ? ld_volatile_i32(&ctl->dlen[dl]) : P.rho;
         __syncthreads();
         const int dcount = s_cnt;
         __syncthreads();
         if (tid == 0) ctl->dlen[dl ^ 1] = 0;
-        ms_stage2<KW>(P, st, &s_grab[1], s_tot[1], ell, dl, qn, dcount, k);
+        ms_stage2<KW>(P, st, &s_grab[1], s_tot[1], ell, dl, qn, dcount, k, &s_acc);
         if (!ms_barrier(ctl, epoch, P.budget_ns)) return;
     }
-    if (tid == 0) ctl->nlevels = ell - 1;
+    if (tid == 0) {
+        ctl->nlevels = ell - 1;
+        if (P.stats) {
+            red_add_u64(&P.stats->launches, 1ull);
+            red_add_u64(&P.stats->levels, (unsigned long long)(ell - 1));
+        }
+    }
+}
+
+// two 512-thread CTAs per SM (64 registers a thread)
+template <int KW>
+__global__ void __launch_bounds__(MS_BLOCK, 2) k_msbfs(MsParams P) {
+    extern __shared__ unsigned s_tab[];   // MS_TAB_BYTES: the warps' subset-OR tables
+    ms_run<KW, false>(P, s_tab, nullptr);
+}
+
+// The tensor-core variant: TC_COLS tensor-memory columns per CTA (two CTAs
+// per SM fill the 512 columns), allocated before and freed after the run,
+// whichever barrier it ended at.
+template <int KW>
+__global__ void __launch_bounds__(MS_BLOCK, 2) k_msbfs_tc(MsParams P) {
+    extern __shared__ __align__(1024) unsigned char s_tiles[];   // TC_SMEM: A / B tiles
+    __shared__ uint32_t s_tmem;
+    __shared__ __align__(8) uint64_t s_mbar[TC_WG];
+    __shared__ int s_flags[TC_WG * TC_FLAGS];
+    __shared__ int s_claim[TC_WG];
+    if (threadIdx.x < 32) tmem_alloc(&s_tmem, TC_COLS);
+    if (threadIdx.x == 0) {
+        for (int g = 0; g < TC_WG; ++g) mbar_init(&s_mbar[g], 1);
+        mbar_init_fence();
+    }
+    // the K-padding half of every tile row stays zero
+    for (size_t i = threadIdx.x; i < TC_SMEM / 16; i += blockDim.x)
+        reinterpret_cast<uint4 *>(s_tiles)[i] = make_uint4(0u, 0u, 0u, 0u);
+    fence_proxy_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    TcState tc;
+    tc.tmem = s_tmem;
+    tc.tiles = s_tiles;
+    tc.mbar = s_mbar;
+    tc.flags = s_flags;
+    tc.claim = s_claim;
+    ms_run<KW, true>(P, nullptr, &tc);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (threadIdx.x < 32) tmem_dealloc(s_tmem, TC_COLS);
 }
 
 __global__ void k_cc(const long long *__restrict__ far, const long long *__restrict__ reach,
@@ -503,15 +781,26 @@ __global__ void k_cc(const long long *__restrict__ far, const long long *__restr
     }
 }
 
-template <int KW>
-int ms_grid() {
+// the kernel of a (lane words, engine) pair and its dynamic shared memory
+static const void *ms_kernel(int KW, bool tc) {
+    if (tc) return KW == 2 ? (const void *)k_msbfs_tc<2> : (KW == 8 ? (const void *)k_msbfs_tc<8> : (const void *)k_msbfs_tc<32>);
+    return KW == 2 ? (const void *)k_msbfs<2> : (KW == 8 ? (const void *)k_msbfs<8> : (const void *)k_msbfs<32>);
+}
+static size_t ms_smem(bool tc) { return tc ? TC_SMEM : MS_TAB_BYTES; }
+
+// Co-resident grid of a kernel; 0 if it cannot be launched.  The
+// tensor-core kernel needs at most two CTAs per SM (each holds TC_COLS of
+// the SM's 512 tensor-memory columns; a third would wait for columns
+// forever), so a larger occupancy refuses it.
+static int ms_grid(int KW, bool tc) {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaFuncSetAttribute(k_msbfs<KW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MS_TAB_BYTES) !=
-        cudaSuccess)
+    const void *fn = ms_kernel(KW, tc);
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ms_smem(tc)) != cudaSuccess)
         return 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_msbfs<KW>, MS_BLOCK, MS_TAB_BYTES);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, MS_BLOCK, ms_smem(tc));
+    if (tc && per * (int)TC_COLS > 512) return 0;
     return per * sms;
 }
 
@@ -573,8 +862,10 @@ static blest_status ms_prepare(blest_graph *h, int kappa) {
     }
     if ((st = dev_alloc_t(h, &m->ctl, 1)) != BLEST_OK) { delete m; return st; }
     if ((st = dev_alloc_t(h, &m->d_src, 1024)) != BLEST_OK) { delete m; return st; }
+    if ((st = dev_alloc_t(h, &m->stats, 1)) != BLEST_OK) { delete m; return st; }
+    if (cudaMemsetAsync(m->stats, 0, sizeof(MsStats), h->stream) != cudaSuccess) { delete m; return BLEST_ERR_CUDA; }
     if (cudaMallocHost((void **)&m->h_ctl, sizeof(MsCtl)) != cudaSuccess) { delete m; return BLEST_ERR_OOM; }
-    m->grid = kappa == 64 ? ms_grid<2>() : (kappa == 256 ? ms_grid<8>() : ms_grid<32>());
+    m->grid = ms_grid(m->KW, false);
     if (m->grid <= 0) { delete m; return BLEST_ERR_CUDA; }
     h->ms = m;
     return BLEST_OK;
@@ -612,11 +903,19 @@ static blest_status ms_launch(blest_graph *h, int k, int *levels_dev, long long 
     P.levels = levels_dev;
     P.far = far;
     P.reach = reach;
+    P.stats = m->stats;
+    P.Nv = (int)h->Nv;
+    P.remap = h->ms_remap;
+    P.track = h->ms_track;
     P.budget_ns = (unsigned long long)h->timeout_ms * 1000000ull;
     if (cudaMemsetAsync(m->ctl, 0, sizeof(MsCtl), h->stream) != cudaSuccess) return BLEST_ERR_CUDA;
     void *args[] = {&P};
-    const void *fn = m->KW == 2 ? (const void *)k_msbfs<2> : (m->KW == 8 ? (const void *)k_msbfs<8> : (const void *)k_msbfs<32>);
-    cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(m->grid), dim3(MS_BLOCK), args, MS_TAB_BYTES, h->stream);
+    const bool tc = h->ms_engine == 1;
+    if (tc && m->grid_tc < 0) m->grid_tc = ms_grid(m->KW, true);
+    const int grid = tc ? m->grid_tc : m->grid;
+    if (grid <= 0) return BLEST_ERR_UNSUPPORTED;
+    cudaError_t e = cudaLaunchCooperativeKernel(ms_kernel(m->KW, tc), dim3(grid), dim3(MS_BLOCK), args, ms_smem(tc),
+                                                h->stream);
     if (e != cudaSuccess) {
         blest_internal_record_cuda_error(e, "cudaLaunchCooperativeKernel(k_msbfs)", __FILE__, __LINE__);
         return BLEST_ERR_CUDA;
@@ -654,6 +953,7 @@ extern "C" blest_status blest_msbfs(blest_handle h, const int32_t *sources, int3
     }
     if (cudaMemcpyAsync(h->ms->d_src, src.data(), (size_t)k * 4, cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
         return BLEST_ERR_CUDA;
+    if (cudaMemsetAsync(h->ms->stats, 0, sizeof(MsStats), h->stream) != cudaSuccess) return BLEST_ERR_CUDA;
     st = ms_launch(h, k, target, nullptr, nullptr);
     if (st == BLEST_OK && !dev) {
         if (cudaMemcpyAsync(levels, target, (size_t)k * (size_t)h->n * 4, cudaMemcpyDeviceToHost, h->stream) !=
@@ -682,7 +982,7 @@ static blest_status closeness_batches(blest_graph *h, int64_t first, int64_t cou
         if ((st = dev_alloc_t(h, &m->sticky, 1)) != BLEST_OK) return st;
     }
     cudaStream_t cs = h->stream;
-    if (!m->cc_exec || m->cc_stream != cs) {
+    if (!m->cc_exec || m->cc_stream != cs || m->cc_engine != h->ms_engine) {
         ms_release_graph(m);
         if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return BLEST_ERR_CUDA;
         k_ms_batch_src<<<1, 1024, 0, cs>>>(m->d_src, m->k_dev, m->cursor);
@@ -701,6 +1001,7 @@ static blest_status closeness_batches(blest_graph *h, int64_t first, int64_t cou
             return BLEST_ERR_CUDA;
         }
         m->cc_stream = cs;
+        m->cc_engine = h->ms_engine;
     }
     const long long range[2] = {(long long)first, (long long)(first + count)};
     if (cudaMemcpyAsync(m->cursor, range, sizeof range, cudaMemcpyHostToDevice, cs) != cudaSuccess)
@@ -729,6 +1030,7 @@ static blest_status closeness_common(blest_graph *h, int64_t first, int64_t coun
     }
     if (cudaMemsetAsync(m->far, 0, (size_t)h->n * 8, h->stream) != cudaSuccess) return BLEST_ERR_CUDA;
     if (cudaMemsetAsync(m->reach, 0, (size_t)h->n * 8, h->stream) != cudaSuccess) return BLEST_ERR_CUDA;
+    if (cudaMemsetAsync(m->stats, 0, sizeof(MsStats), h->stream) != cudaSuccess) return BLEST_ERR_CUDA;
     st = closeness_batches(h, first, count);
     if (st != BLEST_OK) return st;
     // outputs (original ids); host outputs are staged on the device
@@ -764,4 +1066,40 @@ extern "C" blest_status blest_closeness_range(blest_handle h, int64_t first, int
                                               int64_t *reach) {
     if (!h || !far) return BLEST_ERR_INVALID;
     return closeness_common(h, first, count, far, nullptr, reach);
+}
+
+extern "C" blest_status blest_msbfs_stats(blest_handle h, blest_msbfs_counters *out) {
+    if (!h || !out) return BLEST_ERR_INVALID;
+    memset(out, 0, sizeof *out);
+    if (!h->ms) return BLEST_OK;
+    MsStats st;
+    if (cudaMemcpyAsync(&st, h->ms->stats, sizeof st, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+        cudaStreamSynchronize(h->stream) != cudaSuccess)
+        return BLEST_ERR_CUDA;
+    out->kappa = h->ms->kappa;
+    out->launches = (int64_t)st.launches;
+    out->levels = (int64_t)st.levels;
+    out->vss = (int64_t)st.vss;
+    out->hit_words = (int64_t)st.hit_words;
+    out->dirty_sets = (int64_t)st.dirty_sets;
+    return BLEST_OK;
+}
+
+extern "C" blest_status blest_set_msbfs_engine(blest_handle h, int32_t tc) {
+    if (!h || h->many || (tc != 0 && tc != 1)) return BLEST_ERR_INVALID;
+    if (tc && (h->sigma != 8 || h->tau != 128)) return BLEST_ERR_UNSUPPORTED;
+    if (tc && !(h->ms_remap && h->ms_track)) return BLEST_ERR_UNSUPPORTED;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return BLEST_ERR_CUDA;
+    h->ms_engine = tc;
+    return BLEST_OK;
+}
+
+extern "C" blest_status blest_set_msbfs_variant(blest_handle h, int32_t reindex, int32_t tracking) {
+    if (!h || h->many || (reindex != 0 && reindex != 1) || (tracking != 0 && tracking != 1)) return BLEST_ERR_INVALID;
+    if (h->ms_engine == 1 && !(reindex && tracking)) return BLEST_ERR_UNSUPPORTED;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return BLEST_ERR_CUDA;
+    h->ms_remap = reindex;
+    h->ms_track = tracking;
+    if (h->ms) ms_release_graph(h->ms);   // the captured closeness batch bakes the variant in
+    return BLEST_OK;
 }

@@ -87,7 +87,9 @@ def test_ctypes_structs_match_the_header_layout(tmp_path):
 
     import paper_2606_05081_gb300 as blest
     pairs = {"blest_build_opts": blest.BuildOpts, "blest_info": blest.Info,
-             "blest_level_log": blest.LevelLog, "blest_bvss_view": blest.BvssView}
+             "blest_level_log": blest.LevelLog, "blest_bvss_view": blest.BvssView,
+             "blest_degree_report": blest.DegreeReport, "blest_scale_free_report": blest.ScaleFreeReport,
+             "blest_msbfs_counters": blest.MsbfsStats}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "blest.h"', 'int main(void) {']
     for cname, cls in pairs.items():
         lines.append(f'printf("{cname} sizeof %zu\\n", sizeof({cname}));')

@@ -172,3 +172,71 @@ def test_reduction_runs_on_the_host_for_gloo_and_on_the_gpu_for_nccl():
     assert reduce_device(FakeDist("gloo")).type == "cpu"
     if torch.cuda.is_available():
         assert reduce_device(FakeDist("nccl")).type == "cuda"
+
+
+class _WallTimer:
+    def start(self):
+        import time
+        self.t = time.perf_counter()
+
+    def stop(self):
+        import time
+        return (time.perf_counter() - self.t) * 1e3
+
+
+class _OracleHandle:
+    """Stands in for a library handle: closeness_range from the oracle, and
+    a record of the ranges it was asked for."""
+
+    def __init__(self, g):
+        self.partial = _partial_oracle(g)
+        self.calls = []
+
+    def closeness_range(self, first, count, far, reach):
+        self.calls.append((first, count))
+        f, r = self.partial(first, count)
+        far[:] = f
+        reach[:] = r
+
+
+def _bench_split_worker(rank, world, port, q):
+    import sys
+    import torch.distributed as dist
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    g = gg.rmat(11, seed=12)
+    h = _OracleHandle(g)
+    far = np.zeros(g.n, np.int64)
+    reach = np.zeros(g.n, np.int64)
+    ms, f, r, cc, rng = bench.closeness_split_run(h, g.n, rank, world, dist, far, reach, _WallTimer())
+    dist.destroy_process_group()
+    q.put((rank, h.calls, rng, f, r, cc, ms))
+
+
+def test_bench_closeness_splits_sources_over_the_ranks():
+    """The bench's closeness path runs only this rank's source range and
+    all-reduces: two gloo ranks, each asked for its own half, end with the
+    oracle's whole result."""
+    pytest.importorskip("paper_2606_05081_gb300")
+    from paper_2606_05081_gb300.distributed import source_ranges
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    ps = [ctx.Process(target=_bench_split_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in ps:
+        p.start()
+    res = sorted([q.get(timeout=300) for _ in ps], key=lambda x: x[0])
+    for p in ps:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    g = gg.rmat(11, seed=12)
+    far_r, reach_r, cc_r = oracle.closeness(g)
+    ranges = source_ranges(g.n, 2)
+    for rank, calls, rng, f, r, cc, ms in res:
+        assert calls == [ranges[rank]] and tuple(rng) == ranges[rank]
+        assert np.array_equal(f, far_r) and np.array_equal(r, reach_r) and np.array_equal(cc, cc_r)
+    assert res[0][6] == res[1][6]          # the max over ranks

@@ -68,6 +68,23 @@ def test_bvss_matches_oracle(case):
     assert abs(info["update_divergence"] - u) <= 1e-12 * max(1.0, abs(u))
 
 
+@pytest.mark.parametrize("cap", [1, 64])
+@pytest.mark.parametrize("mode", [0, 1, 2, 3, 4])
+def test_fixed_mode_levels_with_scanned_dense_levels(case, blest, mode, cap):
+    """A queue cap below the level sizes: levels past it are counted without
+    being written and the next top-down level scans every VSS's frontier
+    field instead.  Levels must not change."""
+    name, g, h = case
+    h.set_policy(blest.POLICY_FIXED, mode)
+    h.set_queue_cap(cap)
+    try:
+        for s in gg.sources(g, 4, 23):
+            assert np.array_equal(h.bfs(int(s)), oracle.bfs(g, int(s))), (name, mode, cap, s)
+    finally:
+        h.set_queue_cap(0)
+        h.set_policy(blest.POLICY_HEURISTIC)
+
+
 @pytest.mark.parametrize("mode", [0, 1, 2, 3, 4])
 def test_fixed_mode_levels(case, blest, mode):
     name, g, h = case
@@ -242,3 +259,48 @@ def test_reordered_layouts_bit_exact(blest, sigma, tau):
                 for mode in (0, 2, 4):
                     h.set_policy(blest.POLICY_FIXED, mode)
                     assert np.array_equal(h.bfs(int(s)), oracle.bfs(g, int(s))), (reorder, mode, s)
+
+
+@pytest.mark.parametrize("tau", [128, 32])
+def test_hub_slice_sets_long_ranges_and_queue_counts(blest, tau):
+    """Hubs whose slice sets span hundreds of VSSs (the ranges the whole CTA
+    writes at a level's flush) and a queue cap in between: levels exact,
+    and the logged queue length of every level equals the VSS count of the
+    slice sets holding the previous level's vertices (counted in full even
+    where the cap stops the writes)."""
+    stars = gg.disjoint_union(gg.star(20000), gg.star(9000), gg.rmat(13, seed=3))
+    ref_b = oracle.bvss(stars, 8, tau)
+    nv_of_set = np.diff(ref_b["realPtrs"])
+    assert nv_of_set.max() >= 64 * (128 // tau)
+    with blest.build_graph(stars, tau=tau) as h:
+        for cap, mode in [(0, 0), (0, 2), (200, 0), (200, 2), (1, 1 if tau == 128 else 0)]:
+            h.set_queue_cap(cap)
+            h.set_policy(blest.POLICY_FIXED, mode)
+            for s in [0, 20000, 29000, 29001 + 17]:
+                lv = h.bfs(int(s))
+                want = oracle.bfs(stars, int(s))
+                assert np.array_equal(lv, want), (tau, cap, mode, s)
+                for rec in h.level_log():
+                    prev = np.flatnonzero(want == rec["level"] - 1)
+                    assert rec["queue"] == int(nv_of_set[np.unique(prev // 8)].sum()), (tau, cap, mode, s, rec)
+        h.set_queue_cap(0)
+        h.set_policy(blest.POLICY_HEURISTIC)
+
+
+@pytest.mark.parametrize("name", sorted(GRAPHS))
+def test_sixteen_mma_layout_levels(blest, name):
+    """Tensor-core levels with one slice per fragment row (16 MMAs per VSS,
+    the layout the ablation measures Fig. 3's against): levels exact in the
+    eager and lazy tensor-core modes and under the paper's rule."""
+    g = GRAPHS[name]()
+    with blest.build_graph(g) as h:
+        h.set_engine(2)
+        assert h.info()["engine_tc"] == 2
+        srcs = gg.sources(g, 4, 29)
+        for pol, mode in [(blest.POLICY_FIXED, 1), (blest.POLICY_FIXED, 3), (blest.POLICY_HEURISTIC, 0)]:
+            h.set_policy(pol, mode)
+            for s in srcs:
+                assert np.array_equal(h.bfs(int(s)), oracle.bfs(g, int(s))), (name, pol, mode, s)
+    with blest.build_graph(g, tau=32) as h:
+        with pytest.raises(blest.BlestError):
+            h.set_engine(2)

@@ -104,12 +104,11 @@ def test_in_kernel_decisions_and_exact_levels(blest):
         h.set_policy(blest.POLICY_HEURISTIC)
 
 
-def test_trained_network_beats_the_rule_on_held_out_graphs(blest):
-    """Train on per-level timings of small RMAT / grid / BA graphs, evaluate
-    on other seeds and on a held-out family (random geometric graph): the
-    learned policy's total time over the held-out levels is no worse than
-    the paper's rule (and usually lower).  Both are evaluated on the same
-    measured per-level time matrices."""
+def test_training_reduces_loss_and_beats_the_rule_on_new_seeds(blest):
+    """Train on per-level timings of small RMAT / grid / BA graphs with the
+    project's own kernels; the loss falls, and on other seeds of the trained
+    families the learned policy's total time is no worse than the paper's
+    rule (both evaluated on the same measured per-level time matrices)."""
     from paper_2606_05081_gb300 import switch
     train_g = [gg.rmat(15, seed=31), gg.rmat(17, seed=32), gg.grid(256, 256, seed=33), gg.ba(1 << 16, 4, seed=34)]
     hs = [blest.build_graph(x) for x in train_g]
@@ -118,13 +117,34 @@ def test_trained_network_beats_the_rule_on_held_out_graphs(blest):
         h.close()
     w, hist = switch.train(X, Y, M)
     assert hist[-1] < hist[0]
-    held = [gg.rmat(16, seed=41), gg.rgg(1 << 16, 10, seed=42), gg.ba(1 << 17, 8, seed=43)]
+    held = [gg.rmat(16, seed=41), gg.ba(1 << 17, 8, seed=43)]
+    res = []
+    for x in held:
+        with blest.build_graph(x) as h:
+            res.append(switch.evaluate(h, gg.sources(x, 6, 4), w, reps=2))
+    print("new-seed regret", res)
+    # the plain method: the paper's rule with its tensor-core hit test
+    tot_h = sum(r["ms_heuristic_tc"] for r in res)
+    tot_l = sum(r["ms_learned"] for r in res)
+    assert tot_l <= 1.02 * tot_h
+
+
+def test_shipped_network_beats_the_rule_on_held_out_families(blest):
+    """The shipped weights (trained on RMAT, road-like grid and Barabasi-
+    Albert graphs by ``switch train``) against the paper's rule on graphs
+    they were not trained on, one of them a family never seen (random
+    geometric): per graph the learned policy is within 5 % of the rule or
+    faster, and faster in total."""
+    from paper_2606_05081_gb300 import switch
+    w = switch.load_weights()
+    assert w is not None
+    held = [gg.rmat(16, seed=41), gg.rgg(1 << 16, 10, seed=42), gg.ba(1 << 17, 8, seed=43),
+            gg.grid(512, 512, seed=44)]
     res = []
     for x in held:
         with blest.build_graph(x) as h:
             res.append(switch.evaluate(h, gg.sources(x, 6, 4), w, reps=2))
     print("held-out regret", res)
-    # the plain method: the paper's rule with its tensor-core hit test
-    tot_h = sum(r["ms_heuristic_tc"] for r in res)
-    tot_l = sum(r["ms_learned"] for r in res)
-    assert tot_l <= 1.02 * tot_h
+    for r in res:
+        assert r["ms_learned"] <= 1.05 * r["ms_heuristic_tc"], r
+    assert sum(r["ms_learned"] for r in res) < sum(r["ms_heuristic_tc"] for r in res)

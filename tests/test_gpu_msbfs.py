@@ -167,3 +167,134 @@ def test_bfs_many_ragged_sizes_and_isolated(blest):
         got = h.bfs_many(srcs, total_n=int(vo[-1]))
     for i, g in enumerate(gs):
         assert np.array_equal(got[vo[i]:vo[i + 1]], oracle.bfs(g, int(srcs[i])))
+
+
+def _expected_counters(g, k_lanes, kappa, levels, bvss):
+    """The multi-source work counters implied by the oracle's levels: per
+    level l, the sets holding a vertex some lane reached at l - 1 are queued
+    (their VSSs processed), the sets holding a target of an arc from such a
+    vertex are dirty, and each (slice set, row) slot ORs one word per
+    32-lane group that has a frontier lane among the slot's columns."""
+    n = g.n
+    kw = kappa // 32
+    nv_of_set = np.diff(bvss["realPtrs"])
+    src = np.repeat(np.arange(n), np.diff(g.row_ptr))
+    dst = g.col.astype(np.int64)
+    keep = src != dst
+    src, dst = src[keep], dst[keep]
+    slot = (src // 8) * n + dst                    # one BVSS slot per (slice set, row)
+    order = np.argsort(slot, kind="stable")
+    src, dst, slot = src[order], dst[order], slot[order]
+    starts = np.flatnonzero(np.r_[True, slot[1:] != slot[:-1]])
+    lanes_pad = np.zeros((kappa, n), bool)
+    vss = hitw = dirty = nlev = 0
+    ell = 1
+    while True:
+        act = levels == ell - 1                    # k x n frontier of level ell
+        av = act.any(axis=0)
+        sets = np.unique(np.flatnonzero(av) // 8)
+        q = int(nv_of_set[sets].sum()) if len(sets) else 0
+        if q == 0:
+            break
+        nlev += 1
+        vss += q
+        m = av[src]
+        dirty += len(np.unique(dst[m] // 8))
+        lanes_pad[:] = False
+        lanes_pad[:k_lanes] = act
+        words = np.packbits(lanes_pad.reshape(kw, 32, n), axis=1, bitorder="little")   # kw x 4 x n bytes
+        wv = np.ascontiguousarray(words.transpose(2, 0, 1)).reshape(n, kw * 4).view(np.uint32)   # n x kw
+        per_arc = wv[src]                                                              # arcs x kw
+        per_slot = np.bitwise_or.reduceat(per_arc, starts, axis=0)
+        hitw += int((per_slot != 0).sum())
+        ell += 1
+    return {"levels": nlev, "vss": vss, "dirty_sets": dirty, "hit_words": hitw}
+
+
+@pytest.mark.parametrize("name,k,tau", [("rmat12", 64, 128), ("grid_ragged", 200, 128), ("er_directed", 37, 32),
+                                        ("union", 700, 32)])
+def test_msbfs_work_counters_match_the_oracle_levels(blest, name, k, tau):
+    g = MAKERS[name]()
+    srcs = gg.sources(g, k, 11)
+    ref = oracle.bfs_many(g, srcs)
+    kappa = 64 if k <= 64 else (256 if k <= 256 else 1024)
+    want = _expected_counters(g, len(srcs), kappa, ref, oracle.bvss(g, 8, tau))
+    with blest.build_graph(g, tau=tau) as h:
+        assert np.array_equal(h.msbfs(srcs), ref)
+        st = h.msbfs_stats()
+    assert st["kappa"] == kappa and st["launches"] == 1
+    for f in ("levels", "vss", "dirty_sets", "hit_words"):
+        assert st[f] == want[f], (f, st[f], want[f])
+
+
+@pytest.mark.parametrize("name", sorted(MAKERS))
+@pytest.mark.parametrize("k", [1, 37, 64, 200, 256, 700, 1024])
+def test_msbfs_levels_tensor_core_engine(blest, name, k):
+    """Stage 1 on the tcgen05 tensor cores (0/1 bf16 MMA per 128-lane tile
+    and 64 slots): levels bit-exact against the oracle for every batch width."""
+    g = MAKERS[name]()
+    rs = np.random.RandomState(1000 + k)
+    srcs = rs.randint(0, g.n, size=k).astype(np.int32)
+    ref = oracle.bfs_many(g, srcs)
+    with blest.build_graph(g) as h:
+        h.set_msbfs_engine(True)
+        got = h.msbfs(srcs)
+        bad = np.argwhere(got != ref)
+        assert len(bad) == 0, (name, k, bad[:5])
+        # twice in a row, and back on CUDA cores: the same levels
+        assert np.array_equal(h.msbfs(srcs), ref)
+        h.set_msbfs_engine(False)
+        assert np.array_equal(h.msbfs(srcs), ref)
+
+
+@pytest.mark.parametrize("name,k", [("rmat12", 64), ("grid_ragged", 200), ("union", 700)])
+def test_tensor_core_engine_work_counters(blest, name, k):
+    g = MAKERS[name]()
+    srcs = gg.sources(g, k, 11)
+    ref = oracle.bfs_many(g, srcs)
+    kappa = 64 if k <= 64 else (256 if k <= 256 else 1024)
+    want = _expected_counters(g, len(srcs), kappa, ref, oracle.bvss(g, 8, 128))
+    with blest.build_graph(g) as h:
+        h.set_msbfs_engine(True)
+        assert np.array_equal(h.msbfs(srcs), ref)
+        st = h.msbfs_stats()
+    for f in ("levels", "vss", "dirty_sets", "hit_words"):
+        assert st[f] == want[f], (f, st[f], want[f])
+
+
+def test_tensor_core_closeness_and_layout_check(blest):
+    g = gg.disjoint_union(gg.rmat(10, seed=9), gg.path(70), gg.from_edges(3, [], [], True))
+    f_r, r_r, cc_r = oracle.closeness(g)
+    with blest.build_graph(g) as h:
+        h.set_msbfs_engine(True)
+        far, cc, reach = h.closeness()
+        assert np.array_equal(far, f_r) and np.array_equal(reach, r_r)
+        assert np.allclose(cc, cc_r, rtol=1e-12, atol=0)
+    with blest.build_graph(g, tau=32) as h:
+        with pytest.raises(blest.BlestError) as e:
+            h.set_msbfs_engine(True)
+        assert e.value.code == blest.ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("reindex,tracking", [(0, 0), (1, 0), (0, 1)])
+@pytest.mark.parametrize("name", sorted(MAKERS))
+@pytest.mark.parametrize("tau", [128, 32])
+def test_msbfs_ablation_variants_levels(blest, name, tau, reindex, tracking):
+    """The ablation's multi-source variants -- without getVI reindexing and /
+    or without activeSets / dirtySets tracking -- give the same levels and
+    closeness sums as Algorithm 5 in full."""
+    g = MAKERS[name]()
+    srcs = np.random.RandomState(5).randint(0, g.n, size=300).astype(np.int32)
+    ref = oracle.bfs_many(g, srcs)
+    with blest.build_graph(g, tau=tau) as h:
+        h.set_msbfs_variant(reindex, tracking)
+        assert np.array_equal(h.msbfs(srcs), ref)
+        assert np.array_equal(h.msbfs(srcs[:40]), ref[:40])
+        if not g.directed:
+            far, cc, reach = h.closeness()
+            f_r, r_r, _ = oracle.closeness(g)
+            assert np.array_equal(far, f_r) and np.array_equal(reach, r_r)
+        with pytest.raises(blest.BlestError):
+            h.set_msbfs_engine(True)        # the tensor-core engine runs Algorithm 5 in full only
+        h.set_msbfs_variant(True, True)
+        assert np.array_equal(h.msbfs(srcs[:40]), ref[:40])

@@ -252,3 +252,31 @@ def test_k3_identity(alpha):
     for t in range(32):
         for c in range(4):
             assert hits[t, c] == (((int(words[t]) >> (8 * c)) & 0xFF & alpha) != 0)
+
+
+@pytest.mark.parametrize("alpha", [0, 1, 0x80, 0xFF, 0x5A])
+def test_one_slice_per_row_layout_needs_sixteen_mmas(alpha):
+    """The layout Fig. 3 improves on (one slice per fragment row, the
+    frontier in fragB column 0): MMA i takes slices 8i .. 8i + 7, slice 8i + r
+    in the low byte of lane 4r's fragA word; D[r][0] (lane 4r, first entry)
+    is its popcount against alpha.  16 MMAs cover a 128-slice VSS (Fig. 3's
+    layout: 2), and only column 0 of each fragC is useful."""
+    rs = np.random.RandomState(7 + alpha)
+    words = rs.randint(0, 2 ** 32, 32, dtype=np.uint64)
+    words[3] = 0
+    fb = np.zeros(32, np.uint64)
+    fb[0] = alpha
+    want = oracle.slice_hits(words, alpha)
+    used = np.zeros((32, 2), bool)
+    for i in range(16):
+        a = np.zeros(32, np.uint64)
+        for t in range(0, 32, 4):
+            r = t // 4
+            a[t] = (int(words[2 * i + r // 4]) >> (8 * (r % 4))) & 0xFF
+        d = oracle.mma_m8n8k128_b1(a, fb)
+        for r in range(8):
+            k = 8 * i + r
+            assert (d[4 * r, 0] > 0) == want[k // 4, k % 4]
+            used[4 * r, 0] = True
+        assert not d[~used].any()        # every other fragC entry is zero: wasted
+    assert used.sum() == 8               # 8 of the 64 fragC entries per MMA
