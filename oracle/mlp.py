@@ -114,11 +114,13 @@ BU_GUARD_LOG = np.log(16.0)
 def choose(w, raw):
     """Choice with the smallest predicted log time (lowest index on ties);
     bottom-up (choice 4) is excluded on levels with more than 16 unvisited
-    vertices per scheduled slot (raw features 2 and 3)."""
+    vertices per out-arc of the frontier (raw features 2 and 1): a
+    bottom-up level reads every unvisited vertex, a top-down level the
+    frontier's arcs."""
     y, _ = forward(w, raw)
     raw = np.atleast_2d(np.asarray(raw, np.float64))
     y = np.array(y, np.float64, copy=True).reshape(raw.shape[0], OUT)
-    y[raw[:, 2] > raw[:, 3] + BU_GUARD_LOG, 4] = np.inf
+    y[raw[:, 2] > raw[:, 1] + BU_GUARD_LOG, 4] = np.inf
     return np.argmin(y, axis=-1)
 
 

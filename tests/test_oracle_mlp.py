@@ -99,10 +99,14 @@ def test_raw_features():
 
 def test_bottom_up_guard():
     """Bottom-up (choice 4) is skipped exactly when log1p(unvisited) >
-    log1p(slots) + log 16, i.e. more than about 16 unvisited vertices per
-    scheduled slot; otherwise the plain argmin stands."""
+    log1p(frontier out-arcs) + log 16, i.e. more than about 16 unvisited
+    vertices per frontier arc; otherwise the plain argmin stands.  The
+    scheduled slots play no part."""
     w = np.zeros(mlp.NW)
     w[mlp.OFF_ISTD:mlp.OFF_ISTD + 6] = 1.0
     w[mlp.OFF_B3:] = [5, 5, 5, 5, 1, 5, 5, 5, 2]          # bottom-up predicted fastest, choice 8 next
-    raw = mlp.raw_features([10, 10, 10], [40, 40, 40], [1000, 1e6, 16e6], [1e6, 1e4, 1e6], [3, 3, 3], 4.0)
+    raw = mlp.raw_features([10, 10, 10], [1e6, 1e4, 1e6], [1000, 1e6, 16e6], [40, 1e9, 40], [3, 3, 3], 4.0)
     assert mlp.choose(w, raw).tolist() == [4, 8, 4]
+    # 16e6 + 1 < 16 (1e6 + 1): just inside; 16 (1e6 + 1) + 100 unvisited: outside
+    raw2 = mlp.raw_features([10], [1e6], [16e6 + 116], [40], [3], 4.0)
+    assert mlp.choose(w, raw2).tolist() == [8]
