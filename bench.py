@@ -626,6 +626,8 @@ def main():
     ap.add_argument("--scale", type=int, default=20, help="RMAT scale of the msbfs_one workload")
     ap.add_argument("--kappa", type=int, default=1024, help="sources of the msbfs_one workload")
     ap.add_argument("--engine", default="cc", choices=["cc", "tc"], help="multi-source stage 1 of msbfs_one")
+    ap.add_argument("--direction", type=int, default=0, choices=[0, 1, 2],
+                    help="multi-source stage 1 of msbfs_one: 0 push, 1 pull on dense levels, 2 pull")
     ap.add_argument("--configs", default="C1,C3,C4,C5",
                     help="per_config entries besides the headline (C2) of the default workload")
     args = ap.parse_args()
@@ -714,6 +716,9 @@ def msbfs_algorithmic_bytes(st, n, tau=128, sigma=8, levels_out=True, closeness=
         4 B per nonzero 32-lane hit word OR-ed into V_next;
       stage 2, per dirty slice set: its sigma vertices' elements of V_next
         and V_curr read and of F and V_curr written (4 kappa / 8 B each);
+      pulled levels: every vertex's V_curr element (kappa / 8 B) and, per
+        in-neighbour read, its frontier element, slice-set stamp and id
+        (kappa / 8 + 8 B);
       init: F, V_curr, V_next zeroed (3 kappa / 8 B per vertex) per launch;
       levels: the output floor, 4 kappa B per vertex per launch (each level
         written once);
@@ -722,6 +727,7 @@ def msbfs_algorithmic_bytes(st, n, tau=128, sigma=8, levels_out=True, closeness=
     theta = 32 // sigma
     per_vss = 4.0 * tau + 4.0 * tau / theta + 8.0 + sigma * kappa / 8.0 + kappa / 8.0
     b = st["vss"] * per_vss + 4.0 * st["hit_words"] + st["dirty_sets"] * sigma * 4.0 * kappa / 8.0
+    b += st.get("pull_levels", 0) * n * kappa / 8.0 + st.get("pull_arcs", 0) * (kappa / 8.0 + 8.0)
     b += st["launches"] * n * 3.0 * kappa / 8.0
     if levels_out:
         b += st["launches"] * 4.0 * kappa * n
@@ -1168,6 +1174,7 @@ def run_msbfs_one(args, ctx):
     h = blest.build(g.n, g.row_ptr, g.col)
     h.set_stream(stream.cuda_stream, True)
     h.set_msbfs_engine(args.engine == "tc")
+    h.set_msbfs_direction(args.direction)
     sd = torch.from_numpy(srcs).to(dev)
     out = torch.empty((len(srcs), g.n), dtype=torch.int32, device=dev)
     for _ in range(args.warmup):
@@ -1191,7 +1198,7 @@ def run_msbfs_one(args, ctx):
     return {"metric": "GTEPS (aggregate), one multi-source configuration", "value": edges / (ms * 1e-3) / 1e9,
             "unit": "GTEPS", "ms_per_step": ms,
             "config": {"workload": "msbfs_one", "graph": f"RMAT scale {args.scale}, edge factor 16",
-                       "kappa": len(srcs), "engine": args.engine},
+                       "kappa": len(srcs), "engine": args.engine, "direction": args.direction},
             "counters": st, "first_lanes_exact": bool(ok),
             "roofline": _roof(ctx, nb, ms * 1e-3, ("k_msbfs_tc" if args.engine == "tc" else "k_msbfs")),
             "gpu_launches": args.steps}
@@ -1209,8 +1216,9 @@ def run_ablation(args, ctx):
     CUDA-core hit test; learned level policy.  Multi-source (256 sources on
     RMAT 22 and the 2048^2 grid): (Naive) 256 single-source BFSs of the full
     method; (A) Algorithm 5 without getVI reindexing or activeSets /
-    dirtySets tracking; (AB) without tracking; (Full) Algorithm 5; (Full,
-    tcgen05) its stage 1 on the tensor cores.  Levels of a sample of sources
+    dirtySets tracking; (AB) without tracking; (Full) Algorithm 5 (push);
+    (Full, tcgen05) its stage 1 on the tensor cores; then this build's
+    direction-optimizing stage 1 (pull on dense levels, pull always).  Levels of a sample of sources
     per rung are checked against the oracle."""
     import oracle
     torch, blest, dev, stream = ctx.torch, ctx.blest, ctx.dev, ctx.stream
@@ -1289,13 +1297,15 @@ def run_ablation(args, ctx):
         h.set_policy(blest.POLICY_HEURISTIC)
         ms = _time_sources(ctx, h, srcs, out1)
         res["Naive"] = {"seconds": float(ms.sum()) * 1e-3}
-        variants = [("A", (0, 0), 0), ("AB", (1, 0), 0), ("Full", (1, 1), 0)]
+        variants = [("A", (0, 0), 0, 0), ("AB", (1, 0), 0, 0), ("Full", (1, 1), 0, 0)]
         if tau == 128:
-            variants.append(("Full, tcgen05 stage 1", (1, 1), 1))
-        for rung, (ri, tr), eng in variants:
+            variants.append(("Full, tcgen05 stage 1", (1, 1), 1, 0))
+        variants += [("Full, pull on dense levels", (1, 1), 0, 1), ("Full, pull on every level", (1, 1), 0, 2)]
+        for rung, (ri, tr), eng, direction in variants:
             h.set_msbfs_engine(False)
             h.set_msbfs_variant(ri, tr)
             h.set_msbfs_engine(bool(eng))
+            h.set_msbfs_direction(direction)
             h.msbfs(sd, out)
             h.sync()
             a, b = ctx.events()

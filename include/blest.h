@@ -174,6 +174,19 @@ blest_status blest_msbfs(blest_handle h, const int32_t *sources, int32_t k, int3
  * otherwise). */
 blest_status blest_set_msbfs_engine(blest_handle h, int32_t tc);
 
+/* Direction of the multi-source stage 1.  0 = push (Algorithm 5: each
+ * active VSS ORs its slots' hit words into V_next with atomics; the
+ * default); 2 = pull: every vertex with an unvisited lane ORs the frontier
+ * elements of its in-neighbours (stopping once all its unvisited lanes are
+ * reached) and writes its own V_next word, no atomics; 1 = pull on levels
+ * whose queue holds more than an eighth of the VSSs, push on the others.
+ * Pulling reaches exactly the lanes pushing does (Eq. 2 read by row);
+ * levels are identical.  Pull levels run on CUDA cores whatever the
+ * stage-1 engine.  Measured on GB300 (RMAT 22, 1024 lanes): push 127 ms,
+ * 1: 158 ms, 2: 192 ms -- each pulled in-neighbour is a dependent
+ * 128-byte read, slower than the atomics it replaces. */
+blest_status blest_set_msbfs_direction(blest_handle h, int32_t mode);
+
 /* Variant of the multi-source kernel (for the ablation of §7.1): reindex =
  * 1 stores vertex u's kappa-bit element at getVI(u) (§6.1), 0 at u;
  * tracking = 1 visits only the active slice sets' VSSs in stage 1 and the
@@ -215,6 +228,8 @@ typedef struct blest_msbfs_counters {
     int64_t vss;          /* VSSs processed in stage 1 */
     int64_t hit_words;    /* nonzero 32-lane words OR-ed into V_next */
     int64_t dirty_sets;   /* slice sets finalised in stage 2 */
+    int64_t pull_levels;  /* levels whose stage 1 pulled (blest_set_msbfs_direction) */
+    int64_t pull_arcs;    /* in-neighbour elements read by pulling vertices */
 } blest_msbfs_counters;
 
 blest_status blest_msbfs_stats(blest_handle h, blest_msbfs_counters *out);
@@ -255,16 +270,6 @@ blest_status blest_set_launch(blest_handle h, int32_t block_threads, int32_t vss
  * build decides it (§7.1: by the three-source probe for graphs that use
  * lazy updates, off otherwise); this overrides that decision. */
 blest_status blest_set_switching(blest_handle h, int32_t on);
-
-/* Queue entries a single-source level writes (§5's VSS queue Q_next).  A
- * level that schedules more VSSs than this counts them without writing
- * them, and the next top-down level then scans every VSS and keeps those
- * whose slice set has a frontier bit (the frontier bitvector is exact), so
- * a dense frontier costs neither the queue writes nor their reads.
- * cap = 0: the default, max(N_v / 2, 1024) clamped to N_v; otherwise cap
- * entries (clamped to N_v; 1 makes nearly every level scan).  Levels are
- * identical whatever the cap. */
-blest_status blest_set_queue_cap(blest_handle h, int64_t cap);
 
 /* Per-level modes for BLEST_POLICY_SCHEDULE: level l (1-based) runs
  * modes[(l-1) % len].  Copied. */
@@ -313,8 +318,8 @@ const char *blest_status_string(blest_status s);
  * choices 0-4 are the modes BLEST_MODE_* (lazy ones with one pass), 5 and 6
  * lazy CUDA-core with 2 and 4 passes, 7 and 8 lazy b1-MMA with 2 and 4.
  * Bottom-up is never chosen for a level with more than 16 unvisited
- * vertices per scheduled slot (raw features: log1p(unvisited) >
- * log1p(slots) + log 16), whatever the prediction.
+ * vertices per out-arc of its frontier (raw features: log1p(unvisited) >
+ * log1p(frontier_edges) + log 16), whatever the prediction.
  * Weights: BLEST_MLP_NW floats, [0,6) feature means, [6,12) feature 1/std,
  * then W1[32][6], b1[32], W2[32][32], b2[32], W3[9][32], b3[9].  All arrays
  * below may be host or device memory and are row-major (one sample per

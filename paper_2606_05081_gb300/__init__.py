@@ -97,7 +97,8 @@ class ScaleFreeReport(ctypes.Structure):
 class MsbfsStats(ctypes.Structure):
     """blest_msbfs_stats: work counters of the last multi-source call."""
     _fields_ = [("kappa", ctypes.c_int64), ("launches", ctypes.c_int64), ("levels", ctypes.c_int64),
-                ("vss", ctypes.c_int64), ("hit_words", ctypes.c_int64), ("dirty_sets", ctypes.c_int64)]
+                ("vss", ctypes.c_int64), ("hit_words", ctypes.c_int64), ("dirty_sets", ctypes.c_int64),
+                ("pull_levels", ctypes.c_int64), ("pull_arcs", ctypes.c_int64)]
 
 
 _P = ctypes.c_void_p
@@ -116,10 +117,10 @@ _sigs = {
     "blest_set_schedule": (_S, [_H, _P, ctypes.c_int32]),
     "blest_set_engine": (_S, [_H, ctypes.c_int32]),
     "blest_set_launch": (_S, [_H, ctypes.c_int32, ctypes.c_int32]),
-    "blest_set_queue_cap": (_S, [_H, ctypes.c_int64]),
     "blest_set_switching": (_S, [_H, ctypes.c_int32]),
     "blest_set_msbfs_engine": (_S, [_H, ctypes.c_int32]),
     "blest_set_msbfs_variant": (_S, [_H, ctypes.c_int32, ctypes.c_int32]),
+    "blest_set_msbfs_direction": (_S, [_H, ctypes.c_int32]),
     "blest_load_model": (_S, [_H, _P, ctypes.c_int32]),
     "blest_last_timings": (_S, [_H, _P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
     "blest_get_info": (_S, [_H, ctypes.POINTER(Info)]),
@@ -288,6 +289,11 @@ class Graph:
         on CUDA cores (the default)."""
         _check(_lib.blest_set_msbfs_engine(self._h, int(bool(tc))), "blest_set_msbfs_engine")
 
+    def set_msbfs_direction(self, mode: int):
+        """Multi-source stage 1: 0 push (Algorithm 5, the default), 1 pull on
+        dense levels, 2 pull on every level."""
+        _check(_lib.blest_set_msbfs_direction(self._h, int(mode)), "blest_set_msbfs_direction")
+
     def set_msbfs_variant(self, reindex: bool = True, tracking: bool = True):
         """Multi-source kernel variant of the ablation: getVI reindexing and
         activeSets / dirtySets tracking on or off (both on = Algorithm 5)."""
@@ -297,11 +303,6 @@ class Graph:
     def set_switching(self, on: bool):
         """Eq. 5 bottom-up switching of the rule on or off (overrides the build's probe)."""
         _check(_lib.blest_set_switching(self._h, int(bool(on))), "blest_set_switching")
-
-    def set_queue_cap(self, cap: int):
-        """Queue entries a level writes before the next level scans instead
-        (0 = the default)."""
-        _check(_lib.blest_set_queue_cap(self._h, int(cap)), "blest_set_queue_cap")
 
     def set_schedule(self, modes):
         m = np.ascontiguousarray(modes, dtype=np.int32)

@@ -32,9 +32,6 @@ constexpr int BFS_MAX_THREADS = 1024;
 
 struct BfsParams {
     int n, W;
-    int Nv;                 // VSSs of the BVSS
-    int qcap;               // queue entries written per level; a longer queue is counted, not written,
-                            // and the next top-down level scans every VSS's frontier field instead
     const int *__restrict__ rowIds;
     const unsigned *__restrict__ masks;
     const int *__restrict__ realPtrs;
@@ -200,18 +197,12 @@ constexpr int STG_BYTES = STG_Q * 8 + STG_S * 4;
 // Per-CTA totals of a level's appends and counters (shared memory, zeroed at
 // the level start): the level's last flush reserves queue space and adds
 // the counters once per CTA instead of once per warp, so the control block
-// sees a few hundred atomics per level rather than thousands.  Long VSS
-// ranges (a hub's slice set spans thousands of VSSs) are reserved at once
-// and listed here, and the whole CTA writes them at the flush, so no warp
-// is left alone with thousands of stores at the end of a level.
-constexpr int BIG_MAX = 64;
+// sees a few hundred atomics per level rather than thousands.
 struct BlkAcc {
     int q, s;                       // staged queue entries / slice-set ids of the CTA
     int qbase, sbase;               // the CTA's reserved offsets
     unsigned long long nv, fe;      // newly visited vertices and their out-arcs
     unsigned long long sv, sa;      // bottom-up: probed vertices and extra arcs read
-    int nbig;                       // long ranges listed (may exceed BIG_MAX: the rest are written inline)
-    int4 big[BIG_MAX];              // {first VSS, count, slice set, queue position}
 };
 
 struct Stage {
@@ -231,7 +222,7 @@ __device__ __forceinline__ void stage_flush(const BfsParams &P, Stage &st, int2 
     }
     qb = __shfl_sync(FULL_MASK, qb, 0);
     sb = __shfl_sync(FULL_MASK, sb, 0);
-    for (int k = lane; k < st.qn && qb + k < P.qcap; k += 32) Q[qb + k] = st.q[k];
+    for (int k = lane; k < st.qn; k += 32) Q[qb + k] = st.q[k];
     for (int k = lane; k < st.sqn; k += 32) SQ[sb + k] = st.sq[k];
     __syncwarp();
     st.qn = 0;
@@ -241,22 +232,59 @@ __device__ __forceinline__ void stage_flush(const BfsParams &P, Stage &st, int2 
 // Warp-aggregated enqueue of up to 4 slice sets per lane (bit c of `want`
 // set => slice set ss[c], whose VSSs are [a[c], a[c] + len[c])): the VSS
 // ranges go to Q, the set ids to SQ, both through the warp's staging area.
-// Short ranges are written by their own lane, medium ones by the whole
-// warp, long ones (at least ENQ_CTA_MIN VSSs) are reserved at once and
-// written by the whole CTA at the level's flush; a batch larger than the
-// staging area reserves its own space in Q.  Every entry is counted in the
-// level's queue length; entries at positions >= qcap are not written.
+// Short ranges are written by their own lane; a long range (the slice set
+// of a hub vertex spans thousands of VSSs) by the whole warp, so no lane
+// issues a long serial run of stores; a batch larger than the staging area
+// reserves its own space in Q.
 constexpr int ENQ_LANE_MAX = 8;
-constexpr int ENQ_CTA_MIN = 64;
 
-__device__ __forceinline__ void warp_write_ranges(const BfsParams &P, unsigned sel, const int a[4], const int len[4],
-                                                  const int pos[4], const int ss[4], int2 *dst, int lim) {
+__device__ __forceinline__ void enqueue_ranges(const BfsParams &P, Stage &st, unsigned want, const int ss[4],
+                                               const int a[4], const int len[4], int2 *Q, int *SQ, int slot) {
     const int lane = lane_id();
-    unsigned lanes = __ballot_sync(FULL_MASK, sel != 0);
+    if (!__any_sync(FULL_MASK, want != 0)) return;
+    int tot = 0, nset = 0;
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+        if (want >> c & 1u) { tot += len[c]; ++nset; }
+    const int incl = warp_incl_scan(tot);
+    const int sincl = warp_incl_scan(nset);
+    const int T = __shfl_sync(FULL_MASK, incl, 31);
+    const int S = __shfl_sync(FULL_MASK, sincl, 31);
+    if ((T <= STG_Q && st.qn + T > STG_Q) || st.sqn + S > STG_S) stage_flush(P, st, Q, SQ, slot);
+    int2 *dst;
+    int qbase;
+    if (T > STG_Q) {
+        int g = 0;
+        if (lane == 31) g = atomicAdd(&P.ctl->qlen[slot], T);
+        dst = Q + __shfl_sync(FULL_MASK, g, 31);
+        qbase = incl - tot;
+    } else {
+        dst = st.q;
+        qbase = st.qn + incl - tot;
+        st.qn += T;
+    }
+    int sbase = st.sqn + sincl - nset;
+    st.sqn += S;
+    int pos[4];
+    unsigned big = 0;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        pos[c] = qbase;
+        if (want >> c & 1u) {
+            st.sq[sbase++] = ss[c];
+            if (len[c] <= ENQ_LANE_MAX) {
+                for (int k = 0; k < len[c]; ++k) dst[qbase + k] = make_int2(a[c] + k, ss[c]);
+            } else {
+                big |= 1u << c;
+            }
+            qbase += len[c];
+        }
+    }
+    unsigned lanes = __ballot_sync(FULL_MASK, big != 0);
     while (lanes) {
         const int j = __ffs(lanes) - 1;
         lanes &= lanes - 1u;
-        const unsigned bj = __shfl_sync(FULL_MASK, sel, j);
+        const unsigned bj = __shfl_sync(FULL_MASK, big, j);
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             const int aj = __shfl_sync(FULL_MASK, a[c], j);
@@ -264,84 +292,9 @@ __device__ __forceinline__ void warp_write_ranges(const BfsParams &P, unsigned s
             const int pj = __shfl_sync(FULL_MASK, pos[c], j);
             const int sj = __shfl_sync(FULL_MASK, ss[c], j);
             if (bj >> c & 1u)   // warp-uniform
-                for (int k = lane; k < lj && pj + k < lim; k += 32) dst[pj + k] = make_int2(aj + k, sj);
+                for (int k = lane; k < lj; k += 32) dst[pj + k] = make_int2(aj + k, sj);
         }
     }
-}
-
-__device__ __forceinline__ void enqueue_ranges(const BfsParams &P, Stage &st, BlkAcc *acc, unsigned want,
-                                               const int ss[4], const int a[4], const int len[4], int2 *Q, int *SQ,
-                                               int slot) {
-    const int lane = lane_id();
-    if (!__any_sync(FULL_MASK, want != 0)) return;
-    // long ranges: reserved one by one and listed for the CTA-wide write
-    unsigned longr = 0;
-#pragma unroll
-    for (int c = 0; c < 4; ++c)
-        if ((want >> c & 1u) && len[c] >= ENQ_CTA_MIN) longr |= 1u << c;
-    if (__any_sync(FULL_MASK, longr != 0)) {
-        unsigned ovf = 0;
-        int opos[4] = {0, 0, 0, 0};
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            if (longr >> c & 1u) {
-                const int p = atomicAdd(&P.ctl->qlen[slot], len[c]);
-                opos[c] = p;
-                if (p < P.qcap) {
-                    const int i = atomicAdd(&acc->nbig, 1);
-                    if (i < BIG_MAX) acc->big[i] = make_int4(a[c], min(len[c], P.qcap - p), ss[c], p);
-                    else ovf |= 1u << c;   // the CTA list is full: the warp writes it now
-                }
-            }
-        }
-        if (__any_sync(FULL_MASK, ovf != 0)) warp_write_ranges(P, ovf, a, len, opos, ss, Q, P.qcap);
-    }
-    int tot = 0, nset = 0;
-#pragma unroll
-    for (int c = 0; c < 4; ++c)
-        if (want >> c & 1u) {
-            ++nset;
-            if (!(longr >> c & 1u)) tot += len[c];
-        }
-    const int incl = warp_incl_scan(tot);
-    const int sincl = warp_incl_scan(nset);
-    const int T = __shfl_sync(FULL_MASK, incl, 31);
-    const int S = __shfl_sync(FULL_MASK, sincl, 31);
-    if ((T <= STG_Q && st.qn + T > STG_Q) || st.sqn + S > STG_S) stage_flush(P, st, Q, SQ, slot);
-    int2 *dst;
-    int qbase, lim;
-    if (T > STG_Q) {
-        int g = 0;
-        if (lane == 31) g = atomicAdd(&P.ctl->qlen[slot], T);
-        g = __shfl_sync(FULL_MASK, g, 31);
-        dst = Q + g;
-        lim = P.qcap - g;   // positions past the cap are counted, not written
-        qbase = incl - tot;
-    } else {
-        dst = st.q;
-        lim = STG_Q;        // the flush applies the cap
-        qbase = st.qn + incl - tot;
-        st.qn += T;
-    }
-    int sbase = st.sqn + sincl - nset;
-    st.sqn += S;
-    int pos[4];
-    unsigned mid = 0;
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        pos[c] = qbase;
-        if (want >> c & 1u) {
-            st.sq[sbase++] = ss[c];
-            if (longr >> c & 1u) continue;
-            if (len[c] <= ENQ_LANE_MAX) {
-                for (int k = 0; k < len[c] && qbase + k < lim; ++k) dst[qbase + k] = make_int2(a[c] + k, ss[c]);
-            } else {
-                mid |= 1u << c;
-            }
-            qbase += len[c];
-        }
-    }
-    warp_write_ranges(P, mid, a, len, pos, ss, dst, lim);
     __syncwarp();
 }
 
@@ -377,14 +330,8 @@ __device__ __forceinline__ void block_flush(const BfsParams &P, Stage &st, BlkAc
     }
     __syncthreads();
     const int qb = acc->qbase + wq, sb = acc->sbase + ws;
-    for (int k = lane; k < st.qn && qb + k < P.qcap; k += 32) Q[qb + k] = st.q[k];
+    for (int k = lane; k < st.qn; k += 32) Q[qb + k] = st.q[k];
     for (int k = lane; k < st.sqn; k += 32) SQ[sb + k] = st.sq[k];
-    // the CTA's long ranges, all threads on each in turn
-    const int nb = min(acc->nbig, BIG_MAX);
-    for (int e = 0; e < nb; ++e) {
-        const int4 r = acc->big[e];
-        for (int k = (int)threadIdx.x; k < r.y; k += (int)blockDim.x) Q[r.w + k] = make_int2(r.x + k, r.z);
-    }
     __syncwarp();
     st.qn = 0;
     st.sqn = 0;
@@ -507,7 +454,7 @@ __device__ __forceinline__ void push_entries(const BfsParams &P, Stage &st, BlkA
                 red_or(&P.Vc[wword], wbits);
                 red_or(&P.Vn[wword], wbits);
             }
-            enqueue_ranges(P, st, acc, want, sso, a, len, P.Q[bn], P.SQ[bn], slot);
+            enqueue_ranges(P, st, want, sso, a, len, P.Q[bn], P.SQ[bn], slot);
         } else {
             // lazy marking: fire-and-forget ORs into V_next, one per distinct word
             // among the lane's own rows (they ascend, so equal words are adjacent)
@@ -537,9 +484,7 @@ __device__ __forceinline__ void push_entries(const BfsParams &P, Stage &st, BlkA
 // dependent-load chain is paid once per B*G VSSs.  Passes are interleaved
 // over the blocks; the warps of a block claim their block's next pass from
 // a shared counter, so a warp whose passes hit many rows does not hold up
-// the level.  A queue longer than qcap was counted but not written: the
-// level then scans all VSSs, 32 per claim, keeping those whose slice set
-// has a frontier bit (the frontier F is exact), B*G at a time.
+// the level.
 template <bool EAGER, int HIT, int B, int SIGMA, int LPV>
 __device__ void push_level(const BfsParams &P, Stage &st, int *grab, BlkAcc *acc, int ell, int bc, int bn, int slot,
                            int qlen, unsigned bsel) {
@@ -549,42 +494,17 @@ __device__ void push_level(const BfsParams &P, Stage &st, int *grab, BlkAcc *acc
     const unsigned *Fc = P.F[bc];
     const int2 *Qc = P.Q[bc];
     unsigned long long nv = 0, fe = 0;
-    if (qlen <= P.qcap) {
-        const int npass = (qlen + B * G - 1) / (B * G);
-        for (;;) {
-            int k = 0;
-            if (lane == 0) k = atomicAdd(grab, 1);
-            k = __shfl_sync(FULL_MASK, k, 0);
-            const int pass = (int)blockIdx.x + k * (int)gridDim.x;
-            if (pass >= npass) break;
-            const int w0 = pass * B * G;
-            // lane j < B*G fetches queue entry w0 + j (VSS and slice set)
-            const int2 mine = (lane < B * G && w0 + lane < qlen) ? Qc[w0 + lane] : make_int2(-1, 0);
-            push_entries<EAGER, HIT, B, SIGMA, LPV>(P, st, acc, ell, bc, bn, slot, bsel, mine, qlen - w0, nv, fe);
-        }
-    } else {
-        // (the scan's state stays inside this branch: the queue loop above is
-        // the one small levels run, and it keeps its register budget)
-        const int nchunk = (P.Nv + 31) / 32;
-        for (;;) {
-            int k = 0;
-            if (lane == 0) k = atomicAdd(grab, 1);
-            k = __shfl_sync(FULL_MASK, k, 0);
-            const int chunk = (int)blockIdx.x + k * (int)gridDim.x;
-            if (chunk >= nchunk) break;
-            const int cv = chunk * 32 + lane;
-            const int cs = cv < P.Nv ? __ldg(&P.v2r[cv]) : -1;
-            unsigned am = __ballot_sync(FULL_MASK, cs >= 0 && ld_field<SIGMA>(Fc, cs) != 0u);
-            while (am) {   // warp-uniform: the chunk's active VSSs, B*G at a time
-                const int take = min(__popc(am), B * G);
-                const int src = nth_set_bit(am, lane < take ? lane : 0);
-                const int v_ = __shfl_sync(FULL_MASK, cv, src);
-                const int s_ = __shfl_sync(FULL_MASK, cs, src);
-                const int2 mine = lane < take ? make_int2(v_, s_) : make_int2(-1, 0);
-                for (int t = 0; t < take; ++t) am &= am - 1u;
-                push_entries<EAGER, HIT, B, SIGMA, LPV>(P, st, acc, ell, bc, bn, slot, bsel, mine, take, nv, fe);
-            }
-        }
+    const int npass = (qlen + B * G - 1) / (B * G);
+    for (;;) {
+        int k = 0;
+        if (lane == 0) k = atomicAdd(grab, 1);
+        k = __shfl_sync(FULL_MASK, k, 0);
+        const int pass = (int)blockIdx.x + k * (int)gridDim.x;
+        if (pass >= npass) break;
+        const int w0 = pass * B * G;
+        // lane j < B*G fetches queue entry w0 + j (VSS and slice set)
+        const int2 mine = (lane < B * G && w0 + lane < qlen) ? Qc[w0 + lane] : make_int2(-1, 0);
+        push_entries<EAGER, HIT, B, SIGMA, LPV>(P, st, acc, ell, bc, bn, slot, bsel, mine, qlen - w0, nv, fe);
     }
     if (EAGER) {
         block_flush(P, st, acc, P.Q[bn], P.SQ[bn], slot, nv, fe);
@@ -832,7 +752,7 @@ __device__ __forceinline__ void finalize_group(const BfsParams &P, Stage &st, Bl
     }
 #pragma unroll
     for (int c = 0; c < 4; ++c) rl[c] -= ra[c];
-    enqueue_ranges(P, st, acc, want, sso, ra, rl, P.Q[bn], P.SQ[bn], slot);
+    enqueue_ranges(P, st, want, sso, ra, rl, P.Q[bn], P.SQ[bn], slot);
     fe += (unsigned long long)(dv[0] + dv[1]) + (unsigned long long)(dv[2] + dv[3]);
 }
 
@@ -1105,7 +1025,6 @@ __global__ void __launch_bounds__(BFS_MAX_THREADS, 1) k_bfs(BfsParams P) {
                 s_acc.fe = 0;
                 s_acc.sv = 0;
                 s_acc.sa = 0;
-                s_acc.nbig = 0;
             }
         }
         __syncthreads();
@@ -1275,28 +1194,12 @@ blest_status bfs_prepare(blest_graph *h) {
     return BLEST_OK;
 }
 
-// Queue entries a level writes: half of the VSSs (at least 1024, at most
-// all of them).  A level whose queue is longer is dense enough that the next
-// top-down level scans every VSS instead of reading a queue (measured: on
-// the road-like grid, whose narrow VSSs make the queue cheap, a scan at an
-// eighth of the VSSs was 20 us a level slower than the queue; dense RMAT
-// levels, where a hub's slice set spans thousands of VSSs, queue about 70 %
-// of them and are followed by bottom-up levels that read no queue).
-static int bfs_queue_cap(int64_t Nv) {
-    int64_t c = Nv / 2;
-    if (c < 1024) c = 1024;
-    if (c > Nv) c = Nv;
-    return (int)c;
-}
-
 // Enqueue one BFS on h->stream; levels (original ids) land in dev_out.
 blest_status bfs_run(blest_graph *h, int32_t source, int32_t *dev_out) {
     BfsParams P;
     memset(&P, 0, sizeof P);
     P.n = (int)h->n;
     P.W = (int)((h->n + 31) / 32);
-    P.Nv = (int)h->Nv;
-    P.qcap = h->qcap > 0 ? (int)h->qcap : bfs_queue_cap(h->Nv);
     const void *kern = bfs_kernel_for(h->sigma, h->tau, h->block);
     if (!kern) return BLEST_ERR_INTERNAL;
     P.rowIds = h->g.rowIds;
@@ -1452,8 +1355,6 @@ extern "C" blest_status blest_bfs_noalloc(const blest_bvss_view *g, int32_t sour
     if (off > NOALLOC_BYTES) return BLEST_ERR_INTERNAL;
     P.n = (int)n;
     P.W = (int)W;
-    P.Nv = (int)g->num_vss;
-    P.qcap = (int)nv;   // the scratch queues hold every VSS: always written
     P.rowIds = g->row_ids;
     P.masks = g->masks;
     P.realPtrs = g->real_ptrs;

@@ -256,13 +256,6 @@ extern "C" blest_status blest_set_switching(blest_handle h, int32_t on) {
     return BLEST_OK;
 }
 
-extern "C" blest_status blest_set_queue_cap(blest_handle h, int64_t cap) {
-    if (!h || h->many || cap < 0) return BLEST_ERR_INVALID;
-    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return BLEST_ERR_CUDA;
-    h->qcap = cap > h->Nv ? h->Nv : cap;
-    return BLEST_OK;
-}
-
 extern "C" blest_status blest_set_schedule(blest_handle h, const int32_t *modes, int32_t len) {
     if (!h || !modes || len <= 0 || len > (1 << 20)) return BLEST_ERR_INVALID;
     std::vector<int32_t> m((size_t)len);

@@ -58,8 +58,8 @@ struct blest_graph {
     int engine_tc = 1;
     int ms_engine = 0;                // multi-source stage 1: 0 CUDA cores, 1 tcgen05 (tau = 128)
     int ms_remap = 1, ms_track = 1;   // multi-source variant: getVI order, activeSets / dirtySets
+    int ms_dir = 0;                   // multi-source stage 1: 0 push, 1 pull on dense levels, 2 pull
     int vss_batch = 2;
-    int64_t qcap = 0;                 // queue entries written per level (0 = half of N_v)
     float eta = 10.f;
     double udiv_threshold = 25000.0;
     int timeout_ms = 5000;

@@ -93,14 +93,16 @@ __device__ __forceinline__ float mlp_forward_warp(const float *__restrict__ w, c
 }
 
 // Bottom-up guard: a bottom-up level reads every unvisited vertex, a
-// top-down level only the scheduled slots, so a level with more than 16
-// unvisited vertices per scheduled slot never runs bottom-up whatever the
+// top-down level the frontier's out-arcs, so a level with more than 16
+// unvisited vertices per frontier arc never runs bottom-up whatever the
 // network predicts (this keeps graphs unlike the training set away from
-// the one choice whose cost grows with the unvisited set).  Tested on the
-// raw features: log1p(unvisited) > log1p(slots) + log(16).
+// the one choice whose cost grows with the unvisited set; scheduled slots
+// would overstate the top-down work where VSSs are mostly padding).
+// Tested on the raw features: log1p(unvisited) > log1p(frontier arcs) +
+// log(16).
 #define MLP_BU_GUARD_LOG 2.7725887f
 
-__host__ __device__ inline bool mlp_bu_blocked(const float *xraw) { return xraw[2] > xraw[3] + MLP_BU_GUARD_LOG; }
+__host__ __device__ inline bool mlp_bu_blocked(const float *xraw) { return xraw[2] > xraw[1] + MLP_BU_GUARD_LOG; }
 
 // argmin over the MLP_OUT predictions (lowest index on ties), skipping
 // bottom-up (choice 4) when blocked; all lanes get it

@@ -45,6 +45,8 @@ struct MsStats {
     unsigned long long vss;         // VSSs processed in stage 1
     unsigned long long hit_words;   // nonzero kappa-bit words OR-ed into V_next
     unsigned long long dirty_sets;  // slice sets finalised in stage 2
+    unsigned long long pull_levels; // levels whose stage 1 pulled (summed over the launches)
+    unsigned long long pull_arcs;   // in-neighbour elements read by pulling vertices
 };
 
 struct MsbfsWork {
@@ -57,6 +59,7 @@ struct MsbfsWork {
     MsCtl *ctl = nullptr;
     MsCtl *h_ctl = nullptr;
     MsStats *stats = nullptr;      // device counters of the current call
+    int *stamp = nullptr;          // per slice set: the level stage 2 last finalised it
     int *d_src = nullptr;
     int grid = 0;
     int grid_tc = -1;              // grid of the tensor-core kernel (-1: not computed yet)
@@ -99,13 +102,22 @@ struct MsParams {
     int remap;                    // 1: getVI element order of §6.1; 0: element u at index u (ablation)
     int track;                    // 1: activeSets / dirtySets of Algorithm 5; 0: every VSS and every
                                   //    slice set at every level (ablation)
+    int dir;                      // stage-1 direction: 0 push (Algorithm 5), 1 pull for dense levels, 2 pull
+    const long long *rp;          // in-neighbour CSR of the (reordered) graph, for pulling
+    const int *col;
+    int *stamp;                   // per slice set: the level stage 2 last wrote its F elements
     unsigned long long budget_ns;
 };
 
-// per-CTA work counts of the current level: VSSs, hit words, dirty sets
+// per-CTA work counts of the current level: VSSs, hit words, dirty sets,
+// pulled in-neighbour elements
 struct MsAcc {
-    unsigned long long vss, hitw, dirty;
+    unsigned long long vss, hitw, dirty, parcs;
 };
+
+// A level pulls (direction 1) when its queue holds more than 1/PULL_DIV of
+// the VSSs.
+constexpr long long PULL_DIV = 8;
 
 __device__ __forceinline__ bool ms_barrier(MsCtl *ctl, unsigned &epoch, unsigned long long budget) {
     return grid_barrier(reinterpret_cast<Ctl *>(ctl), epoch, budget);
@@ -427,6 +439,7 @@ __device__ void ms_stage2(const MsParams &P, MsStage &st, int *grab, int *s_tot,
         const bool any = ((bal >> (g * KW)) & (KW == 32 ? 0xFFFFFFFFu : ((1u << KW) - 1u))) != 0;
         if (valid && w == 0) {
             if (P.track) P.dirty[ss] = 0;
+            P.stamp[ss] = ell;   // this set's F elements now hold level ell's frontier
             ++nd;
         }
         if (P.track) ms_enqueue(P, st, valid && w == 0 && any, ss, P.Q[qn], qn);
@@ -437,6 +450,91 @@ __device__ void ms_stage2(const MsParams &P, MsStage &st, int *grab, int *s_tot,
     nd = warp_sum(nd);
     if (lane_id() == 0 && nd) atomicAdd(&acc->dirty, nd);
     ms_block_flush(P.Q[qn], &P.ctl->qlen[qn], st.q, st.qn, s_tot);
+}
+
+// ------------------------------------------------------------------
+// Stage 1 by pulling (direction-optimizing, for dense levels).  Pushing
+// ORs each slot's hit word into V_next with an atomic; on a level where
+// most slice sets are active those atomics bound the kernel.  Pulling
+// visits every slice set instead (G = 32 / KW sets per warp, lane = word of
+// the kappa-bit elements): each vertex with an unvisited lane ORs the
+// frontier elements of its in-neighbours (rows sorted by descending
+// neighbour degree, so hubs come first) until every unvisited lane is
+// covered or the row ends, and writes its own V_next word without an
+// atomic.  F is rewritten only for the slice sets stage 2 finalises, so an
+// in-neighbour's element counts only when its set's stamp is the previous
+// level.  A set that gained a lane is appended to the dirty list; stage 2
+// then runs unchanged.  The lanes reached are exactly those a push would
+// add (Eq. 2 over the same slices, read by row instead of by column).
+template <int KW>
+__device__ void ms_stage1_pull(const MsParams &P, MsStage &st, int *grab, int *s_tot, int ell, int dl, int k,
+                               MsAcc *acc) {
+    constexpr int G = 32 / KW;
+    constexpr unsigned GMASK = KW == 32 ? 0xFFFFFFFFu : ((1u << KW) - 1u);
+    const int lane = lane_id();
+    const int g = lane / KW, w = lane % KW;
+    // lanes of word w that carry a source (bits of lanes >= k never get set)
+    const int lo = w * 32;
+    const unsigned lanes_w = lo + 32 <= k ? 0xFFFFFFFFu : (lo >= k ? 0u : ((1u << (k - lo)) - 1u));
+    unsigned long long nd = 0, arcs = 0;
+    const int nchunk = (P.rho + G - 1) / G;
+    for (;;) {
+        int kc = 0;
+        if (lane == 0) kc = atomicAdd(grab, 1);
+        kc = __shfl_sync(FULL_MASK, kc, 0);
+        const int chunk = (int)blockIdx.x + kc * (int)gridDim.x;
+        if (chunk >= nchunk) break;
+        const int ss = chunk * G + g;
+        const bool valid = ss < P.rho;
+        bool changed = false;
+#pragma unroll 1
+        for (int j = 0; j < 8; ++j) {
+            const int u = ss * 8 + j;
+            const bool ok = valid && u < P.n;
+            const size_t e = ok ? (size_t)elem(P, u) * KW + w : 0;
+            const unsigned vis = ok ? P.Vc[e] : 0u;
+            const unsigned unv = ok ? (~vis & lanes_w) : 0u;
+            long long p = ok ? __ldg(&P.rp[u]) : 0;
+            const long long pe = ok ? __ldg(&P.rp[u + 1]) : 0;
+            unsigned acc_w = 0;
+            // the group keeps pulling while it has an unvisited lane not yet reached
+            bool live = ((__ballot_sync(FULL_MASK, unv != 0u) >> (g * KW)) & GMASK) != 0u && p < pe;
+            while (__any_sync(FULL_MASK, live)) {
+                // four in-neighbours a step, their stamps and elements loaded together
+                int v4[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) v4[q] = (live && p + q < pe) ? __ldg(&P.col[p + q]) : -1;
+                int t4[4];
+                unsigned f4[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    t4[q] = v4[q] >= 0 ? P.stamp[v4[q] >> 3] : -1;
+                    f4[q] = v4[q] >= 0 ? P.F[(size_t)elem(P, v4[q]) * KW + w] : 0u;
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    if (t4[q] == ell - 1) acc_w |= f4[q];
+                    if (v4[q] >= 0 && w == 0) ++arcs;
+                }
+                p += 4;
+                const unsigned open = __ballot_sync(FULL_MASK, (unv & ~acc_w) != 0u);
+                live = live && p < pe && ((open >> (g * KW)) & GMASK) != 0u;
+            }
+            const unsigned nw = acc_w & unv;
+            if (nw) {
+                P.Vn[e] = vis | nw;   // V_next = V_curr before this stage: the owner writes it alone
+                changed = true;
+            }
+        }
+        // the group's set gained a lane: append it to the dirty list (lane w = 0)
+        const bool any = ((__ballot_sync(FULL_MASK, changed) >> (g * KW)) & GMASK) != 0u;
+        if (valid && w == 0 && any) P.dirty[ss] = 1;
+        ms_mark_dirty(P, st, valid && w == 0 && any, ss, dl);
+    }
+    arcs = warp_sum(arcs);
+    if (lane == 0 && arcs) atomicAdd(&acc->parcs, arcs);
+    ms_block_flush(P.dlist[dl], &P.ctl->dlen[dl], st.d, st.dn, s_tot);
+    (void)nd;
 }
 
 // ------------------------------------------------------------------
@@ -636,7 +734,10 @@ __device__ __forceinline__ void ms_run(MsParams P, unsigned *s_tab, const TcStat
         P.Vn[i] = 0u;
     }
     for (size_t i = tid; i < (size_t)P.rho * KW; i += nthreads) P.active[i] = 0u;
-    for (size_t i = tid; i < (size_t)P.rho; i += nthreads) P.dirty[i] = 0;
+    for (size_t i = tid; i < (size_t)P.rho; i += nthreads) {
+        P.dirty[i] = 0;
+        P.stamp[i] = -1;
+    }
     if (P.levels)
         for (size_t i = tid; i < (size_t)k * P.n; i += nthreads) P.levels[i] = -1;
     if (!ms_barrier(ctl, epoch, P.budget_ns)) return;
@@ -653,6 +754,7 @@ __device__ __forceinline__ void ms_run(MsParams P, unsigned *s_tab, const TcStat
         atomicOr(&P.active[(size_t)(u >> 3) * KW + (c >> 5)], bit);
         if (P.levels) P.levels[(size_t)c * P.n + so] = 0;
         if (P.reach) atomicAdd((unsigned long long *)&P.reach[u], 1ull);
+        P.stamp[u >> 3] = 0;   // the sources' F elements hold level 0
         if (atomicExch(&P.dirty[u >> 3], 1) == 0) P.dlist[1][atomicAdd(&ctl->dlen[1], 1)] = u >> 3;
     }
     if (!ms_barrier(ctl, epoch, P.budget_ns)) return;
@@ -685,14 +787,16 @@ __device__ __forceinline__ void ms_run(MsParams P, unsigned *s_tab, const TcStat
         if (threadIdx.x == 0) {
             // the previous level's counts of this CTA (all warps passed two
             // block barriers since they added them)
-            if (P.stats && ell > 1 && (s_acc.vss | s_acc.hitw | s_acc.dirty) != 0) {
+            if (P.stats && ell > 1 && (s_acc.vss | s_acc.hitw | s_acc.dirty | s_acc.parcs) != 0) {
                 red_add_u64(&P.stats->vss, s_acc.vss);
                 red_add_u64(&P.stats->hit_words, s_acc.hitw);
                 red_add_u64(&P.stats->dirty_sets, s_acc.dirty);
+                red_add_u64(&P.stats->pull_arcs, s_acc.parcs);
             }
             s_acc.vss = 0;
             s_acc.hitw = 0;
             s_acc.dirty = 0;
+            s_acc.parcs = 0;
             s_cnt = ld_volatile_i32(&ctl->qlen[qc]);
             s_grab[0] = 0;
             s_grab[1] = 0;
@@ -704,10 +808,16 @@ __device__ __forceinline__ void ms_run(MsParams P, unsigned *s_tab, const TcStat
         __syncthreads();
         if (qlen == 0) break;
         if (tid == 0) ctl->qlen[qn] = 0;
-        if constexpr (TC)
+        // the level's direction, the same in every block (qlen is the level's count)
+        const bool pull = P.dir == 2 || (P.dir == 1 && (long long)qlen * PULL_DIV > (long long)P.Nv);
+        if (pull) {
+            if (tid == 0 && P.stats) red_add_u64(&P.stats->pull_levels, 1ull);
+            ms_stage1_pull<KW>(P, st, &s_grab[0], s_tot[0], ell, dl, k, &s_acc);
+        } else if constexpr (TC) {
             ms_stage1_tc<KW>(P, st, &s_grab[0], s_tot[0], qlen, P.Q[qc], dl, s_rows, s_m, *tc, tc_phase, &s_acc);
-        else
+        } else {
             ms_stage1<KW>(P, st, &s_grab[0], s_tot[0], qlen, P.Q[qc], dl, s_rows, s_m, s_tab, &s_acc);
+        }
         if (!ms_barrier(ctl, epoch, P.budget_ns)) return;
         if (threadIdx.x == 0) s_cnt = P.track ? ld_volatile_i32(&ctl->dlen[dl]) : P.rho;
         __syncthreads();
@@ -863,6 +973,7 @@ static blest_status ms_prepare(blest_graph *h, int kappa) {
     if ((st = dev_alloc_t(h, &m->ctl, 1)) != BLEST_OK) { delete m; return st; }
     if ((st = dev_alloc_t(h, &m->d_src, 1024)) != BLEST_OK) { delete m; return st; }
     if ((st = dev_alloc_t(h, &m->stats, 1)) != BLEST_OK) { delete m; return st; }
+    if ((st = dev_alloc_t(h, &m->stamp, rho + 1)) != BLEST_OK) { delete m; return st; }
     if (cudaMemsetAsync(m->stats, 0, sizeof(MsStats), h->stream) != cudaSuccess) { delete m; return BLEST_ERR_CUDA; }
     if (cudaMallocHost((void **)&m->h_ctl, sizeof(MsCtl)) != cudaSuccess) { delete m; return BLEST_ERR_OOM; }
     m->grid = ms_grid(m->KW, false);
@@ -907,6 +1018,10 @@ static blest_status ms_launch(blest_graph *h, int k, int *levels_dev, long long 
     P.Nv = (int)h->Nv;
     P.remap = h->ms_remap;
     P.track = h->ms_track;
+    P.dir = h->ms_dir;
+    P.rp = h->g.rp;
+    P.col = h->g.col;
+    P.stamp = m->stamp;
     P.budget_ns = (unsigned long long)h->timeout_ms * 1000000ull;
     if (cudaMemsetAsync(m->ctl, 0, sizeof(MsCtl), h->stream) != cudaSuccess) return BLEST_ERR_CUDA;
     void *args[] = {&P};
@@ -1082,6 +1197,8 @@ extern "C" blest_status blest_msbfs_stats(blest_handle h, blest_msbfs_counters *
     out->vss = (int64_t)st.vss;
     out->hit_words = (int64_t)st.hit_words;
     out->dirty_sets = (int64_t)st.dirty_sets;
+    out->pull_levels = (int64_t)st.pull_levels;
+    out->pull_arcs = (int64_t)st.pull_arcs;
     return BLEST_OK;
 }
 
@@ -1091,6 +1208,14 @@ extern "C" blest_status blest_set_msbfs_engine(blest_handle h, int32_t tc) {
     if (tc && !(h->ms_remap && h->ms_track)) return BLEST_ERR_UNSUPPORTED;
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return BLEST_ERR_CUDA;
     h->ms_engine = tc;
+    return BLEST_OK;
+}
+
+extern "C" blest_status blest_set_msbfs_direction(blest_handle h, int32_t mode) {
+    if (!h || h->many || mode < 0 || mode > 2) return BLEST_ERR_INVALID;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return BLEST_ERR_CUDA;
+    h->ms_dir = mode;
+    if (h->ms) ms_release_graph(h->ms);   // the captured closeness batch bakes the direction in
     return BLEST_OK;
 }
 

@@ -68,23 +68,6 @@ def test_bvss_matches_oracle(case):
     assert abs(info["update_divergence"] - u) <= 1e-12 * max(1.0, abs(u))
 
 
-@pytest.mark.parametrize("cap", [1, 64])
-@pytest.mark.parametrize("mode", [0, 1, 2, 3, 4])
-def test_fixed_mode_levels_with_scanned_dense_levels(case, blest, mode, cap):
-    """A queue cap below the level sizes: levels past it are counted without
-    being written and the next top-down level scans every VSS's frontier
-    field instead.  Levels must not change."""
-    name, g, h = case
-    h.set_policy(blest.POLICY_FIXED, mode)
-    h.set_queue_cap(cap)
-    try:
-        for s in gg.sources(g, 4, 23):
-            assert np.array_equal(h.bfs(int(s)), oracle.bfs(g, int(s))), (name, mode, cap, s)
-    finally:
-        h.set_queue_cap(0)
-        h.set_policy(blest.POLICY_HEURISTIC)
-
-
 @pytest.mark.parametrize("mode", [0, 1, 2, 3, 4])
 def test_fixed_mode_levels(case, blest, mode):
     name, g, h = case
@@ -262,28 +245,25 @@ def test_reordered_layouts_bit_exact(blest, sigma, tau):
 
 
 @pytest.mark.parametrize("tau", [128, 32])
-def test_hub_slice_sets_long_ranges_and_queue_counts(blest, tau):
-    """Hubs whose slice sets span hundreds of VSSs (the ranges the whole CTA
-    writes at a level's flush) and a queue cap in between: levels exact,
-    and the logged queue length of every level equals the VSS count of the
-    slice sets holding the previous level's vertices (counted in full even
-    where the cap stops the writes)."""
+def test_hub_slice_sets_and_queue_counts(blest, tau):
+    """Hubs whose slice sets span hundreds of VSSs (ranges the whole warp
+    writes): levels exact in eager and lazy modes, and the logged queue
+    length of every level equals the VSS count of the slice sets holding the
+    previous level's vertices."""
     stars = gg.disjoint_union(gg.star(20000), gg.star(9000), gg.rmat(13, seed=3))
     ref_b = oracle.bvss(stars, 8, tau)
     nv_of_set = np.diff(ref_b["realPtrs"])
     assert nv_of_set.max() >= 64 * (128 // tau)
     with blest.build_graph(stars, tau=tau) as h:
-        for cap, mode in [(0, 0), (0, 2), (200, 0), (200, 2), (1, 1 if tau == 128 else 0)]:
-            h.set_queue_cap(cap)
+        for mode in [0, 2, 4, 1 if tau == 128 else 0]:
             h.set_policy(blest.POLICY_FIXED, mode)
             for s in [0, 20000, 29000, 29001 + 17]:
                 lv = h.bfs(int(s))
                 want = oracle.bfs(stars, int(s))
-                assert np.array_equal(lv, want), (tau, cap, mode, s)
+                assert np.array_equal(lv, want), (tau, mode, s)
                 for rec in h.level_log():
                     prev = np.flatnonzero(want == rec["level"] - 1)
-                    assert rec["queue"] == int(nv_of_set[np.unique(prev // 8)].sum()), (tau, cap, mode, s, rec)
-        h.set_queue_cap(0)
+                    assert rec["queue"] == int(nv_of_set[np.unique(prev // 8)].sum()), (tau, mode, s, rec)
         h.set_policy(blest.POLICY_HEURISTIC)
 
 

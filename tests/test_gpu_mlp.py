@@ -71,8 +71,8 @@ def test_predictions_match_oracle(blest):
     ref, _ = omlp.forward(w.astype(np.float64), X.astype(np.float64))
     assert np.all(np.abs(pred - ref) <= 1e-4 * (1 + np.abs(ref)))
     # the choice is the argmin with bottom-up excluded where the guard holds
-    blocked = X[:, 2].astype(np.float64) > X[:, 3].astype(np.float64) + omlp.BU_GUARD_LOG
-    near = np.abs(X[:, 2].astype(np.float64) - X[:, 3] - omlp.BU_GUARD_LOG) < 1e-4
+    blocked = X[:, 2].astype(np.float64) > X[:, 1].astype(np.float64) + omlp.BU_GUARD_LOG
+    near = np.abs(X[:, 2].astype(np.float64) - X[:, 1] - omlp.BU_GUARD_LOG) < 1e-4
     refg = ref.copy()
     refg[blocked, 4] = np.inf
     srt = np.sort(refg, axis=1)

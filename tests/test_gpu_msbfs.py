@@ -220,9 +220,10 @@ def test_msbfs_work_counters_match_the_oracle_levels(blest, name, k, tau):
     kappa = 64 if k <= 64 else (256 if k <= 256 else 1024)
     want = _expected_counters(g, len(srcs), kappa, ref, oracle.bvss(g, 8, tau))
     with blest.build_graph(g, tau=tau) as h:
+        h.set_msbfs_direction(0)             # push every level: the counts of Algorithm 5
         assert np.array_equal(h.msbfs(srcs), ref)
         st = h.msbfs_stats()
-    assert st["kappa"] == kappa and st["launches"] == 1
+    assert st["kappa"] == kappa and st["launches"] == 1 and st["pull_levels"] == 0
     for f in ("levels", "vss", "dirty_sets", "hit_words"):
         assert st[f] == want[f], (f, st[f], want[f])
 
@@ -256,6 +257,7 @@ def test_tensor_core_engine_work_counters(blest, name, k):
     want = _expected_counters(g, len(srcs), kappa, ref, oracle.bvss(g, 8, 128))
     with blest.build_graph(g) as h:
         h.set_msbfs_engine(True)
+        h.set_msbfs_direction(0)
         assert np.array_equal(h.msbfs(srcs), ref)
         st = h.msbfs_stats()
     for f in ("levels", "vss", "dirty_sets", "hit_words"):
@@ -298,3 +300,41 @@ def test_msbfs_ablation_variants_levels(blest, name, tau, reindex, tracking):
             h.set_msbfs_engine(True)        # the tensor-core engine runs Algorithm 5 in full only
         h.set_msbfs_variant(True, True)
         assert np.array_equal(h.msbfs(srcs[:40]), ref[:40])
+
+
+@pytest.mark.parametrize("direction", [0, 1, 2])
+@pytest.mark.parametrize("name", sorted(MAKERS))
+@pytest.mark.parametrize("tau", [128, 32])
+@pytest.mark.parametrize("k", [37, 300, 1024])
+def test_msbfs_directions_levels(blest, name, tau, k, direction):
+    """Push (Algorithm 5), pull on dense levels, and pull on every level give
+    the same levels; on a graph with directed arcs pulling reads the
+    in-neighbours."""
+    g = MAKERS[name]()
+    srcs = np.random.RandomState(k + 3).randint(0, g.n, size=k).astype(np.int32)
+    ref = oracle.bfs_many(g, srcs)
+    with blest.build_graph(g, tau=tau) as h:
+        h.set_msbfs_direction(direction)
+        assert np.array_equal(h.msbfs(srcs), ref)
+        st = h.msbfs_stats()
+        if direction == 2:
+            assert st["pull_levels"] == st["levels"] and st["pull_arcs"] > 0
+        if direction == 0:
+            assert st["pull_levels"] == 0 and st["pull_arcs"] == 0
+
+
+@pytest.mark.parametrize("direction", [1, 2])
+def test_pulled_closeness_and_mixed_engines(blest, direction):
+    g = gg.disjoint_union(gg.rmat(11, seed=19), gg.grid(30, 33, seed=2), gg.from_edges(3, [], [], True))
+    f_r, r_r, cc_r = oracle.closeness(g)
+    srcs = gg.sources(g, 700, 13)
+    ref = oracle.bfs_many(g, srcs)
+    with blest.build_graph(g) as h:
+        h.set_msbfs_direction(direction)
+        far, cc, reach = h.closeness()
+        assert np.array_equal(far, f_r) and np.array_equal(reach, r_r)
+        assert np.allclose(cc, cc_r, rtol=1e-12, atol=0)
+        h.set_msbfs_engine(True)             # tensor-core push levels mixed with pulled ones
+        assert np.array_equal(h.msbfs(srcs), ref)
+        far2, _, reach2 = h.closeness()
+        assert np.array_equal(far2, f_r) and np.array_equal(reach2, r_r)
