@@ -628,6 +628,8 @@ def main():
     ap.add_argument("--engine", default="cc", choices=["cc", "tc"], help="multi-source stage 1 of msbfs_one")
     ap.add_argument("--direction", type=int, default=0, choices=[0, 1, 2],
                     help="multi-source stage 1 of msbfs_one: 0 push, 1 pull on dense levels, 2 pull")
+    ap.add_argument("--staged", type=int, default=1, choices=[0, 1],
+                    help="level output of msbfs_one: 1 staged bytes and a closing transpose, 0 direct stores")
     ap.add_argument("--configs", default="C1,C3,C4,C5",
                     help="per_config entries besides the headline (C2) of the default workload")
     args = ap.parse_args()
@@ -1175,6 +1177,7 @@ def run_msbfs_one(args, ctx):
     h.set_stream(stream.cuda_stream, True)
     h.set_msbfs_engine(args.engine == "tc")
     h.set_msbfs_direction(args.direction)
+    h.set_msbfs_output(bool(args.staged))
     sd = torch.from_numpy(srcs).to(dev)
     out = torch.empty((len(srcs), g.n), dtype=torch.int32, device=dev)
     for _ in range(args.warmup):
@@ -1198,7 +1201,8 @@ def run_msbfs_one(args, ctx):
     return {"metric": "GTEPS (aggregate), one multi-source configuration", "value": edges / (ms * 1e-3) / 1e9,
             "unit": "GTEPS", "ms_per_step": ms,
             "config": {"workload": "msbfs_one", "graph": f"RMAT scale {args.scale}, edge factor 16",
-                       "kappa": len(srcs), "engine": args.engine, "direction": args.direction},
+                       "kappa": len(srcs), "engine": args.engine, "direction": args.direction,
+                       "staged_output": args.staged},
             "counters": st, "first_lanes_exact": bool(ok),
             "roofline": _roof(ctx, nb, ms * 1e-3, ("k_msbfs_tc" if args.engine == "tc" else "k_msbfs")),
             "gpu_launches": args.steps}
@@ -1297,15 +1301,19 @@ def run_ablation(args, ctx):
         h.set_policy(blest.POLICY_HEURISTIC)
         ms = _time_sources(ctx, h, srcs, out1)
         res["Naive"] = {"seconds": float(ms.sum()) * 1e-3}
-        variants = [("A", (0, 0), 0, 0), ("AB", (1, 0), 0, 0), ("Full", (1, 1), 0, 0)]
+        # (rung, (reindex, tracking), tcgen05 stage 1, direction, staged level output)
+        variants = [("A", (0, 0), 0, 0, 0), ("AB", (1, 0), 0, 0, 0), ("Full", (1, 1), 0, 0, 0),
+                    ("Full, staged level output", (1, 1), 0, 0, 1)]
         if tau == 128:
-            variants.append(("Full, tcgen05 stage 1", (1, 1), 1, 0))
-        variants += [("Full, pull on dense levels", (1, 1), 0, 1), ("Full, pull on every level", (1, 1), 0, 2)]
-        for rung, (ri, tr), eng, direction in variants:
+            variants.append(("Full, staged, tcgen05 stage 1", (1, 1), 1, 0, 1))
+        variants += [("Full, staged, pull on dense levels", (1, 1), 0, 1, 1),
+                     ("Full, staged, pull on every level", (1, 1), 0, 2, 1)]
+        for rung, (ri, tr), eng, direction, staged in variants:
             h.set_msbfs_engine(False)
             h.set_msbfs_variant(ri, tr)
             h.set_msbfs_engine(bool(eng))
             h.set_msbfs_direction(direction)
+            h.set_msbfs_output(bool(staged))
             h.msbfs(sd, out)
             h.sync()
             a, b = ctx.events()

@@ -196,6 +196,16 @@ blest_status blest_set_msbfs_direction(blest_handle h, int32_t mode);
  * Levels are identical.  The tensor-core engine runs only (1, 1). */
 blest_status blest_set_msbfs_variant(blest_handle h, int32_t reindex, int32_t tracking);
 
+/* How blest_msbfs writes its k x n source-major levels (not a step of the
+ * paper, which gives no output layout).  staged = 1 (default): stage 2 keeps
+ * one byte per (vertex, lane) in vertex-major rows of kappa bytes (levels
+ * 0..253; deeper levels go straight to the output), and after the last level
+ * the kernel transposes the rows into the output with coalesced stores; the
+ * handle allocates the rows (ceil(n/8) * 8 * kappa bytes) at the first
+ * blest_msbfs.  staged = 0: one int32 store per reached (vertex, lane) in
+ * stage 2, after a -1 fill of the output.  Levels are identical. */
+blest_status blest_set_msbfs_output(blest_handle h, int32_t staged);
+
 /* Exact closeness centrality by all-source BFS in 1024-lane batches (§6.2).
  * far: n int64 distance sums (Eq. 6); cc: n doubles, cc[u] = (reach[u]-1) /
  * far[u] (Eq. 7 with component-size normalisation; 0 when far[u] = 0), may be

@@ -121,6 +121,7 @@ _sigs = {
     "blest_set_msbfs_engine": (_S, [_H, ctypes.c_int32]),
     "blest_set_msbfs_variant": (_S, [_H, ctypes.c_int32, ctypes.c_int32]),
     "blest_set_msbfs_direction": (_S, [_H, ctypes.c_int32]),
+    "blest_set_msbfs_output": (_S, [_H, ctypes.c_int32]),
     "blest_load_model": (_S, [_H, _P, ctypes.c_int32]),
     "blest_last_timings": (_S, [_H, _P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
     "blest_get_info": (_S, [_H, ctypes.POINTER(Info)]),
@@ -293,6 +294,12 @@ class Graph:
         """Multi-source stage 1: 0 push (Algorithm 5, the default), 1 pull on
         dense levels, 2 pull on every level."""
         _check(_lib.blest_set_msbfs_direction(self._h, int(mode)), "blest_set_msbfs_direction")
+
+    def set_msbfs_output(self, staged: bool):
+        """Multi-source levels staged as bytes in vertex-major rows and
+        transposed at the end (the default), or one int32 store per reached
+        (vertex, lane)."""
+        _check(_lib.blest_set_msbfs_output(self._h, int(bool(staged))), "blest_set_msbfs_output")
 
     def set_msbfs_variant(self, reindex: bool = True, tracking: bool = True):
         """Multi-source kernel variant of the ablation: getVI reindexing and

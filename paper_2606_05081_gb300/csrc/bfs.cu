@@ -491,7 +491,6 @@ __device__ void push_level(const BfsParams &P, Stage &st, int *grab, BlkAcc *acc
     using LY = Lay<SIGMA, LPV>;
     constexpr int G = LY::G;
     const int lane = lane_id();
-    const unsigned *Fc = P.F[bc];
     const int2 *Qc = P.Q[bc];
     unsigned long long nv = 0, fe = 0;
     const int npass = (qlen + B * G - 1) / (B * G);

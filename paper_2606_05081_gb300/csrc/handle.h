@@ -59,6 +59,7 @@ struct blest_graph {
     int ms_engine = 0;                // multi-source stage 1: 0 CUDA cores, 1 tcgen05 (tau = 128)
     int ms_remap = 1, ms_track = 1;   // multi-source variant: getVI order, activeSets / dirtySets
     int ms_dir = 0;                   // multi-source stage 1: 0 push, 1 pull on dense levels, 2 pull
+    int ms_out = 1;                   // multi-source levels: 1 staged as bytes, then transposed; 0 direct
     int vss_batch = 2;
     float eta = 10.f;
     double udiv_threshold = 25000.0;

@@ -19,6 +19,12 @@
 //     major) and the closeness sums far += level * popc(diff) (Eq. 6),
 //     reach += popc(diff); activeSets = OR of the diffs; a set with any
 //     active lane enqueues its VSSs.
+// Levels (when asked for) are staged as one byte per (vertex, lane) in
+// vertex-major rows of kappa bytes, so a word's new lanes land in one 32-byte
+// sector; after the last level the grid transposes the rows into the
+// source-major int32 output with coalesced stores.  A lane-major int32 store
+// per reached (vertex, lane) would touch one sector per store in a k x n
+// array far larger than L2.
 // The words of lanes that are inactive for a slice set (activeSets word = 0)
 // are never loaded.
 #include <cstdio>
@@ -60,6 +66,7 @@ struct MsbfsWork {
     MsCtl *h_ctl = nullptr;
     MsStats *stats = nullptr;      // device counters of the current call
     int *stamp = nullptr;          // per slice set: the level stage 2 last finalised it
+    unsigned char *lv8 = nullptr;  // staged levels: rho * 8 rows of kappa bytes (allocated on first use)
     int *d_src = nullptr;
     int grid = 0;
     int grid_tc = -1;              // grid of the tensor-core kernel (-1: not computed yet)
@@ -96,6 +103,8 @@ struct MsParams {
     const int *old_of_new;        // may be null
     const int *k_dev;             // non-null: the batch size is read here (graph replays)
     int *levels;                  // k*n, source-major, original ids; may be null
+    unsigned char *lv8;           // non-null: levels staged as bytes, row u (reordered id) of KW*32
+                                  //    lanes; LV8_FAR marks a lane written directly to levels
     long long *far, *reach;       // may be null
     MsStats *stats;               // work counters (added once per CTA and level)
     int Nv;                       // VSSs of the BVSS
@@ -118,6 +127,53 @@ struct MsAcc {
 // A level pulls (direction 1) when its queue holds more than 1/PULL_DIV of
 // the VSSs.
 constexpr long long PULL_DIV = 8;
+
+// Staged level bytes: 0 .. LV8_FAR - 1 are levels, LV8_NONE is unreached,
+// LV8_FAR a level >= LV8_FAR stored directly in the int32 output.
+constexpr unsigned LV8_FAR = 0xFEu, LV8_NONE = 0xFFu;
+
+// 0xFF in byte q of the result where bit q of the 4-bit x is set
+__device__ __forceinline__ unsigned byte_mask4(unsigned x) {
+    return ((x & 1u) ? 0xFFu : 0u) | ((x & 2u) ? 0xFF00u : 0u) | ((x & 4u) ? 0xFF0000u : 0u) |
+           ((x & 8u) ? 0xFF000000u : 0u);
+}
+
+// The staged level bytes of the lanes in diff (word w of vertex u, reached
+// at level ell); cur holds the lanes reached earlier, whose bytes stay.  A
+// 4-lane group with no earlier lane is written as one word (new lanes ell,
+// the others still unreached); otherwise byte by byte.
+template <int KW>
+__device__ __forceinline__ void lv8_store(const MsParams &P, int u, int w, unsigned diff, unsigned cur, int ell) {
+    const unsigned val = ell < (int)LV8_FAR ? (unsigned)ell : LV8_FAR;
+    const unsigned rep = val * 0x01010101u;
+    unsigned char *row = P.lv8 + (size_t)u * (KW * 32) + (size_t)w * 32;
+    if (cur == 0u) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            unsigned x[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const unsigned m = byte_mask4((diff >> (16 * h + 4 * j)) & 15u);
+                x[j] = (rep & m) | ~m;
+            }
+            reinterpret_cast<uint4 *>(row)[h] = make_uint4(x[0], x[1], x[2], x[3]);
+        }
+        return;
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const unsigned nb = (diff >> (4 * j)) & 15u;
+        if (!nb) continue;
+        if (((cur >> (4 * j)) & 15u) == 0u) {
+            const unsigned m = byte_mask4(nb);
+            reinterpret_cast<unsigned *>(row)[j] = (rep & m) | ~m;
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if ((nb >> q) & 1u) row[4 * j + q] = (unsigned char)val;
+        }
+    }
+}
 
 __device__ __forceinline__ bool ms_barrier(MsCtl *ctl, unsigned &epoch, unsigned long long budget) {
     return grid_barrier(reinterpret_cast<Ctl *>(ctl), epoch, budget);
@@ -409,7 +465,8 @@ __device__ void ms_stage2(const MsParams &P, MsStage &st, int *grab, int *s_tot,
                 if (diff) {
                     P.Vc[e] = next;
                     A |= diff;
-                    if (P.levels) {
+                    if (P.lv8) lv8_store<KW>(P, u, w, diff, cur, ell);
+                    if (P.levels && (!P.lv8 || ell >= (int)LV8_FAR)) {
                         const int uo = P.old_of_new ? __ldg(&P.old_of_new[u]) : u;
                         unsigned d = diff;
                         while (d) {
@@ -702,6 +759,34 @@ __device__ void ms_stage1_tc(const MsParams &P, MsStage &st, int *grab, int *s_t
     ms_block_flush(P.dlist[dl], &P.ctl->dlen[dl], st.d, st.dn, s_tot);
 }
 
+// Staged levels -> the source-major int32 output: a warp takes 32 lanes x
+// 32 vertices (original ids), each thread one vertex's 32 bytes, and writes
+// 32 rows of 128 contiguous bytes.  Out of line: it runs once per launch,
+// and inlined it would take registers from the level loop.
+template <int KW>
+__device__ __noinline__ void lv8_transpose(const unsigned char *lv8, int *levels, const int *new_of_old, int n, int k,
+                                           size_t tid, size_t nthreads) {
+    const int ntc = (k + 31) >> 5;
+    const long long tiles = (long long)((n + 31) >> 5) * ntc;
+    const int lane = lane_id();
+    for (long long t = (long long)(tid >> 5); t < tiles; t += (long long)(nthreads >> 5)) {
+        const int tcol = (int)(t % ntc);
+        const int uo = (int)(t / ntc) * 32 + lane;
+        if (uo >= n) continue;
+        const int u = new_of_old ? __ldg(&new_of_old[uo]) : uo;
+        const uint4 *src = reinterpret_cast<const uint4 *>(lv8 + (size_t)u * (KW * 32) + (size_t)tcol * 32);
+        const uint4 a = __ldcg(src), b = __ldcg(src + 1);
+        const unsigned x[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+        int *o = levels + (size_t)tcol * 32 * (size_t)n + uo;
+        const int cmax = min(32, k - tcol * 32);
+#pragma unroll
+        for (int c = 0; c < 32; ++c) {
+            const unsigned v = (x[c >> 2] >> ((c & 3) * 8)) & 0xFFu;
+            if (c < cmax && v != LV8_FAR) o[(size_t)c * n] = v == LV8_NONE ? -1 : (int)v;
+        }
+    }
+}
+
 // The whole multi-source BFS of one launch (every block calls it; a block
 // returns early only at a grid barrier that failed, all its threads
 // together).  tc: the tensor-core stage 1 (its tensor memory is allocated
@@ -738,8 +823,13 @@ __device__ __forceinline__ void ms_run(MsParams P, unsigned *s_tab, const TcStat
         P.dirty[i] = 0;
         P.stamp[i] = -1;
     }
-    if (P.levels)
+    if (P.lv8) {
+        uint4 *l8 = reinterpret_cast<uint4 *>(P.lv8);
+        const uint4 none = make_uint4(~0u, ~0u, ~0u, ~0u);
+        for (size_t i = tid; i < (size_t)P.rho * KW * 16; i += nthreads) l8[i] = none;
+    } else if (P.levels) {
         for (size_t i = tid; i < (size_t)k * P.n; i += nthreads) P.levels[i] = -1;
+    }
     if (!ms_barrier(ctl, epoch, P.budget_ns)) return;
     // ---- sources: lane c starts at srcs[c]
     if (tid < (size_t)k) {
@@ -752,7 +842,8 @@ __device__ __forceinline__ void ms_run(MsParams P, unsigned *s_tab, const TcStat
         atomicOr(&P.Vn[e], bit);
         atomicOr(&P.F[e], bit);
         atomicOr(&P.active[(size_t)(u >> 3) * KW + (c >> 5)], bit);
-        if (P.levels) P.levels[(size_t)c * P.n + so] = 0;
+        if (P.lv8) P.lv8[(size_t)u * (KW * 32) + c] = 0;
+        else if (P.levels) P.levels[(size_t)c * P.n + so] = 0;
         if (P.reach) atomicAdd((unsigned long long *)&P.reach[u], 1ull);
         P.stamp[u >> 3] = 0;   // the sources' F elements hold level 0
         if (atomicExch(&P.dirty[u >> 3], 1) == 0) P.dlist[1][atomicAdd(&ctl->dlen[1], 1)] = u >> 3;
@@ -827,6 +918,9 @@ __device__ __forceinline__ void ms_run(MsParams P, unsigned *s_tab, const TcStat
         ms_stage2<KW>(P, st, &s_grab[1], s_tot[1], ell, dl, qn, dcount, k, &s_acc);
         if (!ms_barrier(ctl, epoch, P.budget_ns)) return;
     }
+    // ---- staged levels -> source-major int32 (the last level's stage 2
+    // ended at a grid barrier, so every byte is in place)
+    if (P.lv8) lv8_transpose<KW>(P.lv8, P.levels, P.new_of_old, P.n, k, tid, nthreads);
     if (tid == 0) {
         ctl->nlevels = ell - 1;
         if (P.stats) {
@@ -1012,6 +1106,7 @@ static blest_status ms_launch(blest_graph *h, int k, int *levels_dev, long long 
     P.old_of_new = h->g.old_of_new;
     P.k_dev = k_dev;
     P.levels = levels_dev;
+    P.lv8 = (levels_dev && h->ms_out) ? m->lv8 : nullptr;
     P.far = far;
     P.reach = reach;
     P.stats = m->stats;
@@ -1059,6 +1154,9 @@ extern "C" blest_status blest_msbfs(blest_handle h, const int32_t *sources, int3
         if (s < 0 || (int64_t)s >= h->n) return BLEST_ERR_INVALID;
     blest_status st = ms_prepare(h, kappa_for(k));
     if (st != BLEST_OK) return st;
+    if (h->ms_out && !h->ms->lv8 &&
+        (st = dev_alloc_t(h, &h->ms->lv8, (size_t)h->Ns * 8 * (size_t)h->ms->kappa)) != BLEST_OK)
+        return st;
     const bool dev = is_device_ptr(levels);
     int32_t *target = levels;
     if (!dev) {
@@ -1216,6 +1314,13 @@ extern "C" blest_status blest_set_msbfs_direction(blest_handle h, int32_t mode) 
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return BLEST_ERR_CUDA;
     h->ms_dir = mode;
     if (h->ms) ms_release_graph(h->ms);   // the captured closeness batch bakes the direction in
+    return BLEST_OK;
+}
+
+extern "C" blest_status blest_set_msbfs_output(blest_handle h, int32_t staged) {
+    if (!h || h->many || (staged != 0 && staged != 1)) return BLEST_ERR_INVALID;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return BLEST_ERR_CUDA;
+    h->ms_out = staged;
     return BLEST_OK;
 }
 

@@ -338,3 +338,38 @@ def test_pulled_closeness_and_mixed_engines(blest, direction):
         assert np.array_equal(h.msbfs(srcs), ref)
         far2, _, reach2 = h.closeness()
         assert np.array_equal(far2, f_r) and np.array_equal(reach2, r_r)
+
+
+@pytest.mark.parametrize("staged", [1, 0])
+@pytest.mark.parametrize("reorder", [0, 1])
+@pytest.mark.parametrize("k", [5, 300, 1024])
+def test_msbfs_output_paths_deep_and_reordered(blest, staged, reorder, k):
+    """Both ways of writing the source-major levels (staged bytes plus the
+    closing transpose, or direct int32 stores), on a reordered graph (the
+    transpose reads row new_of_old[v] for output column v) and on a path of
+    700 vertices whose levels run past the 253 a staged byte holds (deeper
+    lanes go straight to the output and the transpose must leave them)."""
+    g = gg.disjoint_union(gg.path(700), gg.rmat(10, seed=12), gg.grid(13, 29, seed=13))
+    rs = np.random.RandomState(100 + k)
+    srcs = np.r_[[0, 699, 350], rs.randint(0, g.n, size=k - 3)].astype(np.int32)
+    ref = oracle.bfs_many(g, srcs)
+    assert ref.max() > 300
+    with blest.build_graph(g, reorder=reorder) as h:
+        h.set_msbfs_output(bool(staged))
+        got = h.msbfs(srcs)
+        bad = np.argwhere(got != ref)
+        assert len(bad) == 0, (staged, reorder, k, bad[:5])
+        out = torch.full((k, g.n), 7, dtype=torch.int32, device="cuda")   # every element must be written
+        h.msbfs(torch.from_numpy(srcs).cuda(), out)
+        assert np.array_equal(out.cpu().numpy(), ref)
+
+
+def test_msbfs_output_switch_between_calls(blest):
+    """Staged and direct output alternate on one handle, and a smaller batch
+    after a larger one reuses the larger rows."""
+    g = gg.rmat(12, seed=14)
+    with blest.build_graph(g) as h:
+        for staged, k in ((1, 1024), (0, 200), (1, 64), (1, 1000), (0, 1)):
+            srcs = gg.sources(g, k, k)
+            h.set_msbfs_output(bool(staged))
+            assert np.array_equal(h.msbfs(srcs), oracle.bfs_many(g, srcs)), (staged, k)
