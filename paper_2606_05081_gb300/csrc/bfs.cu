@@ -922,16 +922,23 @@ __device__ __forceinline__ void push_dispatch(const BfsParams &P, Stage &st, int
 // the road-like grid: the kernel is latency-bound and 32 warps is the best
 // trade.
 template <int SIGMA, int LPV>
-__global__ void __launch_bounds__(BFS_MAX_THREADS, 1) k_bfs(BfsParams P) {
+__global__ void __launch_bounds__(BFS_MAX_THREADS, 1) k_bfs(const BfsParams Pk) {
     using LY = Lay<SIGMA, LPV>;
     __shared__ unsigned s_found[BFS_MAX_THREADS];
     __shared__ float s_mlp[MLP_NW];
     extern __shared__ __align__(16) unsigned char s_stage[];   // STG_BYTES per warp
-    if (P.policy == BLEST_POLICY_LEARNED && P.mlp) {
-        mlp_stage_weights(P.mlp, s_mlp);
-        __syncthreads();
-        P.mlp = s_mlp;
+    // The parameters live in shared memory for the whole launch: the level
+    // functions take them by reference and index the buffer rings (F, Q, SQ)
+    // with the level, which would otherwise place a copy of the struct in
+    // local memory and turn every field read into a local load.
+    __shared__ BfsParams s_par;
+    if (threadIdx.x == 0) {
+        s_par = Pk;
+        if (Pk.policy == BLEST_POLICY_LEARNED && Pk.mlp) s_par.mlp = s_mlp;
     }
+    if (Pk.policy == BLEST_POLICY_LEARNED && Pk.mlp) mlp_stage_weights(Pk.mlp, s_mlp);
+    __syncthreads();
+    const BfsParams &P = s_par;
     const int tid = (int)(blockIdx.x * blockDim.x + threadIdx.x);
     const int nthreads = (int)(gridDim.x * blockDim.x);
     const int lane = lane_id();
