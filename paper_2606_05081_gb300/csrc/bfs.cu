@@ -755,8 +755,7 @@ __device__ __forceinline__ void finalize_group(const BfsParams &P, Stage &st, Bl
     fe += (unsigned long long)(dv[0] + dv[1]) + (unsigned long long)(dv[2] + dv[3]);
 }
 
-// Stage 2 over all words: a claim covers two 32-word groups, i and i +
-// half, whose visited words are loaded before either is used; claims are
+// Stage 2 over all words: a claim covers one 32-word group; claims are
 // interleaved over the blocks and taken by the block's warps from a shared
 // counter (the changed words cluster, so a fixed split leaves a few warps
 // with most of the work).
@@ -764,23 +763,30 @@ template <int SIGMA>
 __device__ void finalize_level(const BfsParams &P, Stage &st, int *grab, BlkAcc *acc, int ell, int bn, int slot) {
     const int lane = lane_id();
     unsigned long long nv = 0, fe = 0;
-    const int ngroups = (P.W + 31) / 32, half = (ngroups + 1) / 2;
-    for (;;) {
+    const int ngroups = (P.W + 31) / 32;
+    // one group per claim; the next group's words load while the current
+    // one is finalised
+    auto claim = [&](int &i, unsigned &nx, unsigned &cu) {
         int k = 0;
         if (lane == 0) k = atomicAdd(grab, 1);
         k = __shfl_sync(FULL_MASK, k, 0);
-        const int i = (int)blockIdx.x + k * (int)gridDim.x;
-        if (i >= half) break;
-        unsigned nx[2], cu[2];
-#pragma unroll
-        for (int g2 = 0; g2 < 2; ++g2) {
-            const int tt = (i + g2 * half) * 32 + lane;
-            nx[g2] = tt < P.W ? P.Vn[tt] : 0u;
-            cu[g2] = tt < P.W ? P.Vc[tt] : 0u;
-        }
-#pragma unroll 1
-        for (int g2 = 0; g2 < 2; ++g2)
-            finalize_group<SIGMA>(P, st, acc, (i + g2 * half) * 32, nx[g2], cu[g2], false, ell, bn, slot, nv, fe);
+        i = (int)blockIdx.x + k * (int)gridDim.x;
+        const int tt = i * 32 + lane;
+        const bool ok = i < ngroups && tt < P.W;
+        nx = ok ? P.Vn[tt] : 0u;
+        cu = ok ? P.Vc[tt] : 0u;
+    };
+    int i;
+    unsigned nx, cu;
+    claim(i, nx, cu);
+    while (i < ngroups) {
+        int i1;
+        unsigned nx1, cu1;
+        claim(i1, nx1, cu1);
+        finalize_group<SIGMA>(P, st, acc, i * 32, nx, cu, false, ell, bn, slot, nv, fe);
+        i = i1;
+        nx = nx1;
+        cu = cu1;
     }
     block_flush(P, st, acc, P.Q[bn], P.SQ[bn], slot, nv, fe);
 }
