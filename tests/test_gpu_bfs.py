@@ -284,3 +284,23 @@ def test_sixteen_mma_layout_levels(blest, name):
     with blest.build_graph(g, tau=32) as h:
         with pytest.raises(blest.BlestError):
             h.set_engine(2)
+
+
+@pytest.mark.parametrize("reorder", [0, 1, 2])
+def test_pinned_and_pageable_host_output(blest, reorder):
+    """Page-locked host buffers, 16-byte aligned or not, and a pageable one
+    receive the levels of plain and reordered graphs, every element
+    written."""
+    g = gg.disjoint_union(gg.rmat(12, seed=41), gg.grid(17, 23, seed=42), gg.from_edges(5, [], [], True))
+    srcs = gg.sources(g, 6, 43)
+    refs = oracle.bfs_many(g, srcs)
+    with blest.build_graph(g, reorder=reorder) as h:
+        for off in (0, 1):   # 16-byte aligned, then not
+            base = torch.full((g.n + 1,), 7, dtype=torch.int32).pin_memory()
+            host = base.numpy()[off:off + g.n]
+            for s, ref in zip(srcs, refs):
+                h.bfs(int(s), host)
+                assert np.array_equal(host, ref), (reorder, off, int(s))
+        plain = np.full(g.n, 7, np.int32)
+        h.bfs(int(srcs[0]), plain)
+        assert np.array_equal(plain, refs[0])
