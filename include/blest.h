@@ -281,6 +281,15 @@ blest_status blest_set_launch(blest_handle h, int32_t block_threads, int32_t vss
  * lazy updates, off otherwise); this overrides that decision. */
 blest_status blest_set_switching(blest_handle h, int32_t on);
 
+/* Deferred VSS queues (not a step of the paper): a lazy (Algorithm 3) or
+ * bottom-up (Algorithm 4) level counts the VSS queue of the next level and
+ * writes only its slice-set list; a top-down level that follows writes the
+ * queue from that list first (one pass and a grid barrier), while a
+ * bottom-up level, which reads only the frontier bits, skips it.  mode = 1
+ * on, 0 off, -1 (the default) on exactly when bottom-up switching is on.
+ * Levels are identical. */
+blest_status blest_set_queue_deferral(blest_handle h, int32_t mode);
+
 /* Per-level modes for BLEST_POLICY_SCHEDULE: level l (1-based) runs
  * modes[(l-1) % len].  Copied. */
 blest_status blest_set_schedule(blest_handle h, const int32_t *modes, int32_t len);

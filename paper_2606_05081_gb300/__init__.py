@@ -118,6 +118,7 @@ _sigs = {
     "blest_set_engine": (_S, [_H, ctypes.c_int32]),
     "blest_set_launch": (_S, [_H, ctypes.c_int32, ctypes.c_int32]),
     "blest_set_switching": (_S, [_H, ctypes.c_int32]),
+    "blest_set_queue_deferral": (_S, [_H, ctypes.c_int32]),
     "blest_set_msbfs_engine": (_S, [_H, ctypes.c_int32]),
     "blest_set_msbfs_variant": (_S, [_H, ctypes.c_int32, ctypes.c_int32]),
     "blest_set_msbfs_direction": (_S, [_H, ctypes.c_int32]),
@@ -310,6 +311,11 @@ class Graph:
     def set_switching(self, on: bool):
         """Eq. 5 bottom-up switching of the rule on or off (overrides the build's probe)."""
         _check(_lib.blest_set_switching(self._h, int(bool(on))), "blest_set_switching")
+
+    def set_queue_deferral(self, mode: int):
+        """Deferred VSS queues of lazy and bottom-up levels: 1 on, 0 off, -1
+        (the default) on exactly when bottom-up switching is on."""
+        _check(_lib.blest_set_queue_deferral(self._h, int(mode)), "blest_set_queue_deferral")
 
     def set_schedule(self, modes):
         m = np.ascontiguousarray(modes, dtype=np.int32)

@@ -51,6 +51,7 @@ struct BfsParams {
     int log_cap;
     int src;
     int policy, fixed_mode, lazy, tc, switching;
+    int defer_queue;        // lazy and bottom-up levels count their VSS queue and leave it to the next level
     int tc16;               // tensor-core levels use the 16-MMA layout instead of Fig. 3's
     float eta;
     const int *schedule;
@@ -209,6 +210,8 @@ struct Stage {
     int2 *q;     // this warp's staging area in shared memory
     int *sq;
     int qn, sqn; // staged counts (warp-uniform)
+    int defer;   // the level's VSS queue is counted, not written (warp-uniform)
+    int qdef;    // VSS entries counted but not written by this warp
 };
 
 __device__ __forceinline__ void stage_flush(const BfsParams &P, Stage &st, int2 *Q, int *SQ, int slot) {
@@ -250,6 +253,19 @@ __device__ __forceinline__ void enqueue_ranges(const BfsParams &P, Stage &st, un
     const int sincl = warp_incl_scan(nset);
     const int T = __shfl_sync(FULL_MASK, incl, 31);
     const int S = __shfl_sync(FULL_MASK, sincl, 31);
+    if (st.defer) {
+        // deferred queue: the slice sets are staged, their VSSs only counted
+        // (the next level expands them from the slice-set queue if it pushes)
+        if (st.sqn + S > STG_S) stage_flush(P, st, Q, SQ, slot);
+        int sb = st.sqn + sincl - nset;
+        st.sqn += S;
+        st.qdef += T;
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            if (want >> c & 1u) st.sq[sb++] = ss[c];
+        __syncwarp();
+        return;
+    }
     if ((T <= STG_Q && st.qn + T > STG_Q) || st.sqn + S > STG_S) stage_flush(P, st, Q, SQ, slot);
     int2 *dst;
     int qbase;
@@ -306,7 +322,7 @@ __device__ __forceinline__ void block_flush(const BfsParams &P, Stage &st, BlkAc
     fe = warp_sum(fe);
     int wq = 0, ws = 0;
     if (lane == 0) {
-        if (st.qn) wq = atomicAdd(&acc->q, st.qn);
+        if (st.qn + st.qdef) wq = atomicAdd(&acc->q, st.qn + st.qdef);   // deferred entries follow the staged ones
         if (st.sqn) ws = atomicAdd(&acc->s, st.sqn);
         if (nv) {
             atomicAdd(&acc->nv, nv);
@@ -335,6 +351,64 @@ __device__ __forceinline__ void block_flush(const BfsParams &P, Stage &st, BlkAc
     __syncwarp();
     st.qn = 0;
     st.sqn = 0;
+    st.qdef = 0;
+}
+
+// Writes a deferred VSS queue: the VSS ranges of the nsq slice sets in SQ.
+// Each CTA takes a contiguous share of the slice sets, blockDim.x at a time:
+// a block-wide scan of the range lengths, one reservation in Q per round,
+// then every thread writes entries k, k + blockDim.x, ... of the round,
+// finding each entry's slice set by binary search over the scan, so a hub's
+// range of thousands of VSSs is spread over the whole CTA.  Called by every
+// thread of the grid; a grid barrier follows.  (Push levels take their
+// entries in any order.)
+__device__ void expand_queue(const BfsParams &P, int bc, int sc, int nsq) {
+    __shared__ int s_incl[BFS_MAX_THREADS], s_a[BFS_MAX_THREADS], s_ss[BFS_MAX_THREADS];
+    __shared__ int s_wsum[32];
+    __shared__ int s_tot, s_base;
+    const int lane = lane_id(), warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int *SQc = P.SQ[bc];
+    int2 *Qc = P.Q[bc];
+    const int per = (nsq + (int)gridDim.x - 1) / (int)gridDim.x;
+    const int lo = (int)blockIdx.x * per, hi = min(nsq, lo + per);
+    for (int r0 = lo; r0 < hi; r0 += blockDim.x) {   // CTA-uniform
+        const int j = r0 + (int)threadIdx.x;
+        int ss = 0, a = 0, len = 0;
+        if (j < hi) {
+            ss = SQc[j];
+            a = __ldg(&P.realPtrs[ss]);
+            len = __ldg(&P.realPtrs[ss + 1]) - a;
+        }
+        int incl = warp_incl_scan(len);
+        if (lane == 31) s_wsum[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            const int x = lane < nwarps ? s_wsum[lane] : 0;
+            const int xi = warp_incl_scan(x);
+            s_wsum[lane] = xi - x;
+            if (lane == 31) s_tot = xi;
+        }
+        __syncthreads();
+        incl += s_wsum[warp];
+        s_incl[threadIdx.x] = incl;
+        s_a[threadIdx.x] = a;
+        s_ss[threadIdx.x] = ss;
+        if (threadIdx.x == 0) s_base = s_tot ? atomicAdd(&P.ctl->xq[sc], s_tot) : 0;
+        __syncthreads();
+        const int tot = s_tot, base = s_base;
+        const int nent = min((int)blockDim.x, hi - r0);
+        for (int k = threadIdx.x; k < tot; k += blockDim.x) {
+            int l = 0, h = nent - 1;   // the first entry whose inclusive end exceeds k
+            while (l < h) {
+                const int mid = (l + h) >> 1;
+                if (s_incl[mid] > k) h = mid;
+                else l = mid + 1;
+            }
+            const int ex = l ? s_incl[l - 1] : 0;
+            Qc[base + k] = make_int2(s_a[l] + (k - ex), s_ss[l]);
+        }
+        __syncthreads();   // the arrays are rewritten by the next round
+    }
 }
 
 // ---------------------------------------------------------------- push
@@ -885,6 +959,7 @@ __device__ __forceinline__ void housekeeping(const BfsParams &P, int ell, int bo
     if (rt == 0) {
         ctl->qlen[sz] = 0;
         ctl->sqlen[sz] = 0;
+        ctl->xq[sz] = 0;
         ctl->newv[sz] = 0;
         ctl->fedges[sz] = 0;
         ctl->scan_v[sz] = 0;
@@ -956,8 +1031,10 @@ __global__ void __launch_bounds__(BFS_MAX_THREADS, 1) k_bfs(const BfsParams Pk) 
     st.sq = reinterpret_cast<int *>(s_stage + (size_t)(threadIdx.x >> 5) * STG_BYTES + STG_Q * 8);
     st.qn = 0;
     st.sqn = 0;
+    st.defer = 0;
+    st.qdef = 0;
     __shared__ int s_mode;
-    __shared__ long long s_lvl[4];
+    __shared__ long long s_lvl[5];
     __shared__ int s_grab[3];   // per-level work claims: push passes, stage-2 groups, bottom-up groups
     __shared__ BlkAcc s_acc;    // per-level CTA totals for the last flush
 
@@ -1009,15 +1086,16 @@ __global__ void __launch_bounds__(BFS_MAX_THREADS, 1) k_bfs(const BfsParams Pk) 
         // same control-block words would pile ~20K requests onto one L2 line),
         // decides the mode and publishes both through shared memory.
         if (threadIdx.x < 32) {
-            long long c4[4] = {0, 0, 0, 0};
+            long long c4[5] = {0, 0, 0, 0, 0};
             if (threadIdx.x == 0) {
                 c4[0] = ld_volatile_i32(&ctl->qlen[sc]);
                 c4[1] = (long long)*(volatile unsigned long long *)&ctl->newv[sc];
                 c4[2] = (long long)*(volatile unsigned long long *)&ctl->fedges[sc];
                 c4[3] = ell >= 2 ? ld_volatile_i32(&ctl->sqlen[so]) : 0;
+                c4[4] = ld_volatile_i32(&ctl->sqlen[sc]);
             }
 #pragma unroll
-            for (int i = 0; i < 4; ++i) c4[i] = __shfl_sync(FULL_MASK, c4[i], 0);
+            for (int i = 0; i < 5; ++i) c4[i] = __shfl_sync(FULL_MASK, c4[i], 0);
             const long long unv = (long long)P.n - (visited + c4[1]);
             const int m = c4[0] > 0 ? decide_mode<LY::TC_OK>(P, ell, c4[1], c4[2], unv, c4[0] * LY::TAU,
                                                              (int)c4[0])
@@ -1027,6 +1105,7 @@ __global__ void __launch_bounds__(BFS_MAX_THREADS, 1) k_bfs(const BfsParams Pk) 
                 s_lvl[1] = c4[1];
                 s_lvl[2] = c4[2];
                 s_lvl[3] = c4[3];
+                s_lvl[4] = c4[4];
                 s_mode = m;
                 s_grab[0] = 0;
                 s_grab[1] = 0;
@@ -1044,6 +1123,7 @@ __global__ void __launch_bounds__(BFS_MAX_THREADS, 1) k_bfs(const BfsParams Pk) 
         const long long frontier = s_lvl[1];
         const long long fedges = s_lvl[2];
         const int sql_old = (int)s_lvl[3];
+        const int sql_cur = (int)s_lvl[4];
         const int choice = s_mode;
         const int mode = mlp_choice_mode(choice);
         // VSS passes in flight: the learned choice's, else the launch's setting
@@ -1082,6 +1162,18 @@ __global__ void __launch_bounds__(BFS_MAX_THREADS, 1) k_bfs(const BfsParams Pk) 
             }
         }
         if (qlen == 0) break;
+
+        // A top-down level after a level that deferred its VSS queue writes
+        // the queue first (one pass over the slice-set queue and a barrier).
+        if (st.defer && mode != BLEST_MODE_BOTTOM_UP) {
+            expand_queue(P, bc, sc, sql_cur);
+            if (!grid_barrier(ctl, epoch, P.budget_ns)) return;
+        }
+        // Lazy and bottom-up levels of graphs with bottom-up switching defer
+        // their VSS queue: the level after them is most often bottom-up,
+        // which reads only the frontier bits.
+        st.defer = P.defer_queue && (mode == BLEST_MODE_BOTTOM_UP || mode == BLEST_MODE_PUSH_LAZY_CC ||
+                                     mode == BLEST_MODE_PUSH_LAZY_TC);
 
         if (mode == BLEST_MODE_PUSH_EAGER_CC || mode == BLEST_MODE_PUSH_EAGER_TC) {
             push_dispatch<true, SIGMA, LPV>(P, st, &s_grab[0], &s_acc, mode == BLEST_MODE_PUSH_EAGER_TC, ell, bc, bn, sn, qlen, bsel);
@@ -1237,6 +1329,7 @@ blest_status bfs_run(blest_graph *h, int32_t source, int32_t *dev_out) {
     P.tc = h->engine_tc != 0;
     P.tc16 = h->engine_tc == 2;
     P.switching = h->switching;
+    P.defer_queue = h->defer_queue < 0 ? h->switching : h->defer_queue;
     P.eta = h->eta;
     P.schedule = h->d_schedule;
     P.sched_len = h->sched_len;

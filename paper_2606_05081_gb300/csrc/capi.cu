@@ -250,6 +250,12 @@ extern "C" blest_status blest_set_launch(blest_handle h, int32_t block_threads, 
     return BLEST_OK;
 }
 
+extern "C" blest_status blest_set_queue_deferral(blest_handle h, int32_t mode) {
+    if (!h || h->many || mode < -1 || mode > 1) return BLEST_ERR_INVALID;
+    h->defer_queue = mode;
+    return BLEST_OK;
+}
+
 extern "C" blest_status blest_set_switching(blest_handle h, int32_t on) {
     if (!h || h->many || (on != 0 && on != 1)) return BLEST_ERR_INVALID;
     h->switching = on;

@@ -76,6 +76,7 @@ struct Ctl {
     unsigned long long fedges[4];  // out-arcs of those vertices
     unsigned long long scan_v[4];  // bottom-up: vertices probed
     unsigned long long scan_a[4];  // bottom-up: in-neighbour ids read
+    int xq[4];             // entries written so far when a deferred VSS queue is expanded
 };
 
 // Timed-out grid barrier for a cooperative launch.  Every block calls it the

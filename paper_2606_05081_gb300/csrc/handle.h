@@ -58,6 +58,7 @@ struct blest_graph {
     int engine_tc = 1;
     int ms_engine = 0;                // multi-source stage 1: 0 CUDA cores, 1 tcgen05 (tau = 128)
     int ms_remap = 1, ms_track = 1;   // multi-source variant: getVI order, activeSets / dirtySets
+    int defer_queue = -1;             // deferred VSS queues: -1 on graphs with bottom-up switching, 0 off, 1 on
     int ms_dir = 0;                   // multi-source stage 1: 0 push, 1 pull on dense levels, 2 pull
     int ms_out = 1;                   // multi-source levels: 1 staged as bytes, then transposed; 0 direct
     int vss_batch = 2;

@@ -95,6 +95,32 @@ def test_heuristic_and_random_schedules(case, blest):
     h.set_policy(blest.POLICY_HEURISTIC)
 
 
+@pytest.mark.parametrize("defer", [1, 0])
+def test_deferred_queue_with_every_mode_transition(case, blest, defer):
+    """Lazy and bottom-up levels that defer their VSS queue (counted, then
+    written from the slice-set list by a top-down level that follows):
+    levels are exact under schedules that cover every pair of modes, and
+    the logged queue lengths equal those of the levels that write it."""
+    name, g, h = case
+    srcs = gg.sources(g, 3, 29)
+    refs = [oracle.bfs(g, int(s)) for s in srcs]
+    schedules = [[2, 0], [2, 2], [4, 0], [4, 2], [4, 4, 0], [2, 4, 1, 3, 4], [3, 0, 4, 3, 4, 2, 1]]
+    try:
+        for sched in schedules:
+            h.set_schedule(sched)
+            h.set_policy(blest.POLICY_SCHEDULE)
+            logs = {}
+            for d in (defer, 1 - defer):
+                h.set_queue_deferral(d)
+                for s, r in zip(srcs, refs):
+                    assert np.array_equal(h.bfs(int(s)), r), (name, sched, d, int(s))
+                logs[d] = [(x["level"], x["queue"], x["frontier"]) for x in h.level_log()]
+            assert logs[0] == logs[1], (name, sched)
+    finally:
+        h.set_queue_deferral(-1)
+        h.set_policy(blest.POLICY_HEURISTIC)
+
+
 def test_device_output_and_level_log(case, blest):
     name, g, h = case
     s = int(gg.sources(g, 1, 31)[0])
